@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Containment-query benchmark (one JSON line on rank 0).
+
+Default workload: 64 planar domains with open, noisy loops (4-12 loops of
+32-512 segments of degree 1-5, gaps 1e-4..1e-2, control-point noise 1e-4),
+10M uniform + 1M near-curve queries, classified in one batched call of the
+mixed FP32 + FP64-fallback path.  A step is one such call over the whole
+batch with the queries already in HBM (176 MB of points, larger than L2; L2
+is also flushed between steps outside the timed events).
+
+Also reported: e2e (the same call with host buffers, copies included), the
+plain FP64 path on the same GPU (one launch per domain), the sweep kernel's
+achieved FP32 rate against the ALU peak, the FP64 oracle on the host cores
+(a bounded sample, which doubles as a parity check of the timed results),
+and the SM clocks seen during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload 1..5]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import wn_synth as ws  # noqa: E402
+
+METRIC = "containment queries/s, batched FP32+FP64-fallback vs plain, 0 oracle mismatches"
+UNIT = "queries/s"
+# algorithmic FP32 work of one top-level (query, segment) test of the sweep:
+# ellipse far test ~7 flops + chord angle ~27 flops (atan2 counted as 20)
+FLOPS_PER_PAIR = 34.0
+FP32_LANES_PER_SM = 128
+
+
+def workload(k):
+    if k == 1:
+        d, q = ws.config1()
+        return [d], [q], "one planar [0,1]^2 domain: 64-cubic CCW star (C0) + two 16-cubic CW holes; 100k uniform + 10k near (1e-6) queries"
+    if k == 2:
+        d, q = ws.config2()
+        return d, q, ("64 planar domains, 4-12 loops x 32-512 segments of degree 1-5, every join opened by a "
+                      "1e-4..1e-2 gap, control-point noise 1e-4; 10M uniform + 1M near-curve (1e-7..1e-3) queries")
+    if k == 3:
+        d, q = ws.config3()
+        return d, q, "256 bi-periodic faces (2pi x 2pi), 2-8 loops of 16-256 cubics, 30% non-contractible pairs, 10% open; 20M uniform queries"
+    if k == 4:
+        d, q = ws.config4()
+        return d, q, "10k faces, log-normal segments (median 40) and queries (median 4096, ~2e8 total), 20% periodic"
+    if k == 5:
+        d = [ws.config5_face(f) for f in range(64)]
+        return d, None, "64 planar faces of ~100k cubics (fractal outer loop + 200 holes), 4096x4096 cell-centre grids"
+    raise SystemExit(f"unknown workload {k}")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def oracle_sample(doms, qs, budget_s, threads):
+    """FP64 oracle on a stratified sample of every domain's queries, sized to
+    take about budget_s seconds.  Returns (indices per domain, results, rate)."""
+    import oracle
+    rng = np.random.default_rng(12345)
+    # calibrate on 4 queries per domain
+    t0 = time.perf_counter()
+    for d, q in zip(doms, qs):
+        oracle.query(d, q[:4], threads=threads)
+    per_q = max((time.perf_counter() - t0) / (4 * len(doms)), 1e-7)
+    m = int(np.clip(budget_s * threads / per_q / len(doms), 8, 20000))
+    idx, res = [], []
+    t0 = time.perf_counter()
+    tot = 0
+    for d, q in zip(doms, qs):
+        i = np.sort(rng.choice(len(q), min(m, len(q)), replace=False))
+        w, s, mg = oracle.query(d, q[i], threads=threads, margins=True)
+        idx.append(i)
+        res.append((w, s, mg))
+        tot += len(i)
+    dt = time.perf_counter() - t0
+    return idx, res, tot / dt, tot, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    doms, qs, desc = workload(args.workload)
+    if qs is None:
+        qs = [ws.grid_points(4096, 4096)[::4099] for _ in doms]
+    threads = os.cpu_count() or 1
+    oracle.build()
+    times, nq = [], 0
+    for _ in range(args.warmup + args.steps):
+        _, _, rate, n, dt = oracle_sample(doms, qs, budget_s=min(10.0, 120.0 / max(1, args.steps + args.warmup)),
+                                          threads=threads)
+        times.append((n, dt))
+    tn = sum(n for n, _ in times[args.warmup:])
+    tt = sum(dt for _, dt in times[args.warmup:])
+    value = tn / tt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": desc},
+           "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": threads,
+                            "sample": f"{tn // max(1, args.steps)} stratified queries per step over all domains"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--qpt", type=int, default=0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2510_25159_gb300 as wn
+    from paper_2510_25159_gb300 import build as wb
+
+    wb.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.qpt:
+        wn.set_tuning(qpt=args.qpt)
+
+    doms, qs, desc = workload(args.workload)
+    handles = [wn.Domain.from_dict(d) for d in doms]
+    dev = torch.device("cuda", local)
+    grid = qs is None
+    if not grid:
+        pts_h = np.ascontiguousarray(np.concatenate(qs, axis=0))
+        off = np.concatenate([[0], np.cumsum([len(x) for x in qs])]).astype(np.int64)
+        n_q = int(off[-1])
+        pts = torch.from_numpy(pts_h).to(dev)
+        out_w = torch.empty(n_q, dtype=torch.float64, device=dev)
+        out_s = torch.empty(n_q, dtype=torch.uint8, device=dev)
+        seg = np.array([ws.n_segments(d) for d in doms], dtype=np.float64)
+        pairs = float(np.sum(seg * np.diff(off)))
+    else:
+        n_q = 64 * 4096 * 4096
+        pairs = float(sum(ws.n_segments(d) for d in doms)) * 4096 * 4096
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(prec=wn.MIXED):
+        if grid:
+            for h in handles:
+                wn.query_grid_bitmask(h, 4096, 4096, precision=prec)
+        else:
+            wn.query_batched(handles, pts, off, precision=prec, out_winding=out_w, out_inside=out_s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    wn.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    ktimes, ncalls = wn.kernel_times()
+    wn.set_profiling(False)
+    st = wn.stats()
+    clocks = clk.summary()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n_q * world / (ms / 1e3)
+    launches_per_step = 5 * (64 if grid else 1)
+
+    # roofline of the dominant kernel (the sweep): algorithmic FP32 flops / its event time
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    f_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * f_max * 1e6 / 1e12
+    sweep_ms = ktimes["sweep"] / max(1, ncalls)
+    achieved = pairs * FLOPS_PER_PAIR / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if os.path.exists(tf):
+        try:
+            t = json.load(open(tf))
+            if t.get("workload") == args.workload and t.get("kernel_source_sha") == _kernel_sha():
+                traffic = t.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roof = {"bound": "alu", "kernel": "k_sweep", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
+            "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {f_max:.0f} MHz (sm_max_mhz)",
+            "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs,
+            "kernel_ms": {k: v / max(1, ncalls) for k, v in ktimes.items()}}
+
+    extra = {}
+    # plain FP64 path on the same GPU (one launch per domain)
+    if not args.no_plain and not grid:
+        step(wn.PLAIN_FP64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        step(wn.PLAIN_FP64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        extra["plain_fp64"] = {"value": n_q * world / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                               "launches_per_step": len(handles)}
+        extra["speedup_vs_plain"] = pms / ms
+        step()
+        torch.cuda.synchronize()
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not grid:
+        hp = torch.from_numpy(pts_h).pin_memory()
+        hw = torch.empty(n_q, dtype=torch.float64).pin_memory()
+        hs = torch.empty(n_q, dtype=torch.uint8).pin_memory()
+        hpn, hwn, hsn = hp.numpy(), hw.numpy(), hs.numpy()
+        wn.query_batched(handles, hpn, off, out_winding=hwn, out_inside=hsn)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            wn.query_batched(handles, hpn, off, out_winding=hwn, out_inside=hsn)
+        torch.cuda.synchronize()
+        et = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": n_q * world / et, "unit": UNIT, "ms_per_step": et * 1e3,
+               "h2d_bytes_per_step": int(pts_h.nbytes), "d2h_bytes_per_step": int(n_q * 9)}
+
+    # oracle on the host cores: bounded sample, also a parity check of the timed results
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not grid:
+        import oracle
+        oracle.build()
+        threads = os.cpu_count() or 1
+        idx, res, rate, tot, dt = oracle_sample(doms, qs, args.cpu_budget, threads)
+        w_all = out_w.cpu().numpy()
+        s_all = out_s.cpu().numpy()
+        mism, ties, maxerr = 0, 0, 0.0
+        for d, i, (ow, osd, om), a0 in zip(doms, idx, res, off[:-1]):
+            w = w_all[a0 + i]
+            s = s_all[a0 + i]
+            cp = d["cps"]
+            S = max(1.0, d["period_u"], d["period_v"], float(np.ptp(cp[:, 0])), float(np.ptp(cp[:, 1])))
+            tie = om < 1e-12 * S
+            mism += int(((s != osd) & ~tie).sum())
+            ties += int(((s != osd) & tie).sum())
+            ok = (s != 2) & (osd != 2)
+            if ok.any():
+                maxerr = max(maxerr, float(np.max(np.abs(w[ok] - ow[ok]))))
+        cpu = {"kind": "oracle", "value": rate, "unit": UNIT, "cores": threads,
+               "sample": f"{tot} stratified queries ({tot // len(doms)} per domain) of the same workload, {dt:.1f} s"}
+        parity = {"oracle_mismatches": mism, "ties": ties, "max_abs_domega": maxerr, "checked": tot}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": desc, "domains": len(doms), "queries": n_q,
+                           "segments": int(sum(ws.n_segments(d) for d in doms)),
+                           "l2": "inputs (16 B/query) larger than L2; 256 MB L2 flush between steps outside the events",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+                "clocks": clocks, "parity": parity,
+                "escalation": {"near_pairs": st["near_pairs"], "fp64_pairs": st["fp64_pairs"],
+                               "fp64_queries": st["fp64_queries"], "overflow": st["overflow"]}}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    for h in handles:
+        h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _kernel_sha():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("wn_kernels.cu", "wn_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2510_25159_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    main()

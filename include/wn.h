@@ -1,0 +1,208 @@
+/*
+ * wn.h -- C ABI of the GB300 (sm_103a) containment-query library.
+ *
+ * The library classifies query points (u,v) of a trimmed surface's
+ * parameter domain against the surface's Bezier trimming loops by the
+ * generalized winding number, following Bao, Shen & Wang, "Fast and Robust
+ * Point Containment Queries on Trimmed Surface" (arXiv 2510.25159):
+ *
+ *   - the problem statement and the inside/outside rule: Sec. 4.1;
+ *   - the winding number and its additivity / homotopy invariance: Sec. 3.2,
+ *     Eq. 1-3 (chord winding = signed angle / 2 pi);
+ *   - the recursion: Algorithm 1, with the ellipse bound of Lemma 1 (Eq. 4),
+ *     its sub-segment form (Eq. 5) and B = max_i n |P_i - P_{i-1}| (App. A.1);
+ *   - periodic domains: lifting to the universal covering space (Sec. 4.3),
+ *     periodically extended curves with the line term (Sec. 4.4, Eq. 6-9),
+ *     uni-/bi-periodic domains, loop classes and families (Sec. 4.5,
+ *     Prop. 1-2, Eq. 10-12) and pairing (App. C, Alg. 3-10).
+ *
+ * All functions are plain C: pointers, sizes and a CUDA stream.  Nothing here
+ * names a C++ or PyTorch type.  Every call returns a wn_status; on failure a
+ * thread-local message is available from wn_last_error().
+ */
+#ifndef WN_H
+#define WN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (cudaStream_t); NULL means the legacy default stream. */
+typedef struct CUstream_st *wn_stream;
+
+/* Opaque domain: owns device copies of the lifted loops and the query
+ * tables built from them, plus host bookkeeping.  Create with
+ * wn_create_domain, free with wn_destroy_domain. */
+typedef struct wn_domain wn_domain;
+
+typedef enum {
+    WN_OK = 0,
+    WN_ERR_ARG = 1,       /* bad argument: size, degree, NaN, negative period, pointer */
+    WN_ERR_TOPOLOGY = 2,  /* periodic loops violate Prop. 1 (unpaired or mixed homology,
+                             non-coprime (p,q), |homology| > 1 on a cylinder) or the
+                             pairing of App. C finds no partner */
+    WN_ERR_CUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
+    WN_ERR_OOM = 4,       /* device or host allocation failed */
+    WN_ERR_LIMIT = 5,     /* a size exceeds a documented maximum */
+    WN_ERR_DEVICE = 6     /* a kernel reported an error through the device status word
+                             (a bounded wait ran out); results of that call are invalid */
+} wn_status;
+
+/* out_inside values (Sec. 4.1: classify by omega; on-boundary per Alg. 1). */
+enum { WN_OUTSIDE = 0, WN_INSIDE = 1, WN_BOUNDARY = 2 };
+
+/* precision argument of the query calls */
+enum {
+    WN_PREC_PLAIN_FP64 = 0, /* Algorithm 1 in FP64 per (query, segment), chord angles
+                               summed with atan2: the plain port of the paper's method */
+    WN_PREC_MIXED = 1       /* FP32 sweep with error bands and exact crossing counts,
+                               FP32 recursion on near pairs, FP64 for every decision
+                               whose FP32 error band cannot settle it */
+};
+
+#define WN_MAX_DEGREE 7           /* highest Bezier degree accepted */
+#define WN_MAX_QUERIES_PER_CALL 2147483647LL
+
+/*
+ * Build a domain (Sec. 4.1 input: the trimming loops of one face).
+ *
+ *   loop_offsets    host int32[n_loops+1]; loop l owns segments
+ *                   [loop_offsets[l], loop_offsets[l+1]); loop_offsets[0] == 0.
+ *   n_loops         >= 0.
+ *   degrees         host int32[n_segs], each in 1..WN_MAX_DEGREE
+ *                   (n_segs = loop_offsets[n_loops]).
+ *   control_points  host double[2 * sum(degrees[s] + 1)], x,y interleaved,
+ *                   segment-major; a segment's first and last points are its
+ *                   endpoints gamma(0), gamma(1).  Segments of a loop are
+ *                   consecutive end to start; gaps are allowed (open loops).
+ *   period_u/_v     0 = not periodic on that axis, > 0 = period.  Periodic
+ *                   loops may be stored per-segment wrapped; they are lifted
+ *                   (each segment translated by the lattice vector that brings
+ *                   its start nearest to the previous segment's end).
+ *   epsilon         boundary tolerance of Alg. 1 (strict d < eps);
+ *                   <= 0 selects 1e-9 * max(period_u, period_v, extent of the
+ *                   control-point box).
+ *   out             receives the domain.
+ *
+ * The caller keeps ownership of every input array; the domain copies what it
+ * needs.  Needs a current CUDA device; performs synchronous uploads and, for
+ * bi-periodic domains, launches the pairing kernel (App. C, Alg. 8-10) and
+ * waits for it.  Errors: WN_ERR_ARG, WN_ERR_TOPOLOGY, WN_ERR_OOM, WN_ERR_CUDA.
+ */
+wn_status wn_create_domain(const int32_t *loop_offsets, int32_t n_loops,
+                           const int32_t *degrees, const double *control_points,
+                           double period_u, double period_v, double epsilon,
+                           wn_domain **out);
+
+/* Free a domain (NULL is ignored).  Waits for the device to finish. */
+void wn_destroy_domain(wn_domain *domain);
+
+/*
+ * Classify n points against one domain (Sec. 4.1; Alg. 1 per segment;
+ * Sec. 4.3-4.5 for periodic domains).
+ *
+ *   points       double[2n], x,y interleaved: device memory, or host memory
+ *                (pinned or pageable), in which case the library stages the
+ *                copies on `stream`.  Periodic coordinates may lie outside
+ *                [0, period); they are reduced modulo the period.
+ *   n            0 <= n <= WN_MAX_QUERIES_PER_CALL.
+ *   out_winding  double[n] (device or host, may be NULL): omega, NaN for
+ *                WN_BOUNDARY.
+ *   out_inside   uint8[n]  (device or host, may be NULL): WN_OUTSIDE /
+ *                WN_INSIDE (omega >= 1/2) / WN_BOUNDARY.
+ *   precision    WN_PREC_PLAIN_FP64 or WN_PREC_MIXED.
+ *   stream       work is ordered on this stream.  With device buffers the
+ *                call is asynchronous; with any host buffer it returns after
+ *                the results are in host memory.
+ *
+ * Scratch memory (per-query accumulators and the near-pair queues) is owned
+ * by the library and grown on demand; the first call of a given size
+ * allocates.  Errors: WN_ERR_ARG, WN_ERR_OOM, WN_ERR_CUDA.
+ */
+wn_status wn_query(const wn_domain *domain, const double *points, int64_t n,
+                   double *out_winding, uint8_t *out_inside, int precision,
+                   wn_stream stream);
+
+/*
+ * Classify the points of many domains in one persistent launch: domain d
+ * owns points [point_offsets[d], point_offsets[d+1]).
+ *
+ *   domains        host array of n_domains domain pointers (repeats allowed).
+ *   point_offsets  HOST int64[n_domains+1], non-decreasing, point_offsets[0] == 0.
+ *   points, out_winding, out_inside: as in wn_query, concatenated.
+ *
+ * WN_PREC_MIXED runs one persistent sweep over a global (domain, query-tile)
+ * work list ordered by decreasing cost, then the near-pair, FP64 and
+ * finalize kernels; with WN_PREC_PLAIN_FP64 one plain kernel is launched per
+ * domain.  The tile shape and launch sizes come from wn_set_tuning or the
+ * defaults.  Errors as wn_query.
+ */
+wn_status wn_query_batched(const wn_domain *const *domains, int32_t n_domains,
+                           const int64_t *point_offsets, const double *points,
+                           double *out_winding, uint8_t *out_inside, int precision,
+                           wn_stream stream);
+
+/*
+ * Classify the cell centres ((i + 1/2)/nu, (j + 1/2)/nv), i < nu, j < nv, of a
+ * uniform grid over [0,1]^2 scaled by the periods (or the unit square for a
+ * planar domain) -- the tessellation use of Sec. 5.4.3.  Points are made on
+ * the device.  Bit (j*nu + i) of out_bits (device uint32[(nu*nv + 31)/32],
+ * bit k of word k/32 at position k%32) is 1 for WN_INSIDE or WN_BOUNDARY.
+ * out_boundary (device int64[1], may be NULL) receives the number of
+ * WN_BOUNDARY cells.  1 <= nu, nv <= 65536.
+ */
+wn_status wn_query_grid_bitmask(const wn_domain *domain, int32_t nu, int32_t nv,
+                                uint32_t *out_bits, int64_t *out_boundary, int precision,
+                                wn_stream stream);
+
+/*
+ * Tuning knobs of the mixed path (0 keeps the current value):
+ *   tile_queries_per_thread  1, 2 or 4 queries per sweep thread
+ *   sweep_ctas_per_sm        persistent sweep CTAs per SM (1..8)
+ *   near_ctas_per_sm         near-pair kernel CTAs per SM (1..16)
+ *   use_graph                1 = capture each distinct batched call in a CUDA
+ *                            graph and replay it; 0 = plain launches
+ */
+wn_status wn_set_tuning(int32_t tile_queries_per_thread, int32_t sweep_ctas_per_sm,
+                        int32_t near_ctas_per_sm, int32_t use_graph);
+
+/* Counters of the last mixed call on this thread's device, read after the
+ * stream is synchronised: queries, near pairs, pairs escalated to FP64,
+ * queries recomputed in FP64, near-queue overflows, device error word. */
+typedef struct {
+    int64_t queries;
+    int64_t near_pairs;
+    int64_t fp64_pairs;
+    int64_t fp64_queries;
+    int64_t overflow;
+    int64_t device_error;
+} wn_stats;
+
+wn_status wn_get_stats(wn_stats *out);
+
+/*
+ * Per-kernel device time of the mixed path, for measurement.  With on != 0
+ * every following WN_PREC_MIXED call records CUDA events around each of its
+ * kernels on the call's own stream (so the times are those of the stream the
+ * kernels run on); on == 0 stops recording and drops what was recorded.
+ * wn_kernel_times synchronises the device, writes the summed milliseconds of
+ * the five kernels [sweep, near pairs FP32, pairs FP64, finalize, queries
+ * FP64] into ms5 (host double[5]) and the number of recorded calls into
+ * *n_calls, then clears the record.
+ */
+wn_status wn_set_profiling(int32_t on);
+wn_status wn_kernel_times(double *ms5, int64_t *n_calls);
+
+/* Thread-local description of the last failure ("" when none). */
+const char *wn_last_error(void);
+
+/* Library version string. */
+const char *wn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WN_H */

@@ -1,0 +1,206 @@
+"""Containment queries on trimmed surfaces for GB300 (sm_103a).
+
+Thin ctypes binding of the C ABI in ``include/wn.h`` (``_build/libwn.so``):
+argument marshalling only.  Every step of the query runs in the library's
+CUDA kernels; there is no CPU fallback, and importing a function that needs
+the library raises when ``libwn.so`` has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``).
+
+Device buffers are torch CUDA tensors (``data_ptr()``) ordered on the current
+torch stream; host buffers are numpy arrays (the library stages the copies).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OUTSIDE, INSIDE, BOUNDARY = 0, 1, 2
+PLAIN_FP64, MIXED = 0, 1
+MAX_DEGREE = 7
+
+_STATUS = {0: "WN_OK", 1: "WN_ERR_ARG", 2: "WN_ERR_TOPOLOGY", 3: "WN_ERR_CUDA", 4: "WN_ERR_OOM",
+           5: "WN_ERR_LIMIT", 6: "WN_ERR_DEVICE"}
+_lib = None
+
+
+class WnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class WnStats(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
+                ("fp64_pairs", ctypes.c_int64), ("fp64_queries", ctypes.c_int64),
+                ("overflow", ctypes.c_int64), ("device_error", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.wn_create_domain.argtypes = [P, I32, P, P, D, D, D, ctypes.POINTER(ctypes.c_void_p)]
+        L.wn_destroy_domain.argtypes = [P]
+        L.wn_destroy_domain.restype = None
+        L.wn_query.argtypes = [P, P, I64, P, P, ctypes.c_int, P]
+        L.wn_query_batched.argtypes = [P, I32, P, P, P, P, ctypes.c_int, P]
+        L.wn_query_grid_bitmask.argtypes = [P, I32, I32, P, P, ctypes.c_int, P]
+        L.wn_set_tuning.argtypes = [I32, I32, I32, I32]
+        L.wn_get_stats.argtypes = [ctypes.POINTER(WnStats)]
+        L.wn_last_error.restype = ctypes.c_char_p
+        L.wn_version.restype = ctypes.c_char_p
+        L.wn_set_profiling.argtypes = [I32]
+        L.wn_kernel_times.argtypes = [P, P]
+        for f in ("wn_create_domain", "wn_query", "wn_query_batched", "wn_query_grid_bitmask",
+                  "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise WnError(rc, lib().wn_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Domain:
+    """One face's trimming loops (``wn_create_domain``)."""
+
+    def __init__(self, loop_offsets, degrees, control_points, period_u=0.0, period_v=0.0, eps=0.0):
+        lo = np.ascontiguousarray(loop_offsets, dtype=np.int32)
+        dg = np.ascontiguousarray(degrees, dtype=np.int32)
+        cp = np.ascontiguousarray(control_points, dtype=np.float64).reshape(-1)
+        h = ctypes.c_void_p()
+        self._h = None
+        _check(lib().wn_create_domain(_ptr(lo), len(lo) - 1, _ptr(dg), _ptr(cp), float(period_u),
+                                      float(period_v), float(eps), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_dict(cls, d, eps=None):
+        return cls(d["loop_offsets"], d["degrees"], d["cps"], d["period_u"], d["period_v"],
+                   d["eps"] if eps is None else eps)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and _lib is not None:
+            _lib.wn_destroy_domain(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def query(domain, points, precision=MIXED, out_winding=None, out_inside=None, stream=None):
+    """Winding numbers and states of ``points`` ((n,2) float64, torch CUDA or
+    numpy host).  Returns (winding, inside) in the same kind of memory."""
+    n = int(points.shape[0])
+    if out_winding is None or out_inside is None:
+        if isinstance(points, np.ndarray):
+            out_winding = np.empty(n) if out_winding is None else out_winding
+            out_inside = np.empty(n, dtype=np.uint8) if out_inside is None else out_inside
+        else:
+            import torch
+            out_winding = torch.empty(n, dtype=torch.float64, device=points.device) if out_winding is None else out_winding
+            out_inside = torch.empty(n, dtype=torch.uint8, device=points.device) if out_inside is None else out_inside
+    _check(lib().wn_query(domain.handle, _ptr(points), n, _ptr(out_winding), _ptr(out_inside),
+                          int(precision), _stream(stream)))
+    return out_winding, out_inside
+
+
+def query_batched(domains, points, offsets, precision=MIXED, out_winding=None, out_inside=None,
+                  stream=None):
+    """Many domains in one call: domain d owns points[offsets[d]:offsets[d+1]]."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = int(off[-1])
+    arr = (ctypes.c_void_p * len(domains))(*[d.handle.value for d in domains])
+    if out_winding is None or out_inside is None:
+        if isinstance(points, np.ndarray):
+            out_winding = np.empty(n) if out_winding is None else out_winding
+            out_inside = np.empty(n, dtype=np.uint8) if out_inside is None else out_inside
+        else:
+            import torch
+            out_winding = torch.empty(n, dtype=torch.float64, device=points.device) if out_winding is None else out_winding
+            out_inside = torch.empty(n, dtype=torch.uint8, device=points.device) if out_inside is None else out_inside
+    _check(lib().wn_query_batched(ctypes.cast(arr, ctypes.c_void_p), len(domains), _ptr(off),
+                                  _ptr(points), _ptr(out_winding), _ptr(out_inside),
+                                  int(precision), _stream(stream)))
+    return out_winding, out_inside
+
+
+def query_grid_bitmask(domain, nu, nv, precision=MIXED, stream=None):
+    """Inside/boundary bitmask of the nu x nv cell-centre grid (device)."""
+    import torch
+    words = (nu * nv + 31) // 32
+    bits = torch.empty(words, dtype=torch.int32, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _check(lib().wn_query_grid_bitmask(domain.handle, int(nu), int(nv), _ptr(bits), _ptr(nb),
+                                       int(precision), _stream(stream)))
+    return bits, nb
+
+
+def set_tuning(qpt=0, sweep_ctas_per_sm=0, near_ctas_per_sm=0, use_graph=-1):
+    _check(lib().wn_set_tuning(int(qpt), int(sweep_ctas_per_sm), int(near_ctas_per_sm), int(use_graph)))
+
+
+def stats():
+    s = WnStats()
+    _check(lib().wn_get_stats(ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in WnStats._fields_}
+
+
+KERNELS = ("sweep", "near_fp32", "pairs_fp64", "finalize", "queries_fp64")
+
+
+def set_profiling(on=True):
+    _check(lib().wn_set_profiling(1 if on else 0))
+
+
+def kernel_times():
+    """Summed device milliseconds per mixed-path kernel since the last read,
+    and the number of calls they cover."""
+    ms = np.zeros(5)
+    n = np.zeros(1, dtype=np.int64)
+    _check(lib().wn_kernel_times(_ptr(ms), _ptr(n)))
+    return dict(zip(KERNELS, ms.tolist())), int(n[0])
+
+
+def version():
+    return lib().wn_version().decode()

@@ -1,0 +1,423 @@
+// wn_api.cu -- the C ABI of include/wn.h: domain lifetime, scratch memory,
+// the batched work list, host-buffer staging, tuning and counters.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wn.h"
+#include "wn_internal.h"
+
+using namespace wn;
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;
+Tuning g_tun;
+
+struct DevState {
+    bool init = false;
+    int n_sm = 0;
+    Work W;
+    // host-buffer staging
+    double *st_pts = nullptr;
+    double *st_w = nullptr;
+    uint8_t *st_st = nullptr;
+    int64_t cap_st = 0;
+    // batch tables, reused while the batch layout does not change
+    std::vector<const wn_domain *> key_doms;
+    std::vector<int64_t> key_offsets;
+    int key_qpt = 0;
+    int n_units = 0;
+    std::vector<DomDev> h_doms;
+    std::vector<int4> h_units;
+    wn_stats last{};
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+};
+DevState g_dev[64];
+
+wn_status fail(wn_status s, const std::string &m)
+{
+    g_err = m;
+    return s;
+}
+
+wn_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(e == cudaErrorMemoryAllocation ? WN_ERR_OOM : WN_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t grow(T *&p, int64_t &cap, int64_t need)
+{
+    if (need <= cap && p) return cudaSuccess;
+    if (p) {
+        cudaDeviceSynchronize();
+        cudaFree(p);
+        p = nullptr;
+    }
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, (size_t)std::max<int64_t>(need, 1) * sizeof(T));
+    if (e == cudaSuccess) cap = need;
+    return e;
+}
+
+DevState *dev_state(wn_status &st)
+{
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess || d < 0 || d >= 64) {
+        st = cuda_fail(e == cudaSuccess ? cudaErrorInvalidDevice : e, "cudaGetDevice");
+        return nullptr;
+    }
+    DevState &S = g_dev[d];
+    if (!S.init) {
+        e = cudaDeviceGetAttribute(&S.n_sm, cudaDevAttrMultiProcessorCount, d);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaDeviceGetAttribute");
+            return nullptr;
+        }
+        e = cudaMalloc(&S.W.counters, CNT_N * sizeof(unsigned int));
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaMalloc counters");
+            return nullptr;
+        }
+        cudaMemset(S.W.counters, 0, CNT_N * sizeof(unsigned int));
+        S.init = true;
+    }
+    st = WN_OK;
+    return &S;
+}
+
+// Scratch of the mixed path sized for n queries.
+cudaError_t ensure_work(Work &W, int64_t n)
+{
+    cudaError_t e = cudaSuccess;
+    int64_t nq = std::max<int64_t>(n, 1024);
+    if (nq > W.cap_q) {
+        int64_t c0 = W.cap_q, c1 = W.cap_q, c2 = W.cap_q, c3 = W.cap_q;
+        if ((e = grow(W.acc2, c0, nq)) != cudaSuccess) return e;
+        if ((e = grow(W.theta, c1, nq)) != cudaSuccess) return e;
+        if ((e = grow(W.flags, c2, nq)) != cudaSuccess) return e;
+        if ((e = grow(W.esc_q, c3, nq)) != cudaSuccess) return e;
+        W.cap_q = nq;
+    }
+    const int64_t need_near = std::max<int64_t>(1 << 22, 3 * nq);
+    if ((e = grow(W.near_items, W.cap_near, need_near)) != cudaSuccess) return e;
+    const int64_t need_f64 = std::max<int64_t>(1 << 18, nq / 8);
+    if ((e = grow(W.f64_items, W.cap_f64, need_f64)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *wn_last_error(void) { return g_err.c_str(); }
+
+const char *wn_version(void) { return "wn 0.1 (sm_103a)"; }
+
+wn_status wn_create_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
+                           const double *control_points, double period_u, double period_v,
+                           double epsilon, wn_domain **out)
+{
+    if (!out) return fail(WN_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    std::string err;
+    int rc;
+    try {
+        rc = build_domain(loop_offsets, n_loops, degrees, control_points, period_u, period_v,
+                          epsilon, out, err);
+    } catch (const std::bad_alloc &) {
+        return fail(WN_ERR_OOM, "host allocation failed");
+    }
+    if (rc != 0) return fail((wn_status)rc, err);
+    g_err.clear();
+    return WN_OK;
+}
+
+void wn_destroy_domain(wn_domain *d)
+{
+    if (!d) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != d->device) cudaSetDevice(d->device);
+    cudaDeviceSynchronize();
+    for (void *p : d->allocs) cudaFree(p);
+    if (cur != d->device) cudaSetDevice(cur);
+    // batch tables that name this domain must be rebuilt
+    for (DevState &S : g_dev)
+        for (const wn_domain *k : S.key_doms)
+            if (k == d) {
+                S.key_doms.clear();
+                break;
+            }
+    delete d;
+}
+
+wn_status wn_set_tuning(int32_t qpt, int32_t sweep_ctas_per_sm, int32_t near_ctas_per_sm,
+                        int32_t use_graph)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (qpt != 0 && qpt != 1 && qpt != 2 && qpt != 4) return fail(WN_ERR_ARG, "qpt must be 1, 2 or 4");
+    if (sweep_ctas_per_sm < 0 || sweep_ctas_per_sm > 8) return fail(WN_ERR_ARG, "sweep_ctas_per_sm 1..8");
+    if (near_ctas_per_sm < 0 || near_ctas_per_sm > 16) return fail(WN_ERR_ARG, "near_ctas_per_sm 1..16");
+    if (qpt) g_tun.qpt = qpt;
+    if (sweep_ctas_per_sm) g_tun.sweep_ctas_per_sm = sweep_ctas_per_sm;
+    if (near_ctas_per_sm) g_tun.near_ctas_per_sm = near_ctas_per_sm;
+    if (use_graph >= 0) g_tun.use_graph = use_graph;
+    return WN_OK;
+}
+
+static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
+                            const int64_t *offsets, const double *points, double *out_w,
+                            uint8_t *out_st, int precision, cudaStream_t stream, PointSrc grid,
+                            uint32_t *bits, int64_t *nbound)
+{
+    if (n_domains < 0 || !offsets || (n_domains > 0 && !domains))
+        return fail(WN_ERR_ARG, "bad domain list");
+    if (precision != WN_PREC_PLAIN_FP64 && precision != WN_PREC_MIXED)
+        return fail(WN_ERR_ARG, "precision must be WN_PREC_PLAIN_FP64 or WN_PREC_MIXED");
+    if (offsets[0] != 0) return fail(WN_ERR_ARG, "point_offsets[0] must be 0");
+    for (int d = 0; d < n_domains; d++) {
+        if (!domains[d]) return fail(WN_ERR_ARG, "NULL domain");
+        if (offsets[d + 1] < offsets[d]) return fail(WN_ERR_ARG, "point_offsets must be non-decreasing");
+    }
+    const int64_t n = offsets[n_domains];
+    if (n > WN_MAX_QUERIES_PER_CALL) return fail(WN_ERR_LIMIT, "more than 2^31-1 queries in one call");
+    if (n > 0 && !points && !grid.nu) return fail(WN_ERR_ARG, "points is NULL");
+    if (n == 0) return WN_OK;
+
+    std::lock_guard<std::mutex> lk(g_mu);
+    wn_status st;
+    DevState *S = dev_state(st);
+    if (!S) return st;
+    cudaError_t e;
+
+    // host buffers are staged through library-owned device buffers
+    const bool h_pts = points && !is_device_ptr(points);
+    const bool h_w = out_w && !is_device_ptr(out_w);
+    const bool h_st = out_st && !is_device_ptr(out_st);
+    if ((h_pts || h_w || h_st) && (n > S->cap_st || !S->st_pts)) {
+        if (S->st_pts) {
+            cudaDeviceSynchronize();
+            cudaFree(S->st_pts);
+            cudaFree(S->st_w);
+            cudaFree(S->st_st);
+            S->st_pts = nullptr;
+            S->st_w = nullptr;
+            S->st_st = nullptr;
+        }
+        S->cap_st = 0;
+        if ((e = cudaMalloc(&S->st_pts, 2 * n * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&S->st_w, n * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&S->st_st, n)) != cudaSuccess)
+            return cuda_fail(e, "staging buffers");
+        S->cap_st = n;
+    }
+    if (points && !h_pts && (reinterpret_cast<uintptr_t>(points) & 15))
+        return fail(WN_ERR_ARG, "device points must be 16-byte aligned");
+    const double *d_pts = points;
+    if (h_pts) {
+        if ((e = cudaMemcpyAsync(S->st_pts, points, 2 * n * sizeof(double), cudaMemcpyHostToDevice,
+                                 stream)) != cudaSuccess)
+            return cuda_fail(e, "copy points");
+        d_pts = S->st_pts;
+    }
+    OutDst out;
+    out.w = h_w ? S->st_w : out_w;
+    out.st = h_st ? S->st_st : out_st;
+    out.bits = bits;
+    out.nbound = reinterpret_cast<unsigned long long *>(nbound);
+    PointSrc src = grid;
+    src.pts = grid.nu ? nullptr : d_pts;
+
+    if (precision == WN_PREC_PLAIN_FP64) {
+        if (bits && (e = cudaMemsetAsync(bits, 0, (size_t)((n + 31) / 32) * 4, stream)) != cudaSuccess)
+            return cuda_fail(e, "memset bits");
+        if (nbound && (e = cudaMemsetAsync(nbound, 0, 8, stream)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        for (int d = 0; d < n_domains; d++) {
+            const int64_t q0 = offsets[d], cnt = offsets[d + 1] - offsets[d];
+            if ((e = launch_plain(domains[d]->d_self, q0, cnt, src, out, stream)) != cudaSuccess)
+                return cuda_fail(e, "plain kernel");
+        }
+    } else {
+        const int qpt = g_tun.qpt;
+        const int64_t tile = 256LL * qpt;
+        const bool same = S->key_qpt == qpt && S->key_doms.size() == (size_t)n_domains &&
+                          std::equal(S->key_doms.begin(), S->key_doms.end(), domains) &&
+                          S->key_offsets.size() == (size_t)n_domains + 1 &&
+                          std::equal(S->key_offsets.begin(), S->key_offsets.end(), offsets);
+        if (!same) {
+            S->h_doms.resize(n_domains);
+            std::vector<std::pair<double, int4>> u;
+            for (int d = 0; d < n_domains; d++) {
+                S->h_doms[d] = domains[d]->dev;
+                const int64_t cnt = offsets[d + 1] - offsets[d];
+                // sweep cost of one query of this domain: records of every instance
+                const double work = (double)std::max<int64_t>(domains[d]->sweep_records, 1);
+                for (int64_t q0 = 0; q0 < cnt; q0 += tile) {
+                    const int64_t c = std::min(tile, cnt - q0);
+                    u.push_back({work * (double)c, make_int4(d, (int)(offsets[d] + q0), (int)c, 0)});
+                }
+            }
+            std::stable_sort(u.begin(), u.end(),
+                             [](const std::pair<double, int4> &a, const std::pair<double, int4> &b) {
+                                 return a.first > b.first;
+                             });
+            S->h_units.resize(u.size());
+            for (size_t i = 0; i < u.size(); i++) S->h_units[i] = u[i].second;
+            S->n_units = (int)u.size();
+            int64_t cu = S->W.cap_units, cd = S->W.cap_doms;
+            if ((e = grow(S->W.units, cu, (int64_t)u.size())) != cudaSuccess) return cuda_fail(e, "units");
+            if ((e = grow(S->W.doms, cd, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "doms");
+            if ((e = grow(S->W.offsets, S->W.cap_off, (int64_t)n_domains + 1)) != cudaSuccess)
+                return cuda_fail(e, "offsets");
+            S->W.cap_units = cu;
+            S->W.cap_doms = cd;
+            cudaStreamSynchronize(stream);
+            if ((e = cudaMemcpy(S->W.units, S->h_units.data(), u.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cuda_fail(e, "upload units");
+            if ((e = cudaMemcpy(S->W.doms, S->h_doms.data(), n_domains * sizeof(DomDev),
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cuda_fail(e, "upload domains");
+            if ((e = cudaMemcpy(S->W.offsets, offsets, (n_domains + 1) * sizeof(int64_t),
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cuda_fail(e, "upload offsets");
+            S->key_doms.assign(domains, domains + n_domains);
+            S->key_offsets.assign(offsets, offsets + n_domains + 1);
+            S->key_qpt = qpt;
+        }
+        if ((e = ensure_work(S->W, n)) != cudaSuccess) return cuda_fail(e, "scratch");
+        LaunchCfg cfg{S->n_sm, g_tun, S->profiling ? &S->events : nullptr};
+        if ((e = launch_mixed(S->W, S->W.doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src,
+                              out, cfg, stream)) != cudaSuccess)
+            return cuda_fail(e, "mixed kernels");
+        S->last.queries = n;
+    }
+    if (h_w && (e = cudaMemcpyAsync(out_w, S->st_w, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    stream)) != cudaSuccess)
+        return cuda_fail(e, "copy winding");
+    if (h_st && (e = cudaMemcpyAsync(out_st, S->st_st, n, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "copy states");
+    if (h_pts || h_w || h_st) {
+        if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "synchronize");
+    }
+    return WN_OK;
+}
+
+wn_status wn_query_batched(const wn_domain *const *domains, int32_t n_domains,
+                           const int64_t *point_offsets, const double *points, double *out_winding,
+                           uint8_t *out_inside, int precision, wn_stream stream)
+{
+    PointSrc g{};
+    return query_impl(domains, n_domains, point_offsets, points, out_winding, out_inside, precision,
+                      (cudaStream_t)stream, g, nullptr, nullptr);
+}
+
+wn_status wn_query(const wn_domain *domain, const double *points, int64_t n, double *out_winding,
+                   uint8_t *out_inside, int precision, wn_stream stream)
+{
+    if (!domain) return fail(WN_ERR_ARG, "domain is NULL");
+    if (n < 0) return fail(WN_ERR_ARG, "n < 0");
+    int64_t off[2] = {0, n};
+    PointSrc g{};
+    return query_impl(&domain, 1, off, points, out_winding, out_inside, precision,
+                      (cudaStream_t)stream, g, nullptr, nullptr);
+}
+
+wn_status wn_query_grid_bitmask(const wn_domain *domain, int32_t nu, int32_t nv, uint32_t *out_bits,
+                                int64_t *out_boundary, int precision, wn_stream stream)
+{
+    if (!domain || !out_bits) return fail(WN_ERR_ARG, "domain or out_bits is NULL");
+    if (nu < 1 || nv < 1 || nu > 65536 || nv > 65536) return fail(WN_ERR_LIMIT, "grid size outside 1..65536");
+    const int64_t n = (int64_t)nu * nv;
+    if (n > WN_MAX_QUERIES_PER_CALL) return fail(WN_ERR_LIMIT, "grid larger than 2^31-1 cells");
+    if (!is_device_ptr(out_bits) || (out_boundary && !is_device_ptr(out_boundary)))
+        return fail(WN_ERR_ARG, "grid outputs must be device memory");
+    int64_t off[2] = {0, n};
+    PointSrc g{};
+    g.pts = nullptr;
+    g.nu = nu;
+    g.nv = nv;
+    g.su = domain->dev.Pu > 0 ? domain->dev.Pu : 1.0;
+    g.sv = domain->dev.Pv > 0 ? domain->dev.Pv : 1.0;
+    return query_impl(&domain, 1, off, nullptr, nullptr, nullptr, precision, (cudaStream_t)stream, g,
+                      out_bits, out_boundary);
+}
+
+wn_status wn_set_profiling(int32_t on)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    wn_status st;
+    DevState *S = dev_state(st);
+    if (!S) return st;
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : S->events) cudaEventDestroy(e);
+    S->events.clear();
+    S->profiling = on != 0;
+    return WN_OK;
+}
+
+wn_status wn_kernel_times(double *ms5, int64_t *n_calls)
+{
+    if (!ms5) return fail(WN_ERR_ARG, "ms5 is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    wn_status st;
+    DevState *S = dev_state(st);
+    if (!S) return st;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+    for (int k = 0; k < 5; k++) ms5[k] = 0.0;
+    const size_t calls = S->events.size() / 6;
+    for (size_t c = 0; c < calls; c++)
+        for (int k = 0; k < 5; k++) {
+            float ms = 0.f;
+            if ((e = cudaEventElapsedTime(&ms, S->events[6 * c + k], S->events[6 * c + k + 1])) != cudaSuccess)
+                return cuda_fail(e, "cudaEventElapsedTime");
+            ms5[k] += ms;
+        }
+    if (n_calls) *n_calls = (int64_t)calls;
+    for (cudaEvent_t ev : S->events) cudaEventDestroy(ev);
+    S->events.clear();
+    return WN_OK;
+}
+
+wn_status wn_get_stats(wn_stats *out)
+{
+    if (!out) return fail(WN_ERR_ARG, "out is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    wn_status st;
+    DevState *S = dev_state(st);
+    if (!S) return st;
+    unsigned int c[CNT_N];
+    cudaError_t e = cudaMemcpy(c, S->W.counters, sizeof c, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read counters");
+    out->queries = S->last.queries;
+    out->near_pairs = c[CNT_NEAR];
+    out->fp64_pairs = c[CNT_F64];
+    out->fp64_queries = c[CNT_ESC];
+    out->overflow = (c[CNT_NEAR] > (unsigned long long)S->W.cap_near) ? (int64_t)(c[CNT_NEAR] - S->W.cap_near) : 0;
+    out->device_error = c[CNT_ERR];
+    return WN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+// wn_dev.cuh -- device data layout and arithmetic primitives of the
+// containment-query library (internal; not part of the C ABI).
+//
+// Terminology follows Bao, Shen & Wang, "Fast and Robust Point Containment
+// Queries on Trimmed Surface":
+//   segment  a Bezier curve gamma with control points P_0..P_n (Sec. 4.2)
+//   B        the hodograph bound max_i n|P_i - P_{i-1}| (Lemma 1, App. A.1)
+//   loop     consecutive segments; lifted to the covering space (Sec. 4.3)
+//   instance one lattice copy of a loop that a query may see: the loop itself
+//            (planar), a contractible copy (Alg. 4-5 reading), one copy of a
+//            periodically extended curve (Eq. 9), or a line term (Sec. 4.4)
+//
+// Every copy is a lattice translation T = (I Pu, J Pv) applied to the query
+// (p' = p - T, the translation identity of App. C.1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace wn {
+
+constexpr int kMaxDeg = 7;
+constexpr int kNcp = kMaxDeg + 1;
+constexpr int kDepthCap64 = 64;   // FP64 recursion cap: reported as BOUNDARY
+constexpr int kDepthCap32 = 22;   // FP32 recursion cap: the pair goes to FP64
+
+enum : int { DK_PLANAR = 0, DK_UNI_U = 1, DK_UNI_V = 2, DK_BI = 3 };
+enum : int { IT_ALL = 0, IT_BOX = 1, IT_PE = 2, IT_LINE = 3 };
+enum : uint32_t { QF_BOUNDARY = 1u, QF_ESCALATE = 2u };
+enum : uint32_t { RF_CHORD = 1u, RF_GAP = 2u };
+
+// One lifted loop (FP64).
+struct LoopDev {
+    int s0, s1;                 // segments [s0, s1)
+    int r0, r1;                 // FP32 records [r0, r1)
+    int hp, hq;                 // homology
+    int cls, pad;               // 0 plain, 1 contractible, 2 extended
+    double vx, vy;              // lattice vector (hp Pu, hq Pv)
+    double g0x, g0y;            // gamma(0)
+    double g0vx, g0vy;          // gamma(0) + v
+    double smin, smax, vv;      // slab of the curve along v, v.v
+    double box[4];              // xmin xmax ymin ymax of control points
+    double nlo, nhi;            // extent along the family normal (bi-periodic)
+};
+
+// One instance (FP64 predicate data).
+struct InstDev {
+    int type;                   // IT_*
+    int loop;
+    int pair;                   // bi-periodic pair for the family window, -1 none
+    int axes;                   // IT_BOX: bit0 window x, bit1 window y
+    int r0, r1;                 // FP32 records swept for this instance
+    double Tx, Ty;              // query shift: p' = p - (Tx, Ty)
+    double Fx, Fy;              // family shift for the slab / line: x_f = p - (Fx, Fy)
+    long long I, J;             // lattice units of (Fx, Fy)
+    long long c;                // family index
+    long long k;                // copy index along v
+};
+
+struct PairDev {
+    double plo, phi;            // hull of the n-extents of alpha and shifted beta
+};
+
+// Everything a kernel needs about one domain (copied per batch entry).
+struct DomDev {
+    int kind, n_loops, n_segs, n_inst, n_rec, n_pairs;
+    int total_cp, pad0;
+    double Pu, Pv, eps;
+    double ox, oy;              // origin of the FP32 coordinates
+    double nx, ny, PP;          // family normal and Pu*Pv (bi-periodic)
+    float M;                    // max |P - o|_inf over lifted control points
+    float Racc2;                // squared radius under which gap angles use FP64 deltas
+    float Mq;                   // queries with |p' - o|_inf > Mq go to FP64
+    float pad1;
+    const int *seg_deg;         // [n_segs]
+    const int *seg_cp;          // [n_segs] first control point (in points)
+    const double *cp;           // [2 * total_cp] lifted control points
+    const double *seg_B;        // [n_segs]
+    const LoopDev *loops;       // [n_loops]
+    const InstDev *inst;        // [n_inst]
+    const PairDev *pairs;       // [n_pairs]
+    const float4 *rec;          // [3 * n_rec]
+    const int *rec_seg;         // [n_rec] segment, -1 for a closing chord
+    const double2 *rec_a64;     // [n_rec] exact chord start
+    const double2 *rec_b64;     // [n_rec] exact chord end
+    const double2 *rec_n64;     // [n_rec] exact next vertex
+};
+
+// Near / FP64 work item.
+struct Item {
+    uint32_t q;                 // global query index
+    uint32_t dom;               // batch entry
+    uint32_t inst;
+    uint32_t rec;
+};
+
+// ---------------------------------------------------------------- exact FP64
+// Predicates that decide which copies a query sees are evaluated with
+// explicitly rounded operations (no FMA contraction), in the order the
+// definitions state them.
+__host__ __device__ __forceinline__ double xmul(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ double xadd(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ double xsub(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+__host__ __device__ __forceinline__ double xdiv(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __ddiv_rn(a, b);
+#else
+    return a / b;
+#endif
+}
+
+// Reduce a coordinate into [0, P) (identity when P <= 0).
+__host__ __device__ __forceinline__ double reduce_period(double x, double P)
+{
+    if (!(P > 0)) return x;
+    double r = fmod(x, P);
+    if (r < 0) r = xadd(r, P);
+    if (r >= P) r = 0.0;
+    return r;
+}
+
+// Does instance `in` see the reduced query (x, y)?  Exactly the windows of
+// the contractible copies, the slab of Eq. 9 and the family window.
+__device__ __forceinline__ bool inst_sees(const DomDev &D, const InstDev &in, const LoopDev &L,
+                                          double x, double y)
+{
+    if (in.type == IT_ALL) return true;
+    if (in.type == IT_BOX) {
+        if (in.axes & 1) {
+            double xs = xsub(x, in.Tx);
+            if (!(xs >= L.box[0] && xs <= L.box[1])) return false;
+        }
+        if (in.axes & 2) {
+            double ys = xsub(y, in.Ty);
+            if (!(ys >= L.box[2] && ys <= L.box[3])) return false;
+        }
+        return true;
+    }
+    if (in.pair >= 0) {
+        const PairDev P = D.pairs[in.pair];
+        double np = xadd(xmul(D.nx, x), xmul(D.ny, y));
+        double clo = ceil(xdiv(xsub(np, P.phi), D.PP));
+        double chi = floor(xdiv(xsub(np, P.plo), D.PP));
+        double c = (double)in.c;
+        if (!(c >= clo && c <= chi)) return false;
+    }
+    if (in.type == IT_LINE) return true;
+    // IT_PE: copy k lies in the slab window of the family base point
+    double xf = (D.Pu > 0) ? xsub(x, in.Fx) : x;
+    double yf = (D.Pv > 0) ? xsub(y, in.Fy) : y;
+    double sp = xdiv(xadd(xmul(xf, L.vx), xmul(yf, L.vy)), L.vv);
+    double klo = ceil(xsub(sp, L.smax)), khi = floor(xsub(sp, L.smin));
+    double k = (double)in.k;
+    return k >= klo && k <= khi;
+}
+
+// Line term of Eq. 9 (+1 on the left of L, -1 on the right, 0 on L) for the
+// family base point of a line instance.
+__device__ __forceinline__ int line_side(const DomDev &D, const InstDev &in, const LoopDev &L,
+                                         double x, double y)
+{
+    double xf = (D.Pu > 0) ? xsub(x, in.Fx) : x;
+    double yf = (D.Pv > 0) ? xsub(y, in.Fy) : y;
+    double cr = xsub(xmul(L.vx, xsub(yf, L.g0y)), xmul(L.vy, xsub(xf, L.g0x)));
+    return cr > 0 ? 1 : (cr < 0 ? -1 : 0);
+}
+
+// ---------------------------------------------------------------- Bezier
+// gamma(t) by repeated linear interpolation of the control points.
+template <typename T>
+__device__ __forceinline__ void bez_eval(const T *cx, const T *cy, int n, T t, T &ox, T &oy)
+{
+    T qx[kNcp], qy[kNcp];
+#pragma unroll
+    for (int i = 0; i < kNcp; i++) {
+        qx[i] = cx[i];
+        qy[i] = cy[i];
+    }
+    T s = T(1) - t;
+#pragma unroll
+    for (int r = 1; r < kNcp; r++) {
+#pragma unroll
+        for (int i = 0; i < kNcp - r; i++) {
+            if (i <= n - r) {
+                qx[i] = s * qx[i] + t * qx[i + 1];
+                qy[i] = s * qy[i] + t * qy[i + 1];
+            }
+        }
+    }
+    ox = qx[0];
+    oy = qy[0];
+}
+
+// ---------------------------------------------------------------- Alg. 1, FP64
+// Far actions of Algorithm 1: the chord of an excluded sub-segment either adds
+// its signed angle (Eq. 3, the plain method) or its signed crossing of the
+// +x ray from p (the exact reformulation used by the mixed path).
+struct FarAngle {
+    double ang = 0.0;
+    __device__ __forceinline__ void chord(double ax, double ay, double bx, double by)
+    {
+        ang += atan2(ax * by - ay * bx, ax * bx + ay * by);
+    }
+};
+
+struct FarCross {
+    int cnt = 0;
+    __device__ __forceinline__ void chord(double ax, double ay, double bx, double by)
+    {
+        bool sa = ay > 0.0, sb = by > 0.0;
+        if (sa != sb) {
+            double d = ax * by - ay * bx;
+            if (!sa && sb && d > 0) cnt++;
+            else if (sa && !sb && d < 0) cnt--;
+        }
+    }
+};
+
+// Algorithm 1 over [0,1] of one segment, query (px,py), in FP64.  Points are
+// handled relative to p after evaluation in absolute coordinates.  Returns
+// true when the query is on the boundary (an evaluated point closer than eps,
+// or the depth cap).
+template <class Far>
+__device__ bool alg1_fp64(const double *P, int n, double B, double px, double py, double eps,
+                          Far &far)
+{
+    double cx[kNcp], cy[kNcp];
+#pragma unroll
+    for (int i = 0; i < kNcp; i++) {
+        cx[i] = (i <= n) ? P[2 * i] : 0.0;
+        cy[i] = (i <= n) ? P[2 * i + 1] : 0.0;
+    }
+    double st_t[kDepthCap64 + 2], st_x[kDepthCap64 + 2], st_y[kDepthCap64 + 2];
+    int st_d[kDepthCap64 + 2];
+    double a = 0.0;
+    double ax = cx[0] - px, ay = cy[0] - py;
+    double ra = sqrt(ax * ax + ay * ay);
+    int sp = 0;
+    {
+        double bx = P[2 * n] - px, by = P[2 * n + 1] - py;
+        st_t[0] = 1.0; st_x[0] = bx; st_y[0] = by; st_d[0] = 0;
+        sp = 1;
+    }
+    while (sp > 0) {
+        double b = st_t[sp - 1], bx = st_x[sp - 1], by = st_y[sp - 1];
+        int d = st_d[sp - 1];
+        double rb = sqrt(bx * bx + by * by);
+        if (ra < eps || rb < eps) return true;
+        if (ra + rb > B * (b - a)) {
+            far.chord(ax, ay, bx, by);
+            a = b; ax = bx; ay = by; ra = rb;
+            sp--;
+            continue;
+        }
+        if (d >= kDepthCap64) return true;
+        double m = 0.5 * (a + b), mx, my;
+        bez_eval<double>(cx, cy, n, m, mx, my);
+        st_d[sp - 1] = d + 1;
+        st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;
+        sp++;
+    }
+    return false;
+}
+
+}  // namespace wn

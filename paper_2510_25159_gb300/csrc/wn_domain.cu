@@ -1,0 +1,554 @@
+// wn_domain.cu -- building a domain: validation, lifting to the covering
+// space, loop classes, pairing, and the instance / record tables the query
+// kernels sweep.
+//
+//   lifting (Sec. 4.3): every segment after the first of a loop is translated
+//     by the lattice vector (I Pu, J Pv), I = round((e.x - s.x) / Pu), that
+//     brings its start s nearest to the previous segment's lifted end e;
+//     homology = round((end - start) / period) per periodic axis.
+//   classes (Prop. 1): planar / contractible / extended; on a torus the
+//     extended loops must be +-(p, q) with gcd(p, q) = 1 and |A| = |B|; on a
+//     cylinder |homology| <= 1.
+//   families (Prop. 2): index c = p j - q i, represented by c (i0, j0) with
+//     p j0 - q i0 = 1 (i0 in [0, |p|) for p != 0; i0 = -q, j0 = 0 for p = 0).
+//   pairing (App. C, Alg. 8-10): for each alpha in input order, the copies
+//     beta + w_c (c within 2 of the shift that brings beta's start within one
+//     family spacing of alpha's) that lie left of alpha (PE(beta mid) > 0),
+//     and among them the one left of all others in beta's orientation.  The
+//     PE values come from a device kernel.
+//   instances: for every lattice copy that some query of the base tile can
+//     see -- contractible copies with the shifted query inside the control
+//     point box (both axes on a torus, the periodic axis on a cylinder),
+//     extended-curve copies k inside the slab of Eq. 9, the line term of every
+//     extended curve (and family) -- one InstDev; queries test the exact
+//     window on the device.
+//   records: per loop, one FP32 record per segment (chord endpoints, the
+//     inflated circle that contains the ellipse of Lemma 1 and the eps discs,
+//     the gap to the next vertex) plus, for an extended curve, the closing
+//     chord gamma(0)+v -> gamma(0) that turns W(gamma) - omega(chord) of
+//     Eq. 9 into a closed polygon.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "wn_internal.h"
+
+namespace wn {
+
+namespace {
+
+struct HostLoop {
+    int s0, s1;
+    int hp = 0, hq = 0;
+    int cls = 0;
+    double v[2] = {0, 0}, g0[2] = {0, 0}, g0v[2] = {0, 0};
+    double smin = 0, smax = 0, vv = 0;
+    double box[4];
+    double nlo = 0, nhi = 0;
+};
+
+struct DevBuf {
+    std::vector<void *> *list;
+    cudaError_t err = cudaSuccess;
+    template <typename T>
+    T *up(const std::vector<T> &v)
+    {
+        if (err != cudaSuccess) return nullptr;
+        size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
+        void *p = nullptr;
+        err = cudaMalloc(&p, bytes);
+        if (err != cudaSuccess) return nullptr;
+        list->push_back(p);
+        if (!v.empty()) err = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+        return static_cast<T *>(p);
+    }
+};
+
+long long lround_ll(double x) { return (long long)std::llround(x); }
+
+}  // namespace
+
+int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
+                 const double *cps, double Pu, double Pv, double eps, wn_domain **out,
+                 std::string &err)
+{
+    *out = nullptr;
+    if (n_loops < 0 || !loop_offsets || (n_loops > 0 && (!degrees || !cps))) {
+        err = "null array or negative loop count";
+        return 1;
+    }
+    if (!(Pu >= 0) || !(Pv >= 0) || !std::isfinite(Pu) || !std::isfinite(Pv) || std::isnan(eps)) {
+        err = "periods must be finite and >= 0, epsilon not NaN";
+        return 1;
+    }
+    if (loop_offsets[0] != 0) {
+        err = "loop_offsets[0] must be 0";
+        return 1;
+    }
+    for (int l = 0; l < n_loops; l++)
+        if (loop_offsets[l + 1] < loop_offsets[l]) {
+            err = "loop_offsets must be non-decreasing";
+            return 1;
+        }
+    const int ns = loop_offsets[n_loops];
+    std::vector<int> seg_cp(ns), seg_deg(ns);
+    long long ncp = 0;
+    for (int s = 0; s < ns; s++) {
+        if (degrees[s] < 1 || degrees[s] > kMaxDeg) {
+            err = "segment degree outside 1.." + std::to_string(kMaxDeg);
+            return 1;
+        }
+        seg_deg[s] = degrees[s];
+        seg_cp[s] = (int)ncp;
+        ncp += degrees[s] + 1;
+        if (ncp > (1LL << 30)) {
+            err = "too many control points";
+            return 5;
+        }
+    }
+    std::vector<double> P(cps, cps + 2 * ncp);
+    for (long long i = 0; i < 2 * ncp; i++)
+        if (!std::isfinite(P[i])) {
+            err = "control points must be finite";
+            return 1;
+        }
+    const int kind = (Pu > 0 && Pv > 0) ? DK_BI : (Pu > 0) ? DK_UNI_U : (Pv > 0) ? DK_UNI_V : DK_PLANAR;
+    if (!(eps > 0)) {
+        double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+        for (long long i = 0; i < ncp; i++) {
+            x0 = std::fmin(x0, P[2 * i]); x1 = std::fmax(x1, P[2 * i]);
+            y0 = std::fmin(y0, P[2 * i + 1]); y1 = std::fmax(y1, P[2 * i + 1]);
+        }
+        double S = std::fmax(Pu, Pv);
+        if (ncp) S = std::fmax(S, std::fmax(x1 - x0, y1 - y0));
+        eps = 1e-9 * S;
+    }
+
+    // ---- lifting and per-loop data
+    std::vector<HostLoop> loops(n_loops);
+    std::vector<double> segB(ns);
+    for (int l = 0; l < n_loops; l++) {
+        HostLoop &L = loops[l];
+        L.s0 = loop_offsets[l];
+        L.s1 = loop_offsets[l + 1];
+        for (int s = L.s0 + 1; s < L.s1; s++) {
+            const double *pe = &P[2 * (seg_cp[s - 1] + seg_deg[s - 1])];
+            double *ps = &P[2 * seg_cp[s]];
+            long long I = (Pu > 0) ? lround_ll((pe[0] - ps[0]) / Pu) : 0;
+            long long J = (Pv > 0) ? lround_ll((pe[1] - ps[1]) / Pv) : 0;
+            for (int i = 0; i <= seg_deg[s]; i++) {
+                if (I) ps[2 * i] = ps[2 * i] + (double)I * Pu;
+                if (J) ps[2 * i + 1] = ps[2 * i + 1] + (double)J * Pv;
+            }
+        }
+        if (L.s1 > L.s0) {
+            const double *f = &P[2 * seg_cp[L.s0]];
+            const double *e = &P[2 * (seg_cp[L.s1 - 1] + seg_deg[L.s1 - 1])];
+            if (Pu > 0) L.hp = (int)lround_ll((e[0] - f[0]) / Pu);
+            if (Pv > 0) L.hq = (int)lround_ll((e[1] - f[1]) / Pv);
+        }
+        L.box[0] = L.box[2] = INFINITY;
+        L.box[1] = L.box[3] = -INFINITY;
+        for (int s = L.s0; s < L.s1; s++) {
+            const double *q = &P[2 * seg_cp[s]];
+            const int n = seg_deg[s];
+            double B = 0.0;
+            for (int i = 1; i <= n; i++) {
+                double dx = q[2 * i] - q[2 * i - 2], dy = q[2 * i + 1] - q[2 * i - 1];
+                double b = (double)n * std::sqrt(dx * dx + dy * dy);
+                if (b > B) B = b;
+            }
+            segB[s] = B;
+            for (int i = 0; i <= n; i++) {
+                L.box[0] = std::fmin(L.box[0], q[2 * i]);
+                L.box[1] = std::fmax(L.box[1], q[2 * i]);
+                L.box[2] = std::fmin(L.box[2], q[2 * i + 1]);
+                L.box[3] = std::fmax(L.box[3], q[2 * i + 1]);
+            }
+        }
+        if (kind == DK_PLANAR) L.cls = 0;
+        else if (L.hp == 0 && L.hq == 0) L.cls = 1;
+        else L.cls = 2;
+        if (L.cls == 2) {
+            if (kind != DK_BI && (std::abs(L.hp) > 1 || std::abs(L.hq) > 1)) {
+                err = "a loop winds more than once around the cylinder (Prop. 1)";
+                return 2;
+            }
+            L.v[0] = (Pu > 0) ? (double)L.hp * Pu : 0.0;
+            L.v[1] = (Pv > 0) ? (double)L.hq * Pv : 0.0;
+            const double *f = &P[2 * seg_cp[L.s0]];
+            L.g0[0] = f[0];
+            L.g0[1] = f[1];
+            L.g0v[0] = L.g0[0] + L.v[0];
+            L.g0v[1] = L.g0[1] + L.v[1];
+            L.vv = L.v[0] * L.v[0] + L.v[1] * L.v[1];
+            L.smin = (L.g0v[0] * L.v[0] + L.g0v[1] * L.v[1]) / L.vv;
+            L.smax = L.smin;
+            for (int s = L.s0; s < L.s1; s++) {
+                const double *q = &P[2 * seg_cp[s]];
+                for (int i = 0; i <= seg_deg[s]; i++) {
+                    double sv = (q[2 * i] * L.v[0] + q[2 * i + 1] * L.v[1]) / L.vv;
+                    L.smin = std::fmin(L.smin, sv);
+                    L.smax = std::fmax(L.smax, sv);
+                }
+            }
+        }
+    }
+
+    // ---- bi-periodic classes and family generator
+    int hp = 0, hq = 0;
+    long long i0 = 0, j0 = 0;
+    double nx = 0, ny = 0, PP = Pu * Pv;
+    std::vector<int> A_idx, B_idx;
+    if (kind == DK_BI) {
+        int first = -1;
+        for (int l = 0; l < n_loops; l++)
+            if (loops[l].cls == 2) { first = l; break; }
+        if (first >= 0) {
+            hp = loops[first].hp;
+            hq = loops[first].hq;
+            long long a = std::llabs(hp), b = std::llabs(hq);
+            while (b) { long long t = a % b; a = b; b = t; }
+            if (a != 1) {
+                err = "homology coefficients are not coprime (Prop. 1)";
+                return 2;
+            }
+            for (int l = 0; l < n_loops; l++) {
+                if (loops[l].cls != 2) continue;
+                if (loops[l].hp == hp && loops[l].hq == hq) A_idx.push_back(l);
+                else if (loops[l].hp == -hp && loops[l].hq == -hq) B_idx.push_back(l);
+                else {
+                    err = "non-contractible loops with different homology classes (Prop. 1)";
+                    return 2;
+                }
+            }
+            if (A_idx.size() != B_idx.size()) {
+                err = "unequal numbers of (p,q) and -(p,q) loops (Prop. 1)";
+                return 2;
+            }
+            if (hp == 0) { i0 = -hq; j0 = 0; }
+            else {
+                long long ap = std::llabs(hp);
+                i0 = -1;
+                for (long long i = 0; i < ap; i++)
+                    if ((1 + (long long)hq * i) % hp == 0) { i0 = i; break; }
+                j0 = (1 + (long long)hq * i0) / hp;
+            }
+            nx = -(double)hq * Pv;
+            ny = (double)hp * Pu;
+            for (int l : A_idx) {
+                HostLoop &L = loops[l];
+                L.nlo = INFINITY; L.nhi = -INFINITY;
+                for (int s = L.s0; s < L.s1; s++) {
+                    const double *q = &P[2 * seg_cp[s]];
+                    for (int i = 0; i <= seg_deg[s]; i++) {
+                        double nv = nx * q[2 * i] + ny * q[2 * i + 1];
+                        L.nlo = std::fmin(L.nlo, nv);
+                        L.nhi = std::fmax(L.nhi, nv);
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- FP32 origin and scale over every vertex the records use
+    double bx0 = INFINITY, bx1 = -INFINITY, by0 = INFINITY, by1 = -INFINITY;
+    for (int l = 0; l < n_loops; l++) {
+        const HostLoop &L = loops[l];
+        if (L.s1 == L.s0) continue;
+        bx0 = std::fmin(bx0, L.box[0]); bx1 = std::fmax(bx1, L.box[1]);
+        by0 = std::fmin(by0, L.box[2]); by1 = std::fmax(by1, L.box[3]);
+        if (L.cls == 2) {
+            bx0 = std::fmin(bx0, L.g0v[0]); bx1 = std::fmax(bx1, L.g0v[0]);
+            by0 = std::fmin(by0, L.g0v[1]); by1 = std::fmax(by1, L.g0v[1]);
+        }
+    }
+    double ox = 0.0, oy = 0.0, M = 1.0;
+    if (bx0 <= bx1) {
+        ox = 0.5 * (bx0 + bx1);
+        oy = 0.5 * (by0 + by1);
+        M = std::fmax(std::fmax(bx1 - ox, ox - bx0), std::fmax(by1 - oy, oy - by0));
+        if (!(M > 0)) M = 1.0;
+        M = M * (1.0 + 1e-6);
+    }
+    const double Mq = 2.0 * M;
+    const double Trec = std::ldexp(M + Mq, -22);
+
+    // ---- records
+    std::vector<float4> rec;
+    std::vector<int> rec_seg;
+    std::vector<double2> ra64, rb64, rn64;
+    std::vector<int> loop_r0(n_loops), loop_r1(n_loops);
+    auto f32 = [](double x) { return (float)x; };
+    auto push_rec = [&](const double *a, const double *b, const double *nxt, int seg, double B, bool chord) {
+        float4 r0, r1, r2;
+        r0.x = f32(a[0] - ox); r0.y = f32(a[1] - oy); r0.z = f32(b[0] - ox); r0.w = f32(b[1] - oy);
+        const double cx = 0.5 * (a[0] + b[0]), cy = 0.5 * (a[1] + b[1]);
+        const double R = (0.5 * B + eps) * (1.0 + std::ldexp(1.0, -20)) + 2.0 * Trec;
+        const double gx = nxt[0] - b[0], gy = nxt[1] - b[1];
+        uint32_t fl = (chord ? RF_CHORD : 0u) | ((gx != 0.0 || gy != 0.0) ? RF_GAP : 0u);
+        r1.x = f32(cx - ox); r1.y = f32(cy - oy); r1.z = f32(R * R * (1.0 + std::ldexp(1.0, -20)));
+        uint32_t flb = fl;
+        std::memcpy(&r1.w, &flb, 4);
+        r2.x = f32(gx); r2.y = f32(gy); r2.z = f32(nxt[0] - ox); r2.w = f32(nxt[1] - oy);
+        rec.push_back(r0); rec.push_back(r1); rec.push_back(r2);
+        rec_seg.push_back(seg);
+        ra64.push_back(make_double2(a[0], a[1]));
+        rb64.push_back(make_double2(b[0], b[1]));
+        rn64.push_back(make_double2(nxt[0], nxt[1]));
+    };
+    for (int l = 0; l < n_loops; l++) {
+        const HostLoop &L = loops[l];
+        loop_r0[l] = (int)rec_seg.size();
+        for (int s = L.s0; s < L.s1; s++) {
+            const double *a = &P[2 * seg_cp[s]];
+            const double *b = &P[2 * (seg_cp[s] + seg_deg[s])];
+            const double *nxt;
+            if (s + 1 < L.s1) nxt = &P[2 * seg_cp[s + 1]];
+            else nxt = (L.cls == 2) ? L.g0v : &P[2 * seg_cp[L.s0]];
+            push_rec(a, b, nxt, s, segB[s], false);
+        }
+        if (L.cls == 2 && L.s1 > L.s0) push_rec(L.g0v, L.g0, L.g0, -1, 0.0, true);
+        loop_r1[l] = (int)rec_seg.size();
+    }
+
+    // ---- device upload of the geometry (pairing needs it)
+    wn_domain *D = new wn_domain();
+    cudaGetDevice(&D->device);
+    DevBuf up{&D->allocs};
+    auto fail = [&](int code, const std::string &msg) {
+        for (void *p : D->allocs) cudaFree(p);
+        delete D;
+        err = msg;
+        return code;
+    };
+    std::vector<LoopDev> hl(n_loops);
+    for (int l = 0; l < n_loops; l++) {
+        const HostLoop &L = loops[l];
+        LoopDev &o = hl[l];
+        std::memset(&o, 0, sizeof o);
+        o.s0 = L.s0; o.s1 = L.s1; o.r0 = loop_r0[l]; o.r1 = loop_r1[l];
+        o.hp = L.hp; o.hq = L.hq; o.cls = L.cls;
+        o.vx = L.v[0]; o.vy = L.v[1]; o.g0x = L.g0[0]; o.g0y = L.g0[1];
+        o.g0vx = L.g0v[0]; o.g0vy = L.g0v[1];
+        o.smin = L.smin; o.smax = L.smax; o.vv = L.vv;
+        for (int i = 0; i < 4; i++) o.box[i] = L.box[i];
+        o.nlo = L.nlo; o.nhi = L.nhi;
+    }
+    DomDev &dv = D->dev;
+    std::memset(&dv, 0, sizeof dv);
+    dv.kind = kind; dv.n_loops = n_loops; dv.n_segs = ns; dv.total_cp = (int)ncp;
+    dv.Pu = Pu; dv.Pv = Pv; dv.eps = eps; dv.ox = ox; dv.oy = oy;
+    dv.nx = nx; dv.ny = ny; dv.PP = PP;
+    dv.M = (float)M;
+    dv.Mq = (float)Mq;
+    dv.Racc2 = (float)((0.04 * M) * (0.04 * M));
+    dv.seg_deg = up.up(seg_deg);
+    dv.seg_cp = up.up(seg_cp);
+    dv.cp = up.up(P);
+    dv.seg_B = up.up(segB);
+    dv.loops = up.up(hl);
+    dv.n_rec = (int)rec_seg.size();
+    dv.rec = up.up(rec);
+    dv.rec_seg = up.up(rec_seg);
+    dv.rec_a64 = up.up(ra64);
+    dv.rec_b64 = up.up(rb64);
+    dv.rec_n64 = up.up(rn64);
+    if (up.err != cudaSuccess) return fail(up.err == cudaErrorMemoryAllocation ? 4 : 3,
+                                           std::string("CUDA: ") + cudaGetErrorString(up.err));
+    {
+        std::vector<DomDev> one(1, dv);
+        D->d_self = up.up(one);
+        if (up.err != cudaSuccess) return fail(3, std::string("CUDA: ") + cudaGetErrorString(up.err));
+    }
+
+    // ---- pairing (bi-periodic)
+    struct Pair { int a, b; long long I, J; double plo, phi; };
+    std::vector<Pair> pairs;
+    if (!A_idx.empty()) {
+        std::vector<char> used(n_loops, 0);
+        auto run_pe = [&](const std::vector<PeReq> &req, std::vector<double> &res) -> cudaError_t {
+            res.assign(req.size(), 0.0);
+            if (req.empty()) return cudaSuccess;
+            PeReq *dreq = nullptr;
+            double *dres = nullptr;
+            cudaError_t e = cudaMalloc(&dreq, req.size() * sizeof(PeReq));
+            if (e == cudaSuccess) e = cudaMalloc(&dres, req.size() * sizeof(double));
+            if (e == cudaSuccess) e = cudaMemcpy(dreq, req.data(), req.size() * sizeof(PeReq), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = launch_pe_eval(D->d_self, dreq, (int)req.size(), dres, 0);
+            if (e == cudaSuccess) e = cudaMemcpy(res.data(), dres, req.size() * sizeof(double), cudaMemcpyDeviceToHost);
+            cudaFree(dreq);
+            cudaFree(dres);
+            return e;
+        };
+        for (int a : A_idx) {
+            const HostLoop &LA = loops[a];
+            const double nA = nx * LA.g0[0] + ny * LA.g0[1];
+            struct Cand { int b; long long I, J; };
+            std::vector<Cand> cand;
+            for (int b : B_idx) {
+                if (used[b]) continue;
+                const HostLoop &LB = loops[b];
+                const double nB = nx * LB.g0[0] + ny * LB.g0[1];
+                const long long c0 = lround_ll((nA - nB) / PP);
+                for (long long c = c0 - 2; c <= c0 + 2; c++) cand.push_back({b, c * i0, c * j0});
+            }
+            std::vector<PeReq> req;
+            for (const Cand &c : cand) req.push_back({a, c.b, 0, 0, c.I, c.J});
+            std::vector<double> left;
+            cudaError_t e = run_pe(req, left);
+            if (e != cudaSuccess) return fail(3, std::string("CUDA: ") + cudaGetErrorString(e));
+            std::vector<int> L;
+            for (size_t i = 0; i < cand.size(); i++) {
+                if (std::isnan(left[i])) return fail(2, "trimming loops intersect (pairing met a boundary point)");
+                if (left[i] > 0) L.push_back((int)i);
+            }
+            // relation: cand X left of cand Y in Y's (beta) orientation
+            req.clear();
+            for (int x : L)
+                for (int y : L)
+                    req.push_back({cand[y].b, cand[x].b, cand[y].I, cand[y].J, cand[x].I, cand[x].J});
+            std::vector<double> rel;
+            e = run_pe(req, rel);
+            if (e != cudaSuccess) return fail(3, std::string("CUDA: ") + cudaGetErrorString(e));
+            int best = -1;
+            for (size_t xi = 0; xi < L.size(); xi++) {
+                if (best >= 0) {
+                    size_t bi = std::find(L.begin(), L.end(), best) - L.begin();
+                    double w = rel[xi * L.size() + bi];
+                    if (std::isnan(w)) return fail(2, "trimming loops intersect (pairing met a boundary point)");
+                    if (!(w > 0)) continue;
+                }
+                best = L[xi];
+            }
+            if (best < 0) return fail(2, "no partner found for a non-contractible loop (App. C pairing)");
+            const Cand &bc = cand[best];
+            used[bc.b] = 1;
+            Pair pr{a, bc.b, bc.I, bc.J, LA.nlo, LA.nhi};
+            const HostLoop &LB = loops[bc.b];
+            for (int s = LB.s0; s < LB.s1; s++) {
+                const double *q = &P[2 * seg_cp[s]];
+                for (int i = 0; i <= seg_deg[s]; i++) {
+                    double x = q[2 * i] + (double)bc.I * Pu, y = q[2 * i + 1] + (double)bc.J * Pv;
+                    double nv = nx * x + ny * y;
+                    pr.plo = std::fmin(pr.plo, nv);
+                    pr.phi = std::fmax(pr.phi, nv);
+                }
+            }
+            pairs.push_back(pr);
+        }
+    }
+
+    // ---- instances
+    std::vector<InstDev> inst;
+    auto base_inst = [&](int type, int l) {
+        InstDev in;
+        std::memset(&in, 0, sizeof in);
+        in.type = type;
+        in.loop = l;
+        in.pair = -1;
+        in.r0 = loop_r0[l];
+        in.r1 = loop_r1[l];
+        return in;
+    };
+    const double tile_x[2] = {0.0, (Pu > 0) ? Pu : 0.0}, tile_y[2] = {0.0, (Pv > 0) ? Pv : 0.0};
+    // slab window of copies k of loop l seen from x_f = p - F, p in the base tile
+    auto add_extended = [&](int l, long long I, long long J, int pair, long long c) {
+        const HostLoop &L = loops[l];
+        InstDev ln = base_inst(IT_LINE, l);
+        ln.Fx = (double)I * Pu; ln.Fy = (double)J * Pv;
+        if (!(Pu > 0)) ln.Fx = 0.0;
+        if (!(Pv > 0)) ln.Fy = 0.0;
+        ln.I = I; ln.J = J; ln.pair = pair; ln.c = c;
+        ln.r0 = ln.r1 = 0;
+        inst.push_back(ln);
+        // sp range over the base tile (a cylinder tile is unbounded across the
+        // axis, but v has no component along it)
+        double smn = INFINITY, smx = -INFINITY;
+        for (double tx : tile_x)
+            for (double ty : tile_y) {
+                double xf = tx - ln.Fx, yf = ty - ln.Fy;
+                double sp = (xf * L.v[0] + yf * L.v[1]) / L.vv;
+                smn = std::fmin(smn, sp);
+                smx = std::fmax(smx, sp);
+            }
+        const long long klo = (long long)std::floor(smn - L.smax) - 1;
+        const long long khi = (long long)std::ceil(smx - L.smin) + 1;
+        for (long long k = klo; k <= khi; k++) {
+            InstDev in = base_inst(IT_PE, l);
+            in.Fx = ln.Fx; in.Fy = ln.Fy; in.I = I; in.J = J; in.pair = pair; in.c = c; in.k = k;
+            in.Tx = (Pu > 0) ? (double)(I + k * L.hp) * Pu : 0.0;
+            in.Ty = (Pv > 0) ? (double)(J + k * L.hq) * Pv : 0.0;
+            inst.push_back(in);
+        }
+    };
+    if (kind == DK_PLANAR) {
+        if (n_loops > 0 && ns > 0) {
+            InstDev in = base_inst(IT_ALL, 0);
+            in.r0 = 0;
+            in.r1 = (int)rec_seg.size();
+            inst.push_back(in);
+        }
+    } else {
+        for (int l = 0; l < n_loops; l++) {
+            const HostLoop &L = loops[l];
+            if (L.s1 == L.s0) continue;
+            if (L.cls == 1) {
+                long long ia = 0, ib = 0, ja = 0, jb = 0;
+                if (Pu > 0) {
+                    ia = (long long)std::floor((0.0 - L.box[1]) / Pu) - 1;
+                    ib = (long long)std::ceil((Pu - L.box[0]) / Pu) + 1;
+                }
+                if (Pv > 0) {
+                    ja = (long long)std::floor((0.0 - L.box[3]) / Pv) - 1;
+                    jb = (long long)std::ceil((Pv - L.box[2]) / Pv) + 1;
+                }
+                for (long long i = ia; i <= ib; i++)
+                    for (long long j = ja; j <= jb; j++) {
+                        InstDev in = base_inst(IT_BOX, l);
+                        in.axes = (Pu > 0 ? 1 : 0) | (Pv > 0 ? 2 : 0);
+                        in.Tx = (Pu > 0) ? (double)i * Pu : 0.0;
+                        in.Ty = (Pv > 0) ? (double)j * Pv : 0.0;
+                        inst.push_back(in);
+                    }
+            } else if (L.cls == 2 && kind != DK_BI) {
+                add_extended(l, 0, 0, -1, 0);
+            }
+        }
+        for (size_t k = 0; k < pairs.size(); k++) {
+            const Pair &pr = pairs[k];
+            double nmn = INFINITY, nmx = -INFINITY;
+            for (double tx : tile_x)
+                for (double ty : tile_y) {
+                    double np = nx * tx + ny * ty;
+                    nmn = std::fmin(nmn, np);
+                    nmx = std::fmax(nmx, np);
+                }
+            const long long clo = (long long)std::floor((nmn - pr.phi) / PP) - 1;
+            const long long chi = (long long)std::ceil((nmx - pr.plo) / PP) + 1;
+            for (long long c = clo; c <= chi; c++) {
+                add_extended(pr.a, c * i0, c * j0, (int)k, c);
+                add_extended(pr.b, c * i0 + pr.I, c * j0 + pr.J, (int)k, c);
+            }
+        }
+    }
+    std::vector<PairDev> hp_dev;
+    for (const Pair &pr : pairs) hp_dev.push_back({pr.plo, pr.phi});
+    dv.n_inst = (int)inst.size();
+    dv.n_pairs = (int)pairs.size();
+    dv.inst = up.up(inst);
+    dv.pairs = up.up(hp_dev);
+    if (up.err != cudaSuccess) return fail(up.err == cudaErrorMemoryAllocation ? 4 : 3,
+                                           std::string("CUDA: ") + cudaGetErrorString(up.err));
+    cudaError_t e = cudaMemcpy(D->d_self, &dv, sizeof dv, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(3, std::string("CUDA: ") + cudaGetErrorString(e));
+    D->n_records = (int64_t)rec_seg.size();
+    D->n_instances = (int64_t)inst.size();
+    D->sweep_records = 0;
+    for (const InstDev &in : inst) D->sweep_records += in.r1 - in.r0;
+    *out = D;
+    return 0;
+}
+
+}  // namespace wn

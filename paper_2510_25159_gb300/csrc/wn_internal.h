@@ -1,0 +1,87 @@
+// wn_internal.h -- host-side declarations shared by the library's translation
+// units (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "wn_dev.cuh"
+
+struct wn_domain {
+    wn::DomDev dev;            // device pointers filled in
+    wn::DomDev *d_self;        // device copy of dev
+    std::vector<void *> allocs;  // device allocations owned by the domain
+    int device;
+    int64_t n_records;
+    int64_t n_instances;
+    int64_t sweep_records;     // sum over instances of their record counts
+};
+
+namespace wn {
+
+// Where the query points come from.
+struct PointSrc {
+    const double *pts;         // x,y interleaved, indexed by global query index
+    int32_t nu, nv;            // grid mode when pts == nullptr
+    double su, sv;             // grid scale (period or 1)
+};
+
+// Output of a query call.
+struct OutDst {
+    double *w;                 // may be null
+    uint8_t *st;               // may be null
+    uint32_t *bits;            // grid bitmask mode
+    unsigned long long *nbound;  // grid boundary counter
+};
+
+// Per-device scratch of the mixed path.
+struct Work {
+    int32_t *acc2 = nullptr;   // 2 * crossings + line halves, per query
+    float *theta = nullptr;    // sum of gap angles, per query
+    uint32_t *flags = nullptr; // QF_*, per query
+    Item *near_items = nullptr;
+    Item *f64_items = nullptr;
+    uint2 *esc_q = nullptr;    // (query, batch entry) recomputed in FP64
+    unsigned int *counters = nullptr;  // see CNT_*
+    int4 *units = nullptr;     // (dom, q0, count, 0)
+    DomDev *doms = nullptr;
+    int64_t *offsets = nullptr;  // device copy of point offsets
+    int64_t cap_q = 0, cap_near = 0, cap_f64 = 0, cap_units = 0, cap_doms = 0, cap_off = 0;
+};
+
+enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_ERR = 4, CNT_OVF = 5,
+       CNT_NEAR_TAKEN = 6, CNT_N = 8 };
+
+struct Tuning {
+    int qpt = 2;               // queries per sweep thread
+    int sweep_ctas_per_sm = 4;
+    int near_ctas_per_sm = 8;
+    int use_graph = 0;
+};
+
+struct LaunchCfg {
+    int n_sm;
+    Tuning tun;
+    std::vector<cudaEvent_t> *events;  // non-null: record 6 events per call around the kernels
+};
+
+// Kernels (wn_kernels.cu)
+cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const int4 *d_units,
+                         int n_units, const int64_t *d_offsets, int64_t n_queries, PointSrc src,
+                         OutDst out, const LaunchCfg &cfg, cudaStream_t s);
+cudaError_t launch_plain(const DomDev *d_dom, int64_t q0, int64_t n, PointSrc src, OutDst out,
+                         cudaStream_t s);
+struct PeReq {
+    int a, b;
+    long long IA, JA, IB, JB;
+};
+cudaError_t launch_pe_eval(const DomDev *d_dom, const PeReq *d_req, int n, double *d_out,
+                           cudaStream_t s);
+
+// Domain build (wn_domain.cu)
+int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
+                 const double *cps, double Pu, double Pv, double eps, wn_domain **out,
+                 std::string &err);
+
+}  // namespace wn

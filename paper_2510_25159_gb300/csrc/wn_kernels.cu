@@ -1,0 +1,703 @@
+// wn_kernels.cu -- query kernels of the containment library (sm_103a).
+//
+// Mixed path (WN_PREC_MIXED), per call:
+//   k_sweep     persistent CTAs pop (domain, query-tile) units; each CTA
+//               stages the records of every instance it needs in shared
+//               memory and sweeps them against a register tile of queries.
+//               Per record it applies the root step of Algorithm 1 in FP32:
+//               a circle that contains the ellipse of Eq. 4 (inflated by the
+//               FP32 error bound) decides "far"; a far chord then contributes
+//               its signed crossing of the +x ray from the query (the chord's
+//               Eq. 3 angle is an integer multiple of 2 pi plus endpoint
+//               angles that cancel around each loop), and every gap between
+//               consecutive segments contributes its own crossing and its
+//               exact small angle.  Pairs inside the circle go to a queue.
+//   k_near      FP32 Algorithm 1 on each queued pair in query-relative
+//               coordinates; every test carries an error band, and a pair
+//               whose band cannot settle a decision goes to FP64.
+//   k_f64items  Algorithm 1 in FP64 on those pairs.
+//   k_finalize  omega = crossings + line terms / 2 - sum(gap angles) / 2 pi;
+//               a query whose omega lies within 1e-4 of 1/2, or that any
+//               kernel flagged, is recomputed by the plain FP64 method.
+//   k_f64query  plain FP64 recomputation of those queries.
+// Plain path (WN_PREC_PLAIN_FP64): k_plain, one thread per query running
+// Algorithm 1 in FP64 on every segment the query sees, chord angles summed
+// with atan2 (Eq. 3) -- the paper's method ported as is.
+#include <algorithm>
+
+#include "wn_internal.h"
+
+namespace wn {
+
+constexpr float kTwoM22 = 2.384185791015625e-7f;   // 2^-22
+constexpr float kTwoM24 = 5.9604644775390625e-8f;  // 2^-24
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kOmegaBand = 1e-4;                 // classification band of the mixed path
+constexpr int kSweepThreads = 256;
+constexpr int kChunk = 64;                          // records per shared-memory stage
+
+__device__ __forceinline__ void get_point(const PointSrc &s, uint32_t q, double &x, double &y)
+{
+    if (s.pts) {
+        double2 v = __ldg(reinterpret_cast<const double2 *>(s.pts) + q);
+        x = v.x;
+        y = v.y;
+    } else {
+        uint32_t i = q % (uint32_t)s.nu, j = q / (uint32_t)s.nu;
+        x = ((double)i + 0.5) / (double)s.nu * s.su;
+        y = ((double)j + 0.5) / (double)s.nv * s.sv;
+    }
+}
+
+__device__ __forceinline__ double exact_cross(double2 a, double2 b, double px, double py)
+{
+    double ax = a.x - px, ay = a.y - py, bx = b.x - px, by = b.y - py;
+    return ax * by - ay * bx;
+}
+
+// ------------------------------------------------------------------ sweep
+struct SweepArgs {
+    const DomDev *doms;
+    const int4 *units;
+    int n_units;
+    PointSrc src;
+    int32_t *acc2;
+    float *theta;
+    uint32_t *flags;
+    Item *near_items;
+    long long cap_near;
+    unsigned int *counters;
+};
+
+// One record against one query: root step of Alg. 1 (circle prefilter of
+// the ellipse), chord crossing, gap crossing and gap angle.
+__device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, const float4 R2,
+                                             int ridx, const DomDev *__restrict__ Dp, float fx,
+                                             float fy, float T, double pxp, double pyp,
+                                             float Racc2, int &c, float &dth, bool &near)
+{
+    const float uy = R0.y - fy, wy = R0.w - fy;
+    bool sa = uy > 0.f, sb = wy > 0.f;
+    if (fabsf(uy) <= T) sa = __ldg(&Dp->rec_a64[ridx].y) > pyp;
+    if (fabsf(wy) <= T) sb = __ldg(&Dp->rec_b64[ridx].y) > pyp;
+    const uint32_t fl = __float_as_uint(R1.w);
+    const float wx = R0.z - fx;
+    near = false;
+    c = 0;
+    dth = 0.f;
+    if (!(fl & RF_CHORD)) {
+        const float dcx = R1.x - fx, dcy = R1.y - fy;
+        near = fmaf(dcx, dcx, dcy * dcy) <= R1.z;
+    }
+    if (!near && sa != sb) {
+        const float ux = R0.x - fx;
+        const float D = fmaf(ux, wy, -uy * wx);
+        const float TD = T * (fabsf(ux) + fabsf(uy) + fabsf(wx) + fabsf(wy)) +
+                         kTwoM22 * (fabsf(ux * wy) + fabsf(uy * wx));
+        bool pos = D > 0.f;
+        if (fabsf(D) <= TD)
+            pos = exact_cross(__ldg(&Dp->rec_a64[ridx]), __ldg(&Dp->rec_b64[ridx]), pxp, pyp) > 0;
+        c = (!sa && sb && pos) ? 1 : ((sa && !sb && !pos) ? -1 : 0);
+    }
+    if (fl & RF_GAP) {
+        const float gx = R2.x, gy = R2.y;
+        const float ny = R2.w - fy;
+        bool sn = ny > 0.f;
+        if (fabsf(ny) <= T) sn = __ldg(&Dp->rec_n64[ridx].y) > pyp;
+        float bx = wx, by = wy;
+        if (fmaf(bx, bx, by * by) < Racc2) {
+            const double2 b = __ldg(&Dp->rec_b64[ridx]);
+            bx = (float)(b.x - pxp);
+            by = (float)(b.y - pyp);
+        }
+        const float Dg = fmaf(bx, gy, -by * gx);
+        if (sb != sn) {
+            const float TDg = T * (fabsf(gx) + fabsf(gy)) + kTwoM22 * (fabsf(bx * gy) + fabsf(by * gx));
+            bool pos = Dg > 0.f;
+            if (fabsf(Dg) <= TDg)
+                pos = exact_cross(__ldg(&Dp->rec_b64[ridx]), __ldg(&Dp->rec_n64[ridx]), pxp, pyp) > 0;
+            c += (!sb && sn && pos) ? 1 : ((sb && !sn && !pos) ? -1 : 0);
+        }
+        const float dot = fmaf(bx, bx + gx, by * (by + gy));
+        dth = atan2f(Dg, dot);
+    }
+}
+
+template <int QPT>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs A)
+{
+    __shared__ float4 s_rec[3 * kChunk];
+    __shared__ int s_unit;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[CNT_UNIT], 1u);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= A.n_units) return;
+        const int4 U = __ldg(&A.units[u]);
+        const DomDev *__restrict__ Dp = A.doms + U.x;
+        const double Pu = Dp->Pu, Pv = Dp->Pv, ox = Dp->ox, oy = Dp->oy;
+        const float M = Dp->M, Mq = Dp->Mq, Racc2 = Dp->Racc2;
+        const int n_inst = Dp->n_inst;
+        const float4 *__restrict__ rec = Dp->rec;
+
+        double px[QPT], py[QPT], pxp[QPT], pyp[QPT];
+        float fx[QPT], fy[QPT], T[QPT], th[QPT];
+        int acc[QPT];
+        uint32_t fl[QPT];
+        bool valid[QPT], inc[QPT];
+#pragma unroll
+        for (int k = 0; k < QPT; k++) {
+            const int ql = tid + k * kSweepThreads;
+            valid[k] = ql < U.z;
+            double x = 0.0, y = 0.0;
+            if (valid[k]) get_point(A.src, (uint32_t)(U.y + ql), x, y);
+            px[k] = reduce_period(x, Pu);
+            py[k] = reduce_period(y, Pv);
+            acc[k] = 0;
+            th[k] = 0.f;
+            fl[k] = 0u;
+        }
+        for (int j = 0; j < n_inst; j++) {
+            const InstDev in = Dp->inst[j];
+            const LoopDev &L = Dp->loops[in.loop];
+            int any = 0;
+#pragma unroll
+            for (int k = 0; k < QPT; k++) {
+                inc[k] = valid[k] && !(fl[k] & (QF_BOUNDARY | QF_ESCALATE)) &&
+                         inst_sees(*Dp, in, L, px[k], py[k]);
+                if (in.type == IT_LINE) {
+                    if (inc[k]) {
+                        const int s = line_side(*Dp, in, L, px[k], py[k]);
+                        if (s == 0) fl[k] |= QF_BOUNDARY;
+                        acc[k] += s;
+                    }
+                    inc[k] = false;
+                    continue;
+                }
+                pxp[k] = xsub(px[k], in.Tx);
+                pyp[k] = xsub(py[k], in.Ty);
+                fx[k] = (float)(pxp[k] - ox);
+                fy[k] = (float)(pyp[k] - oy);
+                const float mag = fmaxf(fabsf(fx[k]), fabsf(fy[k]));
+                if (inc[k] && !(mag <= Mq)) {
+                    fl[k] |= QF_ESCALATE;
+                    inc[k] = false;
+                }
+                T[k] = kTwoM22 * (M + mag);
+                any |= inc[k];
+            }
+            if (!__syncthreads_or(any)) continue;
+            for (int r0 = in.r0; r0 < in.r1; r0 += kChunk) {
+                const int cnt = min(kChunk, in.r1 - r0);
+                for (int i = tid; i < 3 * cnt; i += kSweepThreads) s_rec[i] = __ldg(rec + 3 * r0 + i);
+                __syncthreads();
+                for (int r = 0; r < cnt; r++) {
+                    const float4 R0 = s_rec[3 * r], R1 = s_rec[3 * r + 1], R2 = s_rec[3 * r + 2];
+                    bool nr[QPT];
+                    bool any_near = false;
+#pragma unroll
+                    for (int k = 0; k < QPT; k++) {
+                        int c;
+                        float dth;
+                        sweep_record(R0, R1, R2, r0 + r, Dp, fx[k], fy[k], T[k], pxp[k], pyp[k], Racc2,
+                                     c, dth, nr[k]);
+                        nr[k] = nr[k] && inc[k];
+                        if (inc[k]) {
+                            acc[k] += 2 * c;
+                            th[k] += dth;
+                        }
+                        any_near |= nr[k];
+                    }
+                    if (__any_sync(0xffffffffu, any_near)) {
+#pragma unroll
+                        for (int k = 0; k < QPT; k++) {
+                            const unsigned m = __ballot_sync(0xffffffffu, nr[k]);
+                            if (!m) continue;
+                            const int leader = __ffs(m) - 1;
+                            unsigned base = 0;
+                            if (lane == leader) base = atomicAdd(&A.counters[CNT_NEAR], (unsigned)__popc(m));
+                            base = __shfl_sync(0xffffffffu, base, leader);
+                            if (nr[k]) {
+                                const unsigned long long idx = (unsigned long long)base + __popc(m & lt_mask);
+                                if (idx < (unsigned long long)A.cap_near) {
+                                    Item it;
+                                    it.q = (uint32_t)(U.y + tid + k * kSweepThreads);
+                                    it.dom = (uint32_t)U.x;
+                                    it.inst = (uint32_t)j;
+                                    it.rec = (uint32_t)(r0 + r);
+                                    A.near_items[idx] = it;
+                                } else {
+                                    fl[k] |= QF_ESCALATE;
+                                }
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < QPT; k++) {
+            if (!valid[k]) continue;
+            const uint32_t q = (uint32_t)(U.y + tid + k * kSweepThreads);
+            A.acc2[q] = acc[k];
+            A.theta[q] = th[k];
+            A.flags[q] = fl[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ near pairs, FP32
+// Algorithm 1 in FP32 on query-relative control points.  E bounds the
+// absolute error of every evaluated point against the FP64 value.
+// Returns 0 (cnt valid), 1 (boundary), 2 (a band could not decide: redo in FP64).
+__device__ int near_fp32(const float *qx, const float *qy, int n, float B, float eps, float E,
+                         int &cnt)
+{
+    float st_t[kDepthCap32 + 2], st_x[kDepthCap32 + 2], st_y[kDepthCap32 + 2];
+    int st_d[kDepthCap32 + 2];
+    cnt = 0;
+    float a = 0.f, ax = qx[0], ay = qy[0];
+    float ra = sqrtf(fmaf(ax, ax, ay * ay));
+    {
+        const float er = E + ra * kTwoM22;
+        if (ra + er < eps) return 1;
+        if (ra - er < eps) return 2;
+    }
+    st_t[0] = 1.f;
+    st_x[0] = qx[n];
+    st_y[0] = qy[n];
+    st_d[0] = 0;
+    int sp = 1;
+    bool b_tested = false;
+    while (sp > 0) {
+        const float b = st_t[sp - 1], bx = st_x[sp - 1], by = st_y[sp - 1];
+        const int d = st_d[sp - 1];
+        const float rb = sqrtf(fmaf(bx, bx, by * by));
+        if (!b_tested) {
+            const float er = E + rb * kTwoM22;
+            if (rb + er < eps) return 1;
+            if (rb - er < eps) return 2;
+            b_tested = true;
+        }
+        const float lim = B * (b - a);
+        const float s = (ra + rb) - lim;
+        const float es = 2.f * E + (ra + rb + lim) * (2.f * kTwoM22);
+        if (s > es) {
+            const bool sa = ay > 0.f, sb = by > 0.f;
+            if (sa != sb) {
+                const float D = fmaf(ax, by, -ay * bx);
+                if (fabsf(D) <= kTwoM22 * (fabsf(ax * by) + fabsf(ay * bx))) return 2;
+                if (!sa && sb && D > 0.f) cnt++;
+                else if (sa && !sb && D < 0.f) cnt--;
+            }
+            a = b;
+            ax = bx;
+            ay = by;
+            ra = rb;
+            sp--;
+            b_tested = true;   // the next top was tested when it was pushed
+            continue;
+        }
+        if (s >= -es) return 2;
+        if (d >= kDepthCap32) return 2;
+        const float m = 0.5f * (a + b);
+        float mx, my;
+        bez_eval<float>(qx, qy, n, m, mx, my);
+        st_d[sp - 1] = d + 1;
+        st_t[sp] = m;
+        st_x[sp] = mx;
+        st_y[sp] = my;
+        st_d[sp] = d + 1;
+        sp++;
+        b_tested = false;
+    }
+    return 0;
+}
+
+struct NearArgs {
+    const DomDev *doms;
+    PointSrc src;
+    const Item *items;
+    long long cap_near;
+    int32_t *acc2;
+    uint32_t *flags;
+    Item *f64_items;
+    long long cap_f64;
+    unsigned int *counters;
+};
+
+__device__ __forceinline__ void item_query(const DomDev *Dp, const PointSrc &src, const Item &it,
+                                           double &pxp, double &pyp)
+{
+    double x, y;
+    get_point(src, it.q, x, y);
+    x = reduce_period(x, Dp->Pu);
+    y = reduce_period(y, Dp->Pv);
+    const InstDev &in = Dp->inst[it.inst];
+    pxp = xsub(x, in.Tx);
+    pyp = xsub(y, in.Ty);
+}
+
+__global__ void __launch_bounds__(256) k_near(const NearArgs A)
+{
+    unsigned long long n = A.counters[CNT_NEAR];
+    if (n > (unsigned long long)A.cap_near) n = (unsigned long long)A.cap_near;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const Item it = A.items[i];
+        const DomDev *Dp = A.doms + it.dom;
+        double pxp, pyp;
+        item_query(Dp, A.src, it, pxp, pyp);
+        const int s = __ldg(&Dp->rec_seg[it.rec]);
+        const int deg = __ldg(&Dp->seg_deg[s]);
+        const double *P = Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]);
+        float qx[kNcp], qy[kNcp];
+        float mq = 0.f;
+#pragma unroll
+        for (int k = 0; k < kNcp; k++) {
+            if (k <= deg) {
+                qx[k] = (float)(__ldg(P + 2 * k) - pxp);
+                qy[k] = (float)(__ldg(P + 2 * k + 1) - pyp);
+                mq = fmaxf(mq, fabsf(qx[k]) + fabsf(qy[k]));
+            } else {
+                qx[k] = 0.f;
+                qy[k] = 0.f;
+            }
+        }
+        const float B = (float)__ldg(&Dp->seg_B[s]);
+        const float E = (float)(2 * deg + 4) * kTwoM24 * mq;
+        int cnt = 0;
+        const int r = near_fp32(qx, qy, deg, B, (float)Dp->eps, E, cnt);
+        if (r == 2) {
+            const unsigned idx = atomicAdd(&A.counters[CNT_F64], 1u);
+            if (idx < (unsigned long long)A.cap_f64) A.f64_items[idx] = it;
+            else atomicOr(&A.flags[it.q], QF_ESCALATE);
+        } else if (r == 1) {
+            atomicOr(&A.flags[it.q], QF_BOUNDARY);
+        } else if (cnt) {
+            atomicAdd(&A.acc2[it.q], 2 * cnt);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ FP64 pairs
+__global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
+{
+    unsigned long long n = A.counters[CNT_F64];
+    if (n > (unsigned long long)A.cap_f64) n = (unsigned long long)A.cap_f64;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const Item it = A.f64_items[i];
+        const DomDev *Dp = A.doms + it.dom;
+        double pxp, pyp;
+        item_query(Dp, A.src, it, pxp, pyp);
+        const int s = Dp->rec_seg[it.rec];
+        FarCross fc;
+        const bool bnd = alg1_fp64(Dp->cp + 2 * (size_t)Dp->seg_cp[s], Dp->seg_deg[s], Dp->seg_B[s],
+                                   pxp, pyp, Dp->eps, fc);
+        if (bnd) atomicOr(&A.flags[it.q], QF_BOUNDARY);
+        else if (fc.cnt) atomicAdd(&A.acc2[it.q], 2 * fc.cnt);
+    }
+}
+
+// ------------------------------------------------------------------ plain FP64
+// Sum over every instance the query sees of Algorithm 1 (FP64, atan2 chord
+// angles), the chord corrections and line terms of Eq. 9.
+__device__ void plain_query(const DomDev *Dp, double x0, double y0, double &om, int &state)
+{
+    const double x = reduce_period(x0, Dp->Pu), y = reduce_period(y0, Dp->Pv);
+    FarAngle fa;
+    long long half = 0;
+    bool bnd = false;
+    const double eps = Dp->eps;
+    for (int j = 0; j < Dp->n_inst && !bnd; j++) {
+        const InstDev in = Dp->inst[j];
+        const LoopDev &L = Dp->loops[in.loop];
+        if (!inst_sees(*Dp, in, L, x, y)) continue;
+        if (in.type == IT_LINE) {
+            const int s = line_side(*Dp, in, L, x, y);
+            if (s == 0) bnd = true;
+            half += s;
+            continue;
+        }
+        const double qx = xsub(x, in.Tx), qy = xsub(y, in.Ty);
+        for (int s = L.s0; s < L.s1 && !bnd; s++)
+            bnd = alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]), __ldg(&Dp->seg_deg[s]),
+                            __ldg(&Dp->seg_B[s]), qx, qy, eps, fa);
+        if (in.type == IT_PE && !bnd) {
+            const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
+            fa.ang -= atan2(ax * by - ay * bx, ax * bx + ay * by);
+        }
+    }
+    if (bnd) {
+        om = __longlong_as_double(0x7ff8000000000000ULL);
+        state = 2;
+    } else {
+        om = fa.ang / kTwoPi + 0.5 * (double)half;
+        state = om >= 0.5 ? 1 : 0;
+    }
+}
+
+__device__ __forceinline__ void write_out(const OutDst &o, uint32_t q, double om, int st, bool atomic_bits)
+{
+    if (o.w) o.w[q] = om;
+    if (o.st) o.st[q] = (uint8_t)st;
+    if (o.bits && atomic_bits) {
+        if (st != 0) atomicOr(&o.bits[q >> 5], 1u << (q & 31));
+        if (st == 2 && o.nbound) atomicAdd(o.nbound, 1ull);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_plain(const DomDev *Dp, long long q0, long long n,
+                                               PointSrc src, OutDst out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t q = (uint32_t)(q0 + i);
+        double x, y, om;
+        int st;
+        get_point(src, q, x, y);
+        plain_query(Dp, x, y, om, st);
+        write_out(out, q, om, st, true);
+    }
+}
+
+// ------------------------------------------------------------------ finalize
+struct FinArgs {
+    long long n;
+    const int64_t *offsets;
+    int n_doms;
+    const int32_t *acc2;
+    const float *theta;
+    const uint32_t *flags;
+    uint2 *esc;
+    unsigned int *counters;
+    OutDst out;
+};
+
+__device__ __forceinline__ uint32_t find_dom(const int64_t *off, int n_doms, long long q)
+{
+    int lo = 0, hi = n_doms - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return (uint32_t)lo;
+}
+
+__global__ void __launch_bounds__(256) k_finalize(const FinArgs A)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long nround = (A.n + 31) & ~31LL;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nround; i += stride) {
+        const bool in_range = i < A.n;
+        const uint32_t q = (uint32_t)i;
+        int st = 0;
+        double om = 0.0;
+        bool esc = false;
+        if (in_range) {
+            const uint32_t f = A.flags[q];
+            if (f & QF_ESCALATE) {
+                esc = true;
+            } else if (f & QF_BOUNDARY) {
+                st = 2;
+                om = __longlong_as_double(0x7ff8000000000000ULL);
+            } else {
+                om = 0.5 * (double)A.acc2[q] - (double)A.theta[q] / kTwoPi;
+                if (fabs(om - 0.5) < kOmegaBand) esc = true;
+                st = om >= 0.5 ? 1 : 0;
+            }
+            if (esc) {
+                const unsigned idx = atomicAdd(&A.counters[CNT_ESC], 1u);
+                A.esc[idx] = make_uint2(q, find_dom(A.offsets, A.n_doms, (long long)q));
+            } else {
+                write_out(A.out, q, om, st, false);
+            }
+        }
+        if (A.out.bits) {
+            const unsigned m = __ballot_sync(0xffffffffu, in_range && !esc && st != 0);
+            const unsigned mb = __ballot_sync(0xffffffffu, in_range && !esc && st == 2);
+            if ((threadIdx.x & 31) == 0) {
+                A.out.bits[i >> 5] = m;
+                if (mb && A.out.nbound) atomicAdd(A.out.nbound, (unsigned long long)__popc(mb));
+            }
+        }
+    }
+}
+
+struct EscArgs {
+    const DomDev *doms;
+    PointSrc src;
+    const uint2 *esc;
+    const unsigned int *counters;
+    OutDst out;
+};
+
+__global__ void __launch_bounds__(128) k_f64query(const EscArgs A)
+{
+    const unsigned n = A.counters[CNT_ESC];
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint2 e = A.esc[i];
+        double x, y, om;
+        int st;
+        get_point(A.src, e.x, x, y);
+        plain_query(A.doms + e.y, x, y, om, st);
+        write_out(A.out, e.x, om, st, true);
+    }
+}
+
+// ------------------------------------------------------------------ pairing support
+// PE(x, loop a at family shift (IA, JA)) for x = mid(loop b) + (IB Pu, JB Pv),
+// Eq. 9 in FP64 with the slab window (App. C, Alg. 8 ToLeft).
+
+__global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const PeReq R = req[i];
+    const LoopDev &Lb = Dp->loops[R.b];
+    const int m = Lb.s1 - Lb.s0;
+    const int s = Lb.s0 + m / 2;
+    const double t = (m % 2) ? 0.5 : 0.0;
+    const int deg = Dp->seg_deg[s];
+    const double *P = Dp->cp + 2 * (size_t)Dp->seg_cp[s];
+    double cx[kNcp], cy[kNcp];
+    for (int k = 0; k < kNcp; k++) {
+        cx[k] = k <= deg ? P[2 * k] : 0.0;
+        cy[k] = k <= deg ? P[2 * k + 1] : 0.0;
+    }
+    double mx, my;
+    bez_eval<double>(cx, cy, deg, t, mx, my);
+    const double Pu = Dp->Pu, Pv = Dp->Pv;
+    const double x = xadd(mx, xmul((double)R.IB, Pu)), y = xadd(my, xmul((double)R.JB, Pv));
+    const LoopDev &L = Dp->loops[R.a];
+    const double xf = (Pu > 0) ? xsub(x, xmul((double)R.IA, Pu)) : x;
+    const double yf = (Pv > 0) ? xsub(y, xmul((double)R.JA, Pv)) : y;
+    const double cr = xsub(xmul(L.vx, xsub(yf, L.g0y)), xmul(L.vy, xsub(xf, L.g0x)));
+    if (cr == 0) {
+        out[i] = __longlong_as_double(0x7ff8000000000000ULL);
+        return;
+    }
+    FarAngle fa;
+    const double sp = xdiv(xadd(xmul(xf, L.vx), xmul(yf, L.vy)), L.vv);
+    const double klo = ceil(xsub(sp, L.smax)), khi = floor(xsub(sp, L.smin));
+    for (double k = klo; k <= khi; k += 1.0) {
+        const long long kk = (long long)k;
+        const double qx = (Pu > 0) ? xsub(x, xmul((double)(R.IA + kk * L.hp), Pu)) : x;
+        const double qy = (Pv > 0) ? xsub(y, xmul((double)(R.JA + kk * L.hq), Pv)) : y;
+        for (int sg = L.s0; sg < L.s1; sg++) {
+            if (alg1_fp64(Dp->cp + 2 * (size_t)Dp->seg_cp[sg], Dp->seg_deg[sg], Dp->seg_B[sg], qx, qy,
+                          Dp->eps, fa)) {
+                out[i] = __longlong_as_double(0x7ff8000000000000ULL);
+                return;
+            }
+        }
+        const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
+        fa.ang -= atan2(ax * by - ay * bx, ax * bx + ay * by);
+    }
+    out[i] = fa.ang / kTwoPi + (cr > 0 ? 0.5 : -0.5);
+}
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const int4 *d_units,
+                         int n_units, const int64_t *d_offsets, int64_t n_queries, PointSrc src,
+                         OutDst out, const LaunchCfg &cfg, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(W.counters, 0, CNT_N * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t ev[6] = {};
+    if (cfg.events) {
+        for (int i = 0; i < 6; i++) {
+            if ((e = cudaEventCreate(&ev[i])) != cudaSuccess) return e;
+            cfg.events->push_back(ev[i]);
+        }
+    }
+    auto mark = [&](int i) {
+        if (cfg.events) cudaEventRecord(ev[i], s);
+    };
+    if (out.nbound) {
+        e = cudaMemsetAsync(out.nbound, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
+    SweepArgs sa;
+    sa.doms = d_doms;
+    sa.units = d_units;
+    sa.n_units = n_units;
+    sa.src = src;
+    sa.acc2 = W.acc2;
+    sa.theta = W.theta;
+    sa.flags = W.flags;
+    sa.near_items = W.near_items;
+    sa.cap_near = W.cap_near;
+    sa.counters = W.counters;
+    const int sweep_grid = max(1, min(n_units, cfg.n_sm * cfg.tun.sweep_ctas_per_sm));
+    mark(0);
+    switch (cfg.tun.qpt) {
+    case 1: k_sweep<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+    case 4: k_sweep<4><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+    default: k_sweep<2><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+    }
+    NearArgs na;
+    na.doms = d_doms;
+    na.src = src;
+    na.items = W.near_items;
+    na.cap_near = W.cap_near;
+    na.acc2 = W.acc2;
+    na.flags = W.flags;
+    na.f64_items = W.f64_items;
+    na.cap_f64 = W.cap_f64;
+    na.counters = W.counters;
+    mark(1);
+    k_near<<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
+    mark(2);
+    k_f64items<<<cfg.n_sm * 4, 128, 0, s>>>(na);
+    mark(3);
+    FinArgs fa;
+    fa.n = n_queries;
+    fa.offsets = d_offsets;
+    fa.n_doms = n_doms;
+    fa.acc2 = W.acc2;
+    fa.theta = W.theta;
+    fa.flags = W.flags;
+    fa.esc = W.esc_q;
+    fa.counters = W.counters;
+    fa.out = out;
+    const long long fin_blocks = std::max(1LL, std::min((long long)(n_queries + 255) / 256, (long long)cfg.n_sm * 16));
+    k_finalize<<<(int)fin_blocks, 256, 0, s>>>(fa);
+    mark(4);
+    EscArgs ea;
+    ea.doms = d_doms;
+    ea.src = src;
+    ea.esc = W.esc_q;
+    ea.counters = W.counters;
+    ea.out = out;
+    k_f64query<<<cfg.n_sm * 4, 128, 0, s>>>(ea);
+    mark(5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain(const DomDev *d_dom, int64_t q0, int64_t n, PointSrc src, OutDst out,
+                         cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = std::min((long long)(n + 127) / 128, 1LL << 20);
+    k_plain<<<(int)blocks, 128, 0, s>>>(d_dom, q0, n, src, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pe_eval(const DomDev *d_dom, const PeReq *d_req, int n, double *d_out,
+                           cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_pe_eval<<<(n + 63) / 64, 64, 0, s>>>(d_dom, d_req, n, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace wn

@@ -1,0 +1,177 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Sizes span several sweep tiles (512 queries) and ragged tails.  States must
+match exactly except oracle ties (decision margin < 1e-12 * domain scale);
+omega within 1e-9 (plain FP64) / 1e-5 (mixed); closed-loop workloads must
+also match rounded omega exactly."""
+import numpy as np
+import pytest
+
+import wn_synth as ws
+from tests.gpu_util import TOL_MIXED, TOL_PLAIN, compare, run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2510_25159_gb300 as wn
+    return wn
+
+
+PRECS = [("mixed", 1, TOL_MIXED), ("plain", 0, TOL_PLAIN)]
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_workload1_closed(wn, name, prec, tol):
+    dom, q = ws.config1()
+    (w, s), = run(wn, [dom], [q], prec)
+    r = compare(dom, q, w, s, tol, closed=True)
+    assert r["boundary"] == 0
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_workload2_open_noisy(wn, name, prec, tol):
+    doms, qs = ws.config2(n_domains=64, n_uniform=64 * 12000, n_near=64 * 1500,
+                          domain_subset=range(6))
+    res = run(wn, doms, qs, prec)
+    for d, q, (w, s) in zip(doms, qs, res):
+        compare(d, q, w, s, tol)
+
+
+def test_workload2_full_size_sampled(wn):
+    """The benchmark configuration (64 domains, 10M + 1M queries) in one
+    mixed batched call; the oracle checks a stratified sample of every
+    domain's uniform and near-curve queries."""
+    doms, qs = ws.config2()
+    res = run(wn, doms, qs, 1)
+    rng = np.random.default_rng(7)
+    for i, (d, q, (w, s)) in enumerate(zip(doms, qs, res)):
+        n = len(q)
+        nu = n - (1_000_000 // 64 + (1 if i < 1_000_000 % 64 else 0))
+        idx = np.concatenate([rng.choice(nu, 150, replace=False), nu + rng.choice(n - nu, 100, replace=False),
+                              [0, n - 1]])
+        compare(d, q[idx], w[idx], s[idx], TOL_MIXED)
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_workload3_biperiodic(wn, name, prec, tol):
+    doms, qs = ws.config3(n_faces=256, n_queries=256 * 3000, face_subset=range(8))
+    res = run(wn, doms, qs, prec)
+    for d, q, (w, s) in zip(doms, qs, res):
+        compare(d, q, w, s, tol)
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_uniperiodic_cylinders(wn, name, prec, tol):
+    rng = ws.rng_for(40)
+    doms, qs = [], []
+    for f in range(5):
+        lps = ws.uniperiodic_face(rng, 3 + f, (6, 40), P=1.0, degrees=(1, 5))
+        doms.append(ws.make_domain(lps, 1.0, 0.0, eps=1e-9))
+        q = np.stack([rng.uniform(-2, 3, 2500), rng.uniform(-0.1, 1.1, 2500)], axis=1)
+        qs.append(q)
+    res = run(wn, doms, qs, prec)
+    for d, q, (w, s) in zip(doms, qs, res):
+        compare(d, q, w, s, tol)
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_workload4_batched_mixed_kinds(wn, name, prec, tol):
+    S, Q, kind = ws.config4_sizes()
+    pick = list(np.nonzero(kind < 0.1)[0][:6]) + list(np.nonzero((kind >= 0.1) & (kind < 0.2))[0][:6]) + \
+        list(np.nonzero(kind >= 0.2)[0][:20])
+    doms, qs = ws.config4(face_subset=pick, query_scale=0.05)
+    res = run(wn, doms, qs, prec)
+    for d, q, (w, s) in zip(doms, qs, res):
+        compare(d, q, w, s, tol)
+
+
+def test_grid_bitmask(wn):
+    import torch
+    dom = ws.config5_face(0, levels=8, n_holes=25, hole_segs=24)
+    nu, nv = 200, 137
+    pts = ws.grid_points(nu, nv)
+    from oracle import query
+    ow, osd = query(dom, pts)
+    for prec in (1, 0):
+        h = wn.Domain.from_dict(dom)
+        bits, nb = wn.query_grid_bitmask(h, nu, nv, precision=prec)
+        torch.cuda.synchronize()
+        b = bits.cpu().numpy().view(np.uint32)
+        k = np.arange(nu * nv)
+        got = (b[k >> 5] >> (k & 31).astype(np.uint32)) & 1
+        assert np.array_equal(got, (osd != 0).astype(np.uint32))
+        assert int(nb.item()) == int((osd == 2).sum())
+        h.close()
+
+
+def test_edge_cases(wn):
+    import torch
+    # empty query set, single query, ragged tile tails
+    dom, q = ws.config1(n_uniform=1500, n_near=1)
+    h = wn.Domain.from_dict(dom)
+    for n in (0, 1, 511, 512, 513, 1501):
+        pts = torch.from_numpy(q[:n].copy()).cuda()
+        w, s = wn.query(h, pts, precision=1)
+        torch.cuda.synchronize()
+        if n:
+            compare(dom, q[:n], w.cpu().numpy(), s.cpu().numpy(), TOL_MIXED)
+    # points exactly on control points are BOUNDARY, far-away points escalate
+    seg_ends = dom["cps"][::4][:40]
+    far = np.array([[50.0, -30.0], [1e6, 1e6], [-3.0, 0.5]])
+    pts = np.concatenate([seg_ends, far])
+    for prec in (1, 0):
+        w, s = wn.query(h, torch.from_numpy(pts).cuda(), precision=prec)
+        torch.cuda.synchronize()
+        s = s.cpu().numpy()
+        assert np.all(s[:40] == 2)
+        compare(dom, pts, w.cpu().numpy(), s, TOL_MIXED)
+    h.close()
+    # domain without loops: everything outside
+    empty = ws.make_domain([], eps=1e-9)
+    empty["cps"] = np.zeros((0, 2))
+    he = wn.Domain.from_dict(empty)
+    w, s = wn.query(he, torch.rand(700, 2, dtype=torch.float64, device="cuda"), precision=1)
+    assert torch.all(s == 0) and torch.all(w == 0)
+    he.close()
+
+
+def test_max_degree_and_periodic_outside_tile(wn):
+    rng = np.random.default_rng(3)
+    loop = ws.star_loop(rng, (0.5, 0.5), 0.3, 30, 7, ccw=True, bend=0.2)
+    dom = ws.make_domain([loop], eps=1e-9)
+    q = rng.uniform(0, 1, (3000, 2))
+    (w, s), = run(wn, [dom], [q], 1)
+    compare(dom, q, w, s, TOL_MIXED, closed=True)
+    doms, qs = ws.config3(n_faces=256, n_queries=256 * 2000, face_subset=[9, 10])
+    qs = [q + rng.integers(-3, 4, q.shape) * ws.TWO_PI for q in qs]
+    res = run(wn, doms, qs, 1)
+    for d, q, (w, s) in zip(doms, qs, res):
+        compare(d, q, w, s, TOL_MIXED)
+
+
+def test_host_buffers_match_device(wn):
+    doms, qs = ws.config2(n_domains=64, n_uniform=64 * 3000, n_near=64 * 300, domain_subset=range(3))
+    a = run(wn, doms, qs, 1, host=False)
+    b = run(wn, doms, qs, 1, host=True)
+    for (w1, s1), (w2, s2) in zip(a, b):
+        assert np.array_equal(s1, s2)
+        assert np.array_equal(np.nan_to_num(w1, nan=7.0), np.nan_to_num(w2, nan=7.0))
+
+
+def test_stats_and_profiling(wn):
+    doms, qs = ws.config2(n_domains=64, n_uniform=64 * 2000, n_near=64 * 500, domain_subset=range(2))
+    wn.set_profiling(True)
+    run(wn, doms, qs, 1)
+    t, n = wn.kernel_times()
+    wn.set_profiling(False)
+    st = wn.stats()
+    assert n == 1 and t["sweep"] > 0
+    assert st["queries"] == sum(len(q) for q in qs)
+    assert st["overflow"] == 0 and st["device_error"] == 0
