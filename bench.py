@@ -41,7 +41,11 @@ FLOPS_PER_PAIR = 34.0
 FP32_LANES_PER_SM = 128
 
 
-def workload(k):
+def workload(k, scale=1.0):
+    if k == 2 and scale != 1.0:
+        d, q = ws.config2(n_uniform=int(10_000_000 * scale), n_near=int(1_000_000 * scale))
+        return d, q, (f"workload 2 at {scale:g} of its queries (profiling case): 64 planar open/noisy domains, "
+                      f"{int(11_000_000 * scale)} queries")
     if k == 1:
         d, q = ws.config1()
         return [d], [q], "one planar [0,1]^2 domain: 64-cubic CCW star (C0) + two 16-cubic CW holes; 100k uniform + 10k near (1e-6) queries"
@@ -176,6 +180,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--qpt", type=int, default=0)
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the queries (profiling cases)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -197,7 +204,7 @@ def main():
     if args.qpt:
         wn.set_tuning(qpt=args.qpt)
 
-    doms, qs, desc = workload(args.workload)
+    doms, qs, desc = workload(args.workload, args.scale)
     handles = [wn.Domain.from_dict(d) for d in doms]
     dev = torch.device("cuda", local)
     grid = qs is None
@@ -299,7 +306,7 @@ def main():
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if not grid:
+    if not grid and not args.no_e2e:
         hp = torch.from_numpy(pts_h).pin_memory()
         hw = torch.empty(n_q, dtype=torch.float64).pin_memory()
         hs = torch.empty(n_q, dtype=torch.uint8).pin_memory()
@@ -317,7 +324,7 @@ def main():
     # oracle on the host cores: bounded sample, also a parity check of the timed results
     cpu = None
     parity = None
-    if rank == 0 and world == 1 and not grid:
+    if rank == 0 and world == 1 and not grid and not args.no_cpu:
         import oracle
         oracle.build()
         threads = os.cpu_count() or 1

@@ -69,7 +69,7 @@ struct DomDev {
     double ox, oy;              // origin of the FP32 coordinates
     double nx, ny, PP;          // family normal and Pu*Pv (bi-periodic)
     float M;                    // max |P - o|_inf over lifted control points
-    float Racc2;                // squared radius under which gap angles use FP64 deltas
+    float pad2;
     float Mq;                   // queries with |p' - o|_inf > Mq go to FP64
     float pad1;
     const int *seg_deg;         // [n_segs]
@@ -79,7 +79,7 @@ struct DomDev {
     const LoopDev *loops;       // [n_loops]
     const InstDev *inst;        // [n_inst]
     const PairDev *pairs;       // [n_pairs]
-    const float4 *rec;          // [3 * n_rec]
+    const float4 *rec;          // [4 * n_rec]: (a, b), (centre, R^2, flags), (gap, next), (b low)
     const int *rec_seg;         // [n_rec] segment, -1 for a closing chord
     const double2 *rec_a64;     // [n_rec] exact chord start
     const double2 *rec_b64;     // [n_rec] exact chord end

@@ -292,7 +292,14 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         uint32_t flb = fl;
         std::memcpy(&r1.w, &flb, 4);
         r2.x = f32(gx); r2.y = f32(gy); r2.z = f32(nxt[0] - ox); r2.w = f32(nxt[1] - oy);
-        rec.push_back(r0); rec.push_back(r1); rec.push_back(r2);
+        // low parts of the chord end and the next vertex: b - o = r0.zw + r3.xy and
+        // n - o = r2.zw + r3.zw to ~2^-48 relative
+        float4 r3;
+        r3.x = f32((b[0] - ox) - (double)r0.z);
+        r3.y = f32((b[1] - oy) - (double)r0.w);
+        r3.z = f32((nxt[0] - ox) - (double)r2.z);
+        r3.w = f32((nxt[1] - oy) - (double)r2.w);
+        rec.push_back(r0); rec.push_back(r1); rec.push_back(r2); rec.push_back(r3);
         rec_seg.push_back(seg);
         ra64.push_back(make_double2(a[0], a[1]));
         rb64.push_back(make_double2(b[0], b[1]));
@@ -343,7 +350,6 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     dv.nx = nx; dv.ny = ny; dv.PP = PP;
     dv.M = (float)M;
     dv.Mq = (float)Mq;
-    dv.Racc2 = (float)((0.04 * M) * (0.04 * M));
     dv.seg_deg = up.up(seg_deg);
     dv.seg_cp = up.up(seg_cp);
     dv.cp = up.up(P);

@@ -69,17 +69,66 @@ struct SweepArgs {
     unsigned int *counters;
 };
 
-// One record against one query: root step of Alg. 1 (circle prefilter of
-// the ellipse), chord crossing, gap crossing and gap angle.
+// Exact recomputation of one record's crossings and gap angle in FP64, for a
+// (query, record) whose FP32 error bands could not settle a sign.  Out of
+// line so that the FP64 instructions never issue on the fast path.
+__device__ __noinline__ void sweep_record_exact(int ridx, uint32_t fl, bool near,
+                                                const DomDev *__restrict__ Dp, double pxp,
+                                                double pyp, int &c, float &dth)
+{
+    const double2 a = Dp->rec_a64[ridx], b = Dp->rec_b64[ridx], n = Dp->rec_n64[ridx];
+    const bool sa = a.y > pyp, sb = b.y > pyp, sn = n.y > pyp;
+    c = 0;
+    dth = 0.f;
+    if (!near && sa != sb) {
+        const bool pos = exact_cross(a, b, pxp, pyp) > 0;
+        c = (!sa && sb && pos) ? 1 : ((sa && !sb && !pos) ? -1 : 0);
+    }
+    if (fl & RF_GAP) {
+        const double ux = b.x - pxp, uy = b.y - pyp, vx = n.x - pxp, vy = n.y - pyp;
+        const double d = ux * vy - uy * vx;
+        if (sb != sn) {
+            const bool pos = d > 0;
+            c += (!sb && sn && pos) ? 1 : ((sb && !sn && !pos) ? -1 : 0);
+        }
+        dth = (float)atan2(d, ux * vx + uy * vy);
+    }
+}
+
+__device__ __noinline__ float atan2_wide(float y, float x) { return atan2f(y, x); }
+
+// Signed angle atan2(y, x) of a gap seen from the query.  For |y| <= x/4 the
+// odd Gregory series of atan(t), t = y/x, truncated after t^11 (remainder
+// below t^13/13 < 5e-9 |t|); otherwise the library atan2f, out of line.
+__device__ __forceinline__ float gap_angle(float y, float x)
+{
+    if (fabsf(y) <= 0.25f * x) {
+        const float t = __fdividef(y, x);
+        const float t2 = t * t;
+        float p = -1.0f / 11.0f;
+        p = fmaf(p, t2, 1.0f / 9.0f);
+        p = fmaf(p, t2, -1.0f / 7.0f);
+        p = fmaf(p, t2, 1.0f / 5.0f);
+        p = fmaf(p, t2, -1.0f / 3.0f);
+        p = fmaf(p, t2, 1.0f);
+        return t * p;
+    }
+    return atan2_wide(y, x);
+}
+
+// One record against one query in FP32: the root step of Alg. 1 (circle
+// that contains the ellipse of Eq. 4 and the eps discs), the chord's
+// crossing of the +x ray from p, the gap chord's crossing and the gap angle.
+// `slow` is set when an error band cannot settle a sign; the caller then
+// redoes the record with sweep_record_exact.
 __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, const float4 R2,
-                                             int ridx, const DomDev *__restrict__ Dp, float fx,
-                                             float fy, float T, double pxp, double pyp,
-                                             float Racc2, int &c, float &dth, bool &near)
+                                             const float4 R3, float fx, float fy, float fxl,
+                                             float fyl, float T, int &c, float &dth, bool &near,
+                                             bool &slow)
 {
     const float uy = R0.y - fy, wy = R0.w - fy;
-    bool sa = uy > 0.f, sb = wy > 0.f;
-    if (fabsf(uy) <= T) sa = __ldg(&Dp->rec_a64[ridx].y) > pyp;
-    if (fabsf(wy) <= T) sb = __ldg(&Dp->rec_b64[ridx].y) > pyp;
+    const bool sa = uy > 0.f, sb = wy > 0.f;
+    slow = (fabsf(uy) <= T) | (fabsf(wy) <= T);
     const uint32_t fl = __float_as_uint(R1.w);
     const float wx = R0.z - fx;
     near = false;
@@ -94,39 +143,47 @@ __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, c
         const float D = fmaf(ux, wy, -uy * wx);
         const float TD = T * (fabsf(ux) + fabsf(uy) + fabsf(wx) + fabsf(wy)) +
                          kTwoM22 * (fabsf(ux * wy) + fabsf(uy * wx));
-        bool pos = D > 0.f;
-        if (fabsf(D) <= TD)
-            pos = exact_cross(__ldg(&Dp->rec_a64[ridx]), __ldg(&Dp->rec_b64[ridx]), pxp, pyp) > 0;
+        slow |= fabsf(D) <= TD;
+        const bool pos = D > 0.f;
         c = (!sa && sb && pos) ? 1 : ((sa && !sb && !pos) ? -1 : 0);
     }
     if (fl & RF_GAP) {
         const float gx = R2.x, gy = R2.y;
         const float ny = R2.w - fy;
-        bool sn = ny > 0.f;
-        if (fabsf(ny) <= T) sn = __ldg(&Dp->rec_n64[ridx].y) > pyp;
-        float bx = wx, by = wy;
-        if (fmaf(bx, bx, by * by) < Racc2) {
-            const double2 b = __ldg(&Dp->rec_b64[ridx]);
-            bx = (float)(b.x - pxp);
-            by = (float)(b.y - pyp);
-        }
-        const float Dg = fmaf(bx, gy, -by * gx);
+        const bool sn = ny > 0.f;
+        slow |= fabsf(ny) <= T;
+        // b - p and n - p from the hi/lo split of the points: each accurate to
+        // ~2^-23 relative, so no cancellation when the query is near b or n
+        const float bx = wx + (R3.x - fxl), by = wy + (R3.y - fyl);
+        const float vx = (R2.z - fx) + (R3.z - fxl), vy = ny + (R3.w - fyl);
+        // cross(b-p, n-p) = cross(b-p, g): use the short side for accuracy
+        const bool use_g = fmaf(gx, gx, gy * gy) <= fmaf(vx, vx, vy * vy);
+        const float ex = use_g ? gx : vx, ey = use_g ? gy : vy;
+        const float Dg = fmaf(bx, ey, -by * ex);
         if (sb != sn) {
-            const float TDg = T * (fabsf(gx) + fabsf(gy)) + kTwoM22 * (fabsf(bx * gy) + fabsf(by * gx));
-            bool pos = Dg > 0.f;
-            if (fabsf(Dg) <= TDg)
-                pos = exact_cross(__ldg(&Dp->rec_b64[ridx]), __ldg(&Dp->rec_n64[ridx]), pxp, pyp) > 0;
+            slow |= fabsf(Dg) <= 4.0f * kTwoM22 * (fabsf(bx) + fabsf(by)) * (fabsf(ex) + fabsf(ey));
+            const bool pos = Dg > 0.f;
             c += (!sb && sn && pos) ? 1 : ((sb && !sn && !pos) ? -1 : 0);
         }
-        const float dot = fmaf(bx, bx + gx, by * (by + gy));
-        dth = atan2f(Dg, dot);
+        dth = gap_angle(Dg, fmaf(bx, vx, by * vy));
     }
 }
 
-template <int QPT>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs A)
+// Compensated addition of a float into a (hi, lo) pair (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v)
 {
-    __shared__ float4 s_rec[3 * kChunk];
+    const float s = hi + v;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += err;
+}
+
+template <int QPT>
+__global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(const SweepArgs A)
+{
+    __shared__ float4 s_rec[4 * kChunk];
+    __shared__ double2 s_p[QPT][kSweepThreads];   // reduced queries (FP64), read on the slow paths
     __shared__ int s_unit;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -141,12 +198,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs A)
         const int4 U = __ldg(&A.units[u]);
         const DomDev *__restrict__ Dp = A.doms + U.x;
         const double Pu = Dp->Pu, Pv = Dp->Pv, ox = Dp->ox, oy = Dp->oy;
-        const float M = Dp->M, Mq = Dp->Mq, Racc2 = Dp->Racc2;
+        const float M = Dp->M, Mq = Dp->Mq;
         const int n_inst = Dp->n_inst;
         const float4 *__restrict__ rec = Dp->rec;
 
-        double px[QPT], py[QPT], pxp[QPT], pyp[QPT];
-        float fx[QPT], fy[QPT], T[QPT], th[QPT];
+        float fx[QPT], fy[QPT], fxl[QPT], fyl[QPT], T[QPT], th[QPT], thl[QPT];
         int acc[QPT];
         uint32_t fl[QPT];
         bool valid[QPT], inc[QPT];
@@ -156,10 +212,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs A)
             valid[k] = ql < U.z;
             double x = 0.0, y = 0.0;
             if (valid[k]) get_point(A.src, (uint32_t)(U.y + ql), x, y);
-            px[k] = reduce_period(x, Pu);
-            py[k] = reduce_period(y, Pv);
+            s_p[k][tid] = make_double2(reduce_period(x, Pu), reduce_period(y, Pv));
             acc[k] = 0;
             th[k] = 0.f;
+            thl[k] = 0.f;
             fl[k] = 0u;
         }
         for (int j = 0; j < n_inst; j++) {
@@ -168,21 +224,23 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs A)
             int any = 0;
 #pragma unroll
             for (int k = 0; k < QPT; k++) {
+                const double2 p = s_p[k][tid];
                 inc[k] = valid[k] && !(fl[k] & (QF_BOUNDARY | QF_ESCALATE)) &&
-                         inst_sees(*Dp, in, L, px[k], py[k]);
+                         inst_sees(*Dp, in, L, p.x, p.y);
                 if (in.type == IT_LINE) {
                     if (inc[k]) {
-                        const int s = line_side(*Dp, in, L, px[k], py[k]);
+                        const int s = line_side(*Dp, in, L, p.x, p.y);
                         if (s == 0) fl[k] |= QF_BOUNDARY;
                         acc[k] += s;
                     }
                     inc[k] = false;
                     continue;
                 }
-                pxp[k] = xsub(px[k], in.Tx);
-                pyp[k] = xsub(py[k], in.Ty);
-                fx[k] = (float)(pxp[k] - ox);
-                fy[k] = (float)(pyp[k] - oy);
+                const double dx = xsub(p.x, in.Tx) - ox, dy = xsub(p.y, in.Ty) - oy;
+                fx[k] = (float)dx;
+                fy[k] = (float)dy;
+                fxl[k] = (float)(dx - (double)fx[k]);
+                fyl[k] = (float)(dy - (double)fy[k]);
                 const float mag = fmaxf(fabsf(fx[k]), fabsf(fy[k]));
                 if (inc[k] && !(mag <= Mq)) {
                     fl[k] |= QF_ESCALATE;
@@ -194,22 +252,31 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs A)
             if (!__syncthreads_or(any)) continue;
             for (int r0 = in.r0; r0 < in.r1; r0 += kChunk) {
                 const int cnt = min(kChunk, in.r1 - r0);
-                for (int i = tid; i < 3 * cnt; i += kSweepThreads) s_rec[i] = __ldg(rec + 3 * r0 + i);
+                for (int i = tid; i < 4 * cnt; i += kSweepThreads) s_rec[i] = __ldg(rec + 4 * r0 + i);
                 __syncthreads();
+                float tc[QPT];
+#pragma unroll
+                for (int k = 0; k < QPT; k++) tc[k] = 0.f;
                 for (int r = 0; r < cnt; r++) {
-                    const float4 R0 = s_rec[3 * r], R1 = s_rec[3 * r + 1], R2 = s_rec[3 * r + 2];
+                    const float4 R0 = s_rec[4 * r], R1 = s_rec[4 * r + 1], R2 = s_rec[4 * r + 2],
+                                 R3 = s_rec[4 * r + 3];
                     bool nr[QPT];
                     bool any_near = false;
 #pragma unroll
                     for (int k = 0; k < QPT; k++) {
                         int c;
                         float dth;
-                        sweep_record(R0, R1, R2, r0 + r, Dp, fx[k], fy[k], T[k], pxp[k], pyp[k], Racc2,
-                                     c, dth, nr[k]);
+                        bool slow;
+                        sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], c, dth, nr[k], slow);
+                        if (slow && inc[k]) {
+                            const double2 p = s_p[k][tid];
+                            sweep_record_exact(r0 + r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
+                                               xsub(p.y, in.Ty), c, dth);
+                        }
                         nr[k] = nr[k] && inc[k];
                         if (inc[k]) {
                             acc[k] += 2 * c;
-                            th[k] += dth;
+                            tc[k] += dth;
                         }
                         any_near |= nr[k];
                     }
@@ -238,6 +305,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs A)
                         }
                     }
                 }
+#pragma unroll
+                for (int k = 0; k < QPT; k++) two_sum_add(th[k], thl[k], tc[k]);
                 __syncthreads();
             }
         }
@@ -246,7 +315,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs A)
             if (!valid[k]) continue;
             const uint32_t q = (uint32_t)(U.y + tid + k * kSweepThreads);
             A.acc2[q] = acc[k];
-            A.theta[q] = th[k];
+            A.theta[q] = th[k] + thl[k];
             A.flags[q] = fl[k];
         }
     }
@@ -427,7 +496,9 @@ __device__ void plain_query(const DomDev *Dp, double x0, double y0, double &om, 
             continue;
         }
         const double qx = xsub(x, in.Tx), qy = xsub(y, in.Ty);
-        for (int s = L.s0; s < L.s1 && !bnd; s++)
+        // the planar instance covers every loop of the domain
+        const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
+        for (int s = sb; s < se && !bnd; s++)
             bnd = alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]), __ldg(&Dp->seg_deg[s]),
                             __ldg(&Dp->seg_B[s]), qx, qy, eps, fa);
         if (in.type == IT_PE && !bnd) {
@@ -540,16 +611,71 @@ struct EscArgs {
     OutDst out;
 };
 
-__global__ void __launch_bounds__(128) k_f64query(const EscArgs A)
+// Plain FP64 recomputation of the escalated queries: one CTA per query, its
+// threads share the segments of every instance the query sees and reduce the
+// chord-angle sums (same arithmetic as k_plain, summed in another order).
+constexpr int kEscThreads = 128;
+
+__global__ void __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
 {
+    __shared__ double s_ang[kEscThreads];
+    __shared__ int s_bnd[kEscThreads];
+    const int tid = threadIdx.x;
     const unsigned n = A.counters[CNT_ESC];
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
         const uint2 e = A.esc[i];
-        double x, y, om;
-        int st;
-        get_point(A.src, e.x, x, y);
-        plain_query(A.doms + e.y, x, y, om, st);
-        write_out(A.out, e.x, om, st, true);
+        const DomDev *Dp = A.doms + e.y;
+        double x0, y0;
+        get_point(A.src, e.x, x0, y0);
+        const double x = reduce_period(x0, Dp->Pu), y = reduce_period(y0, Dp->Pv);
+        FarAngle fa;
+        long long half = 0;
+        bool bnd = false;
+        for (int j = 0; j < Dp->n_inst; j++) {
+            const InstDev in = Dp->inst[j];
+            const LoopDev &L = Dp->loops[in.loop];
+            if (!inst_sees(*Dp, in, L, x, y)) continue;
+            if (in.type == IT_LINE) {
+                if (tid == 0) {
+                    const int sd = line_side(*Dp, in, L, x, y);
+                    bnd |= sd == 0;
+                    half += sd;
+                }
+                continue;
+            }
+            const double qx = xsub(x, in.Tx), qy = xsub(y, in.Ty);
+            const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
+            for (int sg = sb + tid; sg < se && !bnd; sg += kEscThreads)
+                bnd |= alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[sg]), __ldg(&Dp->seg_deg[sg]),
+                                 __ldg(&Dp->seg_B[sg]), qx, qy, Dp->eps, fa);
+            if (in.type == IT_PE && tid == 0) {
+                const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
+                fa.ang -= atan2(ax * by - ay * bx, ax * bx + ay * by);
+            }
+        }
+        s_ang[tid] = fa.ang;
+        s_bnd[tid] = bnd ? 1 : 0;
+        __syncthreads();
+        for (int w = kEscThreads / 2; w > 0; w >>= 1) {
+            if (tid < w) {
+                s_ang[tid] += s_ang[tid + w];
+                s_bnd[tid] |= s_bnd[tid + w];
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            double om;
+            int st;
+            if (s_bnd[0]) {
+                om = __longlong_as_double(0x7ff8000000000000ULL);
+                st = 2;
+            } else {
+                om = s_ang[0] / kTwoPi + 0.5 * (double)half;
+                st = om >= 0.5 ? 1 : 0;
+            }
+            write_out(A.out, e.x, om, st, true);
+        }
+        __syncthreads();
     }
 }
 
@@ -678,7 +804,7 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     ea.esc = W.esc_q;
     ea.counters = W.counters;
     ea.out = out;
-    k_f64query<<<cfg.n_sm * 4, 128, 0, s>>>(ea);
+    k_f64query<<<cfg.n_sm * 2, kEscThreads, 0, s>>>(ea);
     mark(5);
     return cudaGetLastError();
 }
