@@ -195,6 +195,45 @@ wn_status wn_get_stats(wn_stats *out);
 wn_status wn_set_profiling(int32_t on);
 wn_status wn_kernel_times(double *ms5, int64_t *n_calls);
 
+/*
+ * wn_query_noalloc -- the WN_PREC_MIXED query of wn_query for one domain,
+ * without any memory allocation.  (The paper has no counterpart: this is a
+ * deployment variant of the same computation.)
+ *
+ * Some callers cannot let the library call cudaMalloc at query time: code
+ * running inside a custom device allocator or memory-pool callback (a nested
+ * allocation would re-enter the allocator), real-time or certified loops
+ * that forbid allocation once they have started, and processes held to a
+ * fixed device-memory budget.  This entry point keeps all of its scratch
+ * (per-query accumulators, the near-pair and FP64 queues, the work list)
+ * in one fixed-size device array that is part of the library image: every
+ * process that loads the library holds it (about 6.6 MB) on each device it
+ * uses, until it exits.  The call itself makes no cudaMalloc, cudaFree or
+ * other allocating call.
+ *
+ *   domain       from wn_create_domain (not modified).
+ *   points       DEVICE double[2n], x,y interleaved, 16-byte aligned.
+ *   n            0..WN_NOALLOC_MAX_QUERIES; larger n returns WN_ERR_LIMIT
+ *                (split the batch, or use wn_query).
+ *   out_winding  DEVICE double[n] or NULL; out_inside DEVICE uint8[n] or NULL
+ *                (same meaning as in wn_query).
+ *   stream       all work is queued on this stream; the call is asynchronous.
+ *
+ * Results equal wn_query(..., WN_PREC_MIXED, ...) on the same inputs.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call on a device shares the one array, and each call
+ * re-initialises what it needs, so calls that may overlap on the GPU (on
+ * different streams without ordering between them) race and give wrong
+ * results: order them on one stream, or with events.
+ * Errors: WN_ERR_ARG (NULL domain, n < 0, host or misaligned pointers),
+ * WN_ERR_LIMIT (n too large), WN_ERR_CUDA.  No message is recorded for
+ * wn_last_error (recording one could allocate host memory).
+ */
+#define WN_NOALLOC_MAX_QUERIES 65536
+wn_status wn_query_noalloc(const wn_domain *domain, const double *points, int64_t n,
+                           double *out_winding, uint8_t *out_inside, wn_stream stream);
+
 /* Thread-local description of the last failure ("" when none). */
 const char *wn_last_error(void);
 

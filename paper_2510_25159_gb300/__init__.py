@@ -63,6 +63,8 @@ def lib():
         L.wn_get_stats.argtypes = [ctypes.POINTER(WnStats)]
         L.wn_last_error.restype = ctypes.c_char_p
         L.wn_version.restype = ctypes.c_char_p
+        L.wn_query_noalloc.argtypes = [P, P, I64, P, P, P]
+        L.wn_query_noalloc.restype = ctypes.c_int
         L.wn_set_profiling.argtypes = [I32]
         L.wn_kernel_times.argtypes = [P, P]
         for f in ("wn_create_domain", "wn_query", "wn_query_batched", "wn_query_grid_bitmask",
@@ -143,6 +145,17 @@ def query(domain, points, precision=MIXED, out_winding=None, out_inside=None, st
     _check(lib().wn_query(domain.handle, _ptr(points), n, _ptr(out_winding), _ptr(out_inside),
                           int(precision), _stream(stream)))
     return out_winding, out_inside
+
+
+NOALLOC_MAX_QUERIES = 65536
+
+
+def query_noalloc(domain, points, out_winding, out_inside, stream=None):
+    """``wn_query_noalloc``: the mixed query of one domain with no memory
+    allocation by the library (device tensors only, at most
+    NOALLOC_MAX_QUERIES points).  Returns the status code."""
+    return int(lib().wn_query_noalloc(domain.handle, _ptr(points), int(points.shape[0]),
+                                      _ptr(out_winding), _ptr(out_inside), _stream(stream)))
 
 
 def query_batched(domains, points, offsets, precision=MIXED, out_winding=None, out_inside=None,
