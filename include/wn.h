@@ -158,15 +158,22 @@ wn_status wn_query_grid_bitmask(const wn_domain *domain, int32_t nu, int32_t nv,
                                 wn_stream stream);
 
 /*
- * Tuning knobs of the mixed path (0 keeps the current value):
+ * Tuning knobs of the mixed path (0 keeps the current value for the first
+ * three, a negative value keeps it for the last three):
  *   tile_queries_per_thread  1, 2 or 4 queries per sweep thread
  *   sweep_ctas_per_sm        persistent sweep CTAs per SM (1..8)
  *   near_ctas_per_sm         near-pair kernel CTAs per SM (1..16)
  *   use_graph                1 = capture each distinct batched call in a CUDA
  *                            graph and replay it; 0 = plain launches
+ *   tree                     1 = sweep record clusters (gap angles of far
+ *                            clusters from their series expansion); 0 = sweep
+ *                            every record for every query
+ *   bucket                   1 = order the queries by spatial cell before the
+ *                            sweep (results do not depend on it)
  */
 wn_status wn_set_tuning(int32_t tile_queries_per_thread, int32_t sweep_ctas_per_sm,
-                        int32_t near_ctas_per_sm, int32_t use_graph);
+                        int32_t near_ctas_per_sm, int32_t use_graph, int32_t tree,
+                        int32_t bucket);
 
 /* Counters of the last mixed call on this thread's device, read after the
  * stream is synchronised: queries, near pairs, pairs escalated to FP64,
@@ -188,12 +195,12 @@ wn_status wn_get_stats(wn_stats *out);
  * kernels on the call's own stream (so the times are those of the stream the
  * kernels run on); on == 0 stops recording and drops what was recorded.
  * wn_kernel_times synchronises the device, writes the summed milliseconds of
- * the five kernels [sweep, near pairs FP32, pairs FP64, finalize, queries
- * FP64] into ms5 (host double[5]) and the number of recorded calls into
- * *n_calls, then clears the record.
+ * the six stages [query bucketing (3 kernels), sweep, near pairs FP32, pairs
+ * FP64, finalize, queries FP64] into ms6 (host double[6]) and the number of
+ * recorded calls into *n_calls, then clears the record.
  */
 wn_status wn_set_profiling(int32_t on);
-wn_status wn_kernel_times(double *ms5, int64_t *n_calls);
+wn_status wn_kernel_times(double *ms6, int64_t *n_calls);
 
 /*
  * wn_query_noalloc -- the WN_PREC_MIXED query of wn_query for one domain,

@@ -59,7 +59,7 @@ def lib():
         L.wn_query.argtypes = [P, P, I64, P, P, ctypes.c_int, P]
         L.wn_query_batched.argtypes = [P, I32, P, P, P, P, ctypes.c_int, P]
         L.wn_query_grid_bitmask.argtypes = [P, I32, I32, P, P, ctypes.c_int, P]
-        L.wn_set_tuning.argtypes = [I32, I32, I32, I32]
+        L.wn_set_tuning.argtypes = [I32, I32, I32, I32, I32, I32]
         L.wn_get_stats.argtypes = [ctypes.POINTER(WnStats)]
         L.wn_last_error.restype = ctypes.c_char_p
         L.wn_version.restype = ctypes.c_char_p
@@ -189,8 +189,9 @@ def query_grid_bitmask(domain, nu, nv, precision=MIXED, stream=None):
     return bits, nb
 
 
-def set_tuning(qpt=0, sweep_ctas_per_sm=0, near_ctas_per_sm=0, use_graph=-1):
-    _check(lib().wn_set_tuning(int(qpt), int(sweep_ctas_per_sm), int(near_ctas_per_sm), int(use_graph)))
+def set_tuning(qpt=0, sweep_ctas_per_sm=0, near_ctas_per_sm=0, use_graph=-1, tree=-1, bucket=-1):
+    _check(lib().wn_set_tuning(int(qpt), int(sweep_ctas_per_sm), int(near_ctas_per_sm), int(use_graph),
+                               int(tree), int(bucket)))
 
 
 def stats():
@@ -199,7 +200,7 @@ def stats():
     return {k: getattr(s, k) for k, _ in WnStats._fields_}
 
 
-KERNELS = ("sweep", "near_fp32", "pairs_fp64", "finalize", "queries_fp64")
+KERNELS = ("bucket", "sweep", "near_fp32", "pairs_fp64", "finalize", "queries_fp64")
 
 
 def set_profiling(on=True):
@@ -209,7 +210,7 @@ def set_profiling(on=True):
 def kernel_times():
     """Summed device milliseconds per mixed-path kernel since the last read,
     and the number of calls they cover."""
-    ms = np.zeros(5)
+    ms = np.zeros(len(KERNELS))
     n = np.zeros(1, dtype=np.int64)
     _check(lib().wn_kernel_times(_ptr(ms), _ptr(n)))
     return dict(zip(KERNELS, ms.tolist())), int(n[0])

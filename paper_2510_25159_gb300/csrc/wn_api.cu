@@ -121,6 +121,12 @@ cudaError_t ensure_work(Work &W, int64_t n)
     if ((e = grow(W.near_items, W.cap_near, need_near)) != cudaSuccess) return e;
     const int64_t need_f64 = std::max<int64_t>(1 << 18, nq / 8);
     if ((e = grow(W.f64_items, W.cap_f64, need_f64)) != cudaSuccess) return e;
+    if (nq > W.cap_bin_q || !W.perm) {
+        int64_t c0 = W.cap_bin_q, c1 = W.cap_bin_q;
+        if ((e = grow(W.cell_of, c0, nq)) != cudaSuccess) return e;
+        if ((e = grow(W.perm, c1, nq)) != cudaSuccess) return e;
+        W.cap_bin_q = nq;
+    }
     return cudaSuccess;
 }
 
@@ -172,7 +178,7 @@ void wn_destroy_domain(wn_domain *d)
 }
 
 wn_status wn_set_tuning(int32_t qpt, int32_t sweep_ctas_per_sm, int32_t near_ctas_per_sm,
-                        int32_t use_graph)
+                        int32_t use_graph, int32_t tree, int32_t bucket)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     if (qpt != 0 && qpt != 1 && qpt != 2 && qpt != 4) return fail(WN_ERR_ARG, "qpt must be 1, 2 or 4");
@@ -182,6 +188,8 @@ wn_status wn_set_tuning(int32_t qpt, int32_t sweep_ctas_per_sm, int32_t near_cta
     if (sweep_ctas_per_sm) g_tun.sweep_ctas_per_sm = sweep_ctas_per_sm;
     if (near_ctas_per_sm) g_tun.near_ctas_per_sm = near_ctas_per_sm;
     if (use_graph >= 0) g_tun.use_graph = use_graph;
+    if (tree >= 0) g_tun.tree = tree != 0;
+    if (bucket >= 0) g_tun.bucket = bucket != 0;
     return WN_OK;
 }
 
@@ -302,6 +310,35 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             if ((e = cudaMemcpy(S->W.offsets, offsets, (n_domains + 1) * sizeof(int64_t),
                                 cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cuda_fail(e, "upload offsets");
+            // spatial buckets: about 256 queries per cell, cells over the domain's
+            // box (the base tile on periodic axes)
+            std::vector<int4> dcell(n_domains);
+            std::vector<float4> dbox(n_domains);
+            int64_t ncell = 0;
+            for (int d = 0; d < n_domains; d++) {
+                const DomDev &dv = domains[d]->dev;
+                const int64_t cnt = offsets[d + 1] - offsets[d];
+                const int G = (int)std::max<double>(1.0, std::floor(std::sqrt((double)cnt / 256.0)));
+                const double x0 = dv.Pu > 0 ? 0.0 : dv.ox - dv.M, wx = dv.Pu > 0 ? dv.Pu : 2.0 * dv.M;
+                const double y0 = dv.Pv > 0 ? 0.0 : dv.oy - dv.M, wy = dv.Pv > 0 ? dv.Pv : 2.0 * dv.M;
+                dcell[d] = make_int4((int)ncell, G, 0, 0);
+                dbox[d] = make_float4((float)x0, (float)y0, (float)(G / wx), (float)(G / wy));
+                ncell += (int64_t)G * G;
+            }
+            if (ncell > INT32_MAX) return fail(WN_ERR_LIMIT, "too many query cells");
+            {
+                int64_t c1 = S->W.cap_dbin, c2 = S->W.cap_dbin;
+                if ((e = grow(S->W.dcell, c1, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
+                if ((e = grow(S->W.dbox, c2, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
+                S->W.cap_dbin = std::min(c1, c2);
+            }
+            if ((e = grow(S->W.cell_cnt, S->W.cap_cells, ncell)) != cudaSuccess) return cuda_fail(e, "cells");
+            S->W.n_cells = (int)ncell;
+            if ((e = cudaMemcpy(S->W.dcell, dcell.data(), n_domains * sizeof(int4), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess ||
+                (e = cudaMemcpy(S->W.dbox, dbox.data(), n_domains * sizeof(float4), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                return cuda_fail(e, "upload cells");
             S->key_doms.assign(domains, domains + n_domains);
             S->key_offsets.assign(offsets, offsets + n_domains + 1);
             S->key_qpt = qpt;
@@ -377,23 +414,25 @@ wn_status wn_set_profiling(int32_t on)
     return WN_OK;
 }
 
-wn_status wn_kernel_times(double *ms5, int64_t *n_calls)
+wn_status wn_kernel_times(double *ms6, int64_t *n_calls)
 {
-    if (!ms5) return fail(WN_ERR_ARG, "ms5 is NULL");
+    if (!ms6) return fail(WN_ERR_ARG, "ms6 is NULL");
     std::lock_guard<std::mutex> lk(g_mu);
     wn_status st;
     DevState *S = dev_state(st);
     if (!S) return st;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "synchronize");
-    for (int k = 0; k < 5; k++) ms5[k] = 0.0;
-    const size_t calls = S->events.size() / 6;
+    const int ni = kProfEvents - 1;
+    for (int k = 0; k < ni; k++) ms6[k] = 0.0;
+    const size_t calls = S->events.size() / kProfEvents;
     for (size_t c = 0; c < calls; c++)
-        for (int k = 0; k < 5; k++) {
+        for (int k = 0; k < ni; k++) {
             float ms = 0.f;
-            if ((e = cudaEventElapsedTime(&ms, S->events[6 * c + k], S->events[6 * c + k + 1])) != cudaSuccess)
+            if ((e = cudaEventElapsedTime(&ms, S->events[kProfEvents * c + k],
+                                          S->events[kProfEvents * c + k + 1])) != cudaSuccess)
                 return cuda_fail(e, "cudaEventElapsedTime");
-            ms5[k] += ms;
+            ms6[k] += ms;
         }
     if (n_calls) *n_calls = (int64_t)calls;
     for (cudaEvent_t ev : S->events) cudaEventDestroy(ev);

@@ -50,6 +50,7 @@ struct InstDev {
     int pair;                   // bi-periodic pair for the family window, -1 none
     int axes;                   // IT_BOX: bit0 window x, bit1 window y
     int r0, r1;                 // FP32 records swept for this instance
+    int c0, c1;                 // record clusters covering [r0, r1)
     double Tx, Ty;              // query shift: p' = p - (Tx, Ty)
     double Fx, Fy;              // family shift for the slab / line: x_f = p - (Fx, Fy)
     long long I, J;             // lattice units of (Fx, Fy)
@@ -84,7 +85,26 @@ struct DomDev {
     const double2 *rec_a64;     // [n_rec] exact chord start
     const double2 *rec_b64;     // [n_rec] exact chord end
     const double2 *rec_n64;     // [n_rec] exact next vertex
+    const float4 *clu;          // [kCluF4 * n_clusters] record clusters, see below
+    int n_clusters, pad3;
 };
+
+// Record clusters: runs of at most kCluRecs consecutive records of one loop.
+// Per cluster, kCluF4 float4 (FP32, relative to the domain origin):
+//   [0] near box (xmin, xmax, ymin, ymax): outside it, by the query's error
+//       band, a query is outside every record's circle (so far from every
+//       segment's ellipse and eps discs);
+//   [1] (ymin, ymax, xmax) of every vertex of its pieces, and (rho r_c)^2;
+//   [2] expansion centre z_c, hi and lo parts;
+//   [3] (r_c, gap flag, first record, end record) -- the last two as int bits;
+//   [4 ..] kCluTerms complex coefficients c_k of the Laurent expansion of the
+//       sum of the cluster's gap angles:
+//         sum_gaps theta = Im sum_k c_k w^k,   w = r_c / (z_c - p),
+//       valid for |z_c - p| >= rho r_c.
+constexpr int kCluRecs = 16;
+constexpr int kCluTerms = 12;
+constexpr int kCluF4 = 4 + kCluTerms / 2;
+constexpr double kCluRho = 4.0;
 
 // Near / FP64 work item.
 struct Item {

@@ -47,6 +47,14 @@ struct Work {
     int4 *units = nullptr;     // (dom, q0, count, 0)
     DomDev *doms = nullptr;
     int64_t *offsets = nullptr;  // device copy of point offsets
+    // spatial bucketing of the queries (null: sweep in input order)
+    int *cell_of = nullptr;    // per query
+    int *perm = nullptr;       // per query
+    int *cell_cnt = nullptr;   // per cell
+    int4 *dcell = nullptr;     // per domain: first cell, G
+    float4 *dbox = nullptr;    // per domain: x0, y0, G / width, G / height
+    int n_cells = 0;
+    int64_t cap_bin_q = 0, cap_cells = 0, cap_dbin = 0;
     int64_t cap_q = 0, cap_near = 0, cap_f64 = 0, cap_units = 0, cap_doms = 0, cap_off = 0;
 };
 
@@ -58,12 +66,16 @@ struct Tuning {
     int sweep_ctas_per_sm = 4;
     int near_ctas_per_sm = 8;
     int use_graph = 0;
+    int tree = 1;              // 1: cluster sweep with gap-angle expansions; 0: flat sweep
+    int bucket = 1;            // 1: bucket queries spatially before the sweep
 };
+
+constexpr int kProfEvents = 7;   // events per profiled mixed call (6 intervals)
 
 struct LaunchCfg {
     int n_sm;
     Tuning tun;
-    std::vector<cudaEvent_t> *events;  // non-null: record 6 events per call around the kernels
+    std::vector<cudaEvent_t> *events;  // non-null: record kProfEvents events per call
 };
 
 // Kernels (wn_kernels.cu)

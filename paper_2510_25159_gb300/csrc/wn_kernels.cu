@@ -60,6 +60,7 @@ struct SweepArgs {
     const DomDev *doms;
     const int4 *units;
     int n_units;
+    const int *perm;            // position -> query index (spatially bucketed), or null
     PointSrc src;
     int32_t *acc2;
     float *theta;
@@ -177,6 +178,362 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v)
     const float err = (hi - (s - bb)) + (v - bb);
     hi = s;
     lo += err;
+}
+
+// Crossings only (chord and gap chord) of one record, for a query known to be
+// outside every circle of the record's cluster.
+__device__ __forceinline__ void sweep_record_cross(const float4 R0, const float4 R1, const float4 R2,
+                                                   float fx, float fy, float T, int &c, bool &slow)
+{
+    const float uy = R0.y - fy, wy = R0.w - fy;
+    const bool sa = uy > 0.f, sb = wy > 0.f;
+    slow = (fabsf(uy) <= T) | (fabsf(wy) <= T);
+    const uint32_t fl = __float_as_uint(R1.w);
+    const float wx = R0.z - fx;
+    c = 0;
+    if (sa != sb) {
+        const float ux = R0.x - fx;
+        const float D = fmaf(ux, wy, -uy * wx);
+        const float TD = T * (fabsf(ux) + fabsf(uy) + fabsf(wx) + fabsf(wy)) +
+                         kTwoM22 * (fabsf(ux * wy) + fabsf(uy * wx));
+        slow |= fabsf(D) <= TD;
+        const bool pos = D > 0.f;
+        c = (!sa && sb && pos) ? 1 : ((sa && !sb && !pos) ? -1 : 0);
+    }
+    if (fl & RF_GAP) {
+        const float ny = R2.w - fy;
+        const bool sn = ny > 0.f;
+        slow |= fabsf(ny) <= T;
+        if (sb != sn) {
+            const float vx = R2.z - fx;
+            const float Dg = fmaf(wx, ny, -wy * vx);
+            const float TDg = T * (fabsf(wx) + fabsf(wy) + fabsf(vx) + fabsf(ny)) +
+                              kTwoM22 * (fabsf(wx * ny) + fabsf(wy * vx));
+            slow |= fabsf(Dg) <= TDg;
+            const bool pos = Dg > 0.f;
+            c += (!sb && sn && pos) ? 1 : ((sb && !sn && !pos) ? -1 : 0);
+        }
+    }
+}
+
+// Sum of a cluster's gap angles at the query from its Laurent expansion
+// (valid at |z_c - p| >= rho r_c): Im sum_k c_k w^k, w = r_c / (z_c - p).
+__device__ __forceinline__ float cluster_gap_sum(const float4 *__restrict__ C, float fx, float fy,
+                                                 float fxl, float fyl)
+{
+    const float dx = (C[2].x - fx) + (C[2].z - fxl);
+    const float dy = (C[2].y - fy) + (C[2].w - fyl);
+    const float inv = __fdividef(C[3].x, fmaf(dx, dx, dy * dy));
+    const float wr = dx * inv, wi = -dy * inv;
+    const float *cf = reinterpret_cast<const float *>(C + 4);
+    float sr = cf[2 * (kCluTerms - 1)], si = cf[2 * (kCluTerms - 1) + 1];
+#pragma unroll
+    for (int k = kCluTerms - 2; k >= 0; k--) {
+        const float tr = fmaf(sr, wr, fmaf(-si, wi, cf[2 * k]));
+        const float ti = fmaf(sr, wi, fmaf(si, wr, cf[2 * k + 1]));
+        sr = tr;
+        si = ti;
+    }
+    return fmaf(sr, wi, si * wr);
+}
+
+constexpr int kChunkClu = 4;                            // clusters per shared-memory stage
+constexpr int kChunkRecs = kChunkClu * kCluRecs;
+
+// Tree sweep.  Per (query, cluster): outside the cluster's near box and at
+// least rho r_c away, the gap angles come from the cluster's expansion and
+// only crossings need the records (and only when the query's +x ray can
+// meet the cluster); otherwise the records are swept in full.  The choice
+// is made per query, so results do not depend on which queries share a
+// tile; tiles of spatially bucketed queries let whole warps skip clusters.
+template <int QPT>
+__global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep_tree(const SweepArgs A)
+{
+    __shared__ float4 s_rec[4 * kChunkRecs];
+    __shared__ float4 s_clu[kCluF4 * kChunkClu];
+    __shared__ double2 s_p[QPT][kSweepThreads];
+    __shared__ int s_unit;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[CNT_UNIT], 1u);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= A.n_units) return;
+        const int4 U = __ldg(&A.units[u]);
+        const DomDev *__restrict__ Dp = A.doms + U.x;
+        const double Pu = Dp->Pu, Pv = Dp->Pv, ox = Dp->ox, oy = Dp->oy;
+        const float M = Dp->M, Mq = Dp->Mq;
+        const int n_inst = Dp->n_inst;
+        const float4 *__restrict__ rec = Dp->rec;
+        const float4 *__restrict__ clu = Dp->clu;
+
+        float fx[QPT], fy[QPT], fxl[QPT], fyl[QPT], T[QPT], th[QPT], thl[QPT];
+        int acc[QPT];
+        uint32_t fl[QPT], qid[QPT];
+        bool valid[QPT], inc[QPT];
+#pragma unroll
+        for (int k = 0; k < QPT; k++) {
+            const int ql = tid + k * kSweepThreads;
+            valid[k] = ql < U.z;
+            qid[k] = 0;
+            double x = 0.0, y = 0.0;
+            if (valid[k]) {
+                qid[k] = A.perm ? (uint32_t)__ldg(&A.perm[U.y + ql]) : (uint32_t)(U.y + ql);
+                get_point(A.src, qid[k], x, y);
+            }
+            s_p[k][tid] = make_double2(reduce_period(x, Pu), reduce_period(y, Pv));
+            acc[k] = 0;
+            th[k] = 0.f;
+            thl[k] = 0.f;
+            fl[k] = 0u;
+        }
+        for (int j = 0; j < n_inst; j++) {
+            const InstDev in = Dp->inst[j];
+            const LoopDev &L = Dp->loops[in.loop];
+            int any = 0;
+#pragma unroll
+            for (int k = 0; k < QPT; k++) {
+                const double2 p = s_p[k][tid];
+                inc[k] = valid[k] && !(fl[k] & (QF_BOUNDARY | QF_ESCALATE)) && inst_sees(*Dp, in, L, p.x, p.y);
+                if (in.type == IT_LINE) {
+                    if (inc[k]) {
+                        const int sd = line_side(*Dp, in, L, p.x, p.y);
+                        if (sd == 0) fl[k] |= QF_BOUNDARY;
+                        acc[k] += sd;
+                    }
+                    inc[k] = false;
+                    continue;
+                }
+                const double dx = xsub(p.x, in.Tx) - ox, dy = xsub(p.y, in.Ty) - oy;
+                fx[k] = (float)dx;
+                fy[k] = (float)dy;
+                fxl[k] = (float)(dx - (double)fx[k]);
+                fyl[k] = (float)(dy - (double)fy[k]);
+                const float mag = fmaxf(fabsf(fx[k]), fabsf(fy[k]));
+                if (inc[k] && !(mag <= Mq)) {
+                    fl[k] |= QF_ESCALATE;
+                    inc[k] = false;
+                }
+                T[k] = kTwoM22 * (M + mag);
+                any |= inc[k];
+            }
+            if (!__syncthreads_or(any)) continue;
+            for (int cb = in.c0; cb < in.c1; cb += kChunkClu) {
+                const int ncl = min(kChunkClu, in.c1 - cb);
+                for (int i = tid; i < kCluF4 * ncl; i += kSweepThreads) s_clu[i] = __ldg(clu + kCluF4 * cb + i);
+                __syncthreads();
+                // per-query decisions for the clusters of this stage
+                uint32_t nfull[QPT], ncross[QPT], mpm[QPT];
+                float tc[QPT];
+                int need = 0;
+#pragma unroll
+                for (int k = 0; k < QPT; k++) {
+                    nfull[k] = ncross[k] = mpm[k] = 0u;
+                    tc[k] = 0.f;
+                }
+                for (int c = 0; c < ncl; c++) {
+                    const float4 *C = s_clu + kCluF4 * c;
+                    const float4 nb = C[0], yx = C[1];
+                    const bool gaps = C[3].y != 0.f;
+#pragma unroll
+                    for (int k = 0; k < QPT; k++) {
+                        const bool outside = (fx[k] < nb.x - T[k]) | (fx[k] > nb.y + T[k]) |
+                                             (fy[k] < nb.z - T[k]) | (fy[k] > nb.w + T[k]);
+                        const bool cross = !((fy[k] > yx.y + T[k]) | (fy[k] < yx.x - T[k]) | (fx[k] > yx.z + T[k]));
+                        bool mp = outside;
+                        if (gaps && outside) {
+                            const float dx = (C[2].x - fx[k]) + (C[2].z - fxl[k]);
+                            const float dy = (C[2].y - fy[k]) + (C[2].w - fyl[k]);
+                            mp = fmaf(dx, dx, dy * dy) >= yx.w;
+                        }
+                        if (inc[k]) {
+                            if (!mp) nfull[k] |= 1u << c;
+                            else mpm[k] |= 1u << c;
+                            if (cross) ncross[k] |= 1u << c;
+                        }
+                    }
+                    if (gaps) {
+#pragma unroll
+                        for (int k = 0; k < QPT; k++)
+                            if (inc[k] && (mpm[k] >> c & 1u)) tc[k] += cluster_gap_sum(C, fx[k], fy[k], fxl[k], fyl[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < QPT; k++) need |= (int)(nfull[k] | ncross[k]);
+                if (__syncthreads_or(need)) {
+                    const int rb = __float_as_int(s_clu[3].z);
+                    const int re = __float_as_int(s_clu[kCluF4 * (ncl - 1) + 3].w);
+                    for (int i = tid; i < 4 * (re - rb); i += kSweepThreads) s_rec[i] = __ldg(rec + 4 * rb + i);
+                    __syncthreads();
+                    for (int c = 0; c < ncl; c++) {
+                        uint32_t wf = 0, wc = 0;
+#pragma unroll
+                        for (int k = 0; k < QPT; k++) {
+                            wf |= nfull[k];
+                            wc |= ncross[k];
+                        }
+                        wf = __reduce_or_sync(0xffffffffu, wf) >> c & 1u;
+                        wc = __reduce_or_sync(0xffffffffu, wc) >> c & 1u;
+                        if (!wf && !wc) continue;
+                        const int r0 = __float_as_int(s_clu[kCluF4 * c + 3].z);
+                        const int r1 = __float_as_int(s_clu[kCluF4 * c + 3].w);
+                        for (int r = r0; r < r1; r++) {
+                            const int sr = r - rb;
+                            const float4 R0 = s_rec[4 * sr], R1 = s_rec[4 * sr + 1], R2 = s_rec[4 * sr + 2];
+                            if (wf) {
+                                const float4 R3 = s_rec[4 * sr + 3];
+                                bool nr[QPT];
+                                bool any_near = false;
+#pragma unroll
+                                for (int k = 0; k < QPT; k++) {
+                                    int cc;
+                                    float dth;
+                                    bool slow;
+                                    sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, nr[k], slow);
+                                    if (slow && inc[k]) {
+                                        const double2 p = s_p[k][tid];
+                                        sweep_record_exact(r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
+                                                           xsub(p.y, in.Ty), cc, dth);
+                                    }
+                                    nr[k] = nr[k] && inc[k];
+                                    if (inc[k]) {
+                                        acc[k] += 2 * cc;
+                                        if (nfull[k] >> c & 1u) tc[k] += dth;
+                                    }
+                                    any_near |= nr[k];
+                                }
+                                if (__any_sync(0xffffffffu, any_near)) {
+#pragma unroll
+                                    for (int k = 0; k < QPT; k++) {
+                                        const unsigned m = __ballot_sync(0xffffffffu, nr[k]);
+                                        if (!m) continue;
+                                        const int leader = __ffs(m) - 1;
+                                        unsigned base = 0;
+                                        if (lane == leader) base = atomicAdd(&A.counters[CNT_NEAR], (unsigned)__popc(m));
+                                        base = __shfl_sync(0xffffffffu, base, leader);
+                                        if (nr[k]) {
+                                            const unsigned long long idx = (unsigned long long)base + __popc(m & lt_mask);
+                                            if (idx < (unsigned long long)A.cap_near) {
+                                                Item it;
+                                                it.q = qid[k];
+                                                it.dom = (uint32_t)U.x;
+                                                it.inst = (uint32_t)j;
+                                                it.rec = (uint32_t)r;
+                                                A.near_items[idx] = it;
+                                            } else {
+                                                fl[k] |= QF_ESCALATE;
+                                            }
+                                        }
+                                    }
+                                }
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < QPT; k++) {
+                                    int cc;
+                                    bool slow;
+                                    sweep_record_cross(R0, R1, R2, fx[k], fy[k], T[k], cc, slow);
+                                    if (slow && inc[k]) {
+                                        const double2 p = s_p[k][tid];
+                                        float dth;
+                                        sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
+                                                           xsub(p.y, in.Ty), cc, dth);
+                                    }
+                                    if (inc[k]) acc[k] += 2 * cc;
+                                }
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < QPT; k++) two_sum_add(th[k], thl[k], tc[k]);
+                __syncthreads();
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < QPT; k++) {
+            if (!valid[k]) continue;
+            A.acc2[qid[k]] = acc[k];
+            A.theta[qid[k]] = th[k] + thl[k];
+            A.flags[qid[k]] = fl[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ spatial bucketing
+// Queries of each domain are counted into a G x G grid of cells over the
+// domain's box and scattered cell by cell, so that a sweep tile covers a
+// small area.  Only the order of work changes: every query's arithmetic is
+// the same in any order.
+struct BinArgs {
+    const DomDev *doms;
+    const int4 *units;
+    int n_units;
+    PointSrc src;
+    const int4 *dcell;          // per domain: first cell, G
+    const float4 *dbox;         // per domain: x0, y0, G / width, G / height
+    int *cell_of;               // per query
+    int *cnt;                   // per cell: count, then cursor
+    int *perm;
+    int n_cells;
+};
+
+__global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
+{
+    const int4 U = A.units[blockIdx.x];
+    const DomDev *Dp = A.doms + U.x;
+    const int4 dc = A.dcell[U.x];
+    const float4 bx = A.dbox[U.x];
+    for (int i = threadIdx.x; i < U.z; i += blockDim.x) {
+        const uint32_t q = (uint32_t)(U.y + i);
+        double x, y;
+        get_point(A.src, q, x, y);
+        x = reduce_period(x, Dp->Pu);
+        y = reduce_period(y, Dp->Pv);
+        int cx = (int)floorf(((float)x - bx.x) * bx.z), cy = (int)floorf(((float)y - bx.y) * bx.w);
+        cx = min(max(cx, 0), dc.y - 1);
+        cy = min(max(cy, 0), dc.y - 1);
+        const int cell = dc.x + cy * dc.y + ((cy & 1) ? dc.y - 1 - cx : cx);
+        A.cell_of[q] = cell;
+        atomicAdd(&A.cnt[cell], 1);
+    }
+}
+
+// Exclusive scan of the cell counts in one CTA.
+__global__ void __launch_bounds__(1024) k_bin_scan(const BinArgs A)
+{
+    __shared__ int s_sum[1024];
+    const int t = threadIdx.x;
+    const int per = (A.n_cells + 1023) / 1024;
+    const int b = t * per, e = min(b + per, A.n_cells);
+    int sum = 0;
+    for (int i = b; i < e; i++) sum += A.cnt[i];
+    s_sum[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int v = t >= off ? s_sum[t - off] : 0;
+        __syncthreads();
+        s_sum[t] += v;
+        __syncthreads();
+    }
+    int run = s_sum[t] - sum;
+    for (int i = b; i < e; i++) {
+        const int c = A.cnt[i];
+        A.cnt[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bin_scatter(const BinArgs A)
+{
+    const int4 U = A.units[blockIdx.x];
+    for (int i = threadIdx.x; i < U.z; i += blockDim.x) {
+        const int q = U.y + i;
+        A.perm[atomicAdd(&A.cnt[A.cell_of[q]], 1)] = q;
+    }
 }
 
 template <int QPT>
@@ -738,9 +1095,9 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
 {
     cudaError_t e = cudaMemsetAsync(W.counters, 0, CNT_N * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    cudaEvent_t ev[6] = {};
+    cudaEvent_t ev[kProfEvents] = {};
     if (cfg.events) {
-        for (int i = 0; i < 6; i++) {
+        for (int i = 0; i < kProfEvents; i++) {
             if ((e = cudaEventCreate(&ev[i])) != cudaSuccess) return e;
             cfg.events->push_back(ev[i]);
         }
@@ -752,10 +1109,31 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
         e = cudaMemsetAsync(out.nbound, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
+    const bool bucket = cfg.tun.tree && cfg.tun.bucket && W.perm && W.cell_of && W.cell_cnt && W.dcell &&
+                        W.dbox && W.n_cells > 0;
+    mark(0);
+    if (bucket) {
+        BinArgs ba;
+        ba.doms = d_doms;
+        ba.units = d_units;
+        ba.n_units = n_units;
+        ba.src = src;
+        ba.dcell = W.dcell;
+        ba.dbox = W.dbox;
+        ba.cell_of = W.cell_of;
+        ba.cnt = W.cell_cnt;
+        ba.perm = W.perm;
+        ba.n_cells = W.n_cells;
+        if ((e = cudaMemsetAsync(W.cell_cnt, 0, (size_t)W.n_cells * sizeof(int), s)) != cudaSuccess) return e;
+        k_bin_count<<<n_units, 256, 0, s>>>(ba);
+        k_bin_scan<<<1, 1024, 0, s>>>(ba);
+        k_bin_scatter<<<n_units, 256, 0, s>>>(ba);
+    }
     SweepArgs sa;
     sa.doms = d_doms;
     sa.units = d_units;
     sa.n_units = n_units;
+    sa.perm = bucket ? W.perm : nullptr;
     sa.src = src;
     sa.acc2 = W.acc2;
     sa.theta = W.theta;
@@ -764,11 +1142,19 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     sa.cap_near = W.cap_near;
     sa.counters = W.counters;
     const int sweep_grid = max(1, min(n_units, cfg.n_sm * cfg.tun.sweep_ctas_per_sm));
-    mark(0);
-    switch (cfg.tun.qpt) {
-    case 1: k_sweep<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
-    case 4: k_sweep<4><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
-    default: k_sweep<2><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+    mark(1);
+    if (cfg.tun.tree) {
+        switch (cfg.tun.qpt) {
+        case 1: k_sweep_tree<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+        case 4: k_sweep_tree<4><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+        default: k_sweep_tree<2><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+        }
+    } else {
+        switch (cfg.tun.qpt) {
+        case 1: k_sweep<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+        case 4: k_sweep<4><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+        default: k_sweep<2><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
+        }
     }
     NearArgs na;
     na.doms = d_doms;
@@ -780,11 +1166,11 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     na.f64_items = W.f64_items;
     na.cap_f64 = W.cap_f64;
     na.counters = W.counters;
-    mark(1);
-    k_near<<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
     mark(2);
-    k_f64items<<<cfg.n_sm * 4, 128, 0, s>>>(na);
+    k_near<<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
     mark(3);
+    k_f64items<<<cfg.n_sm * 4, 128, 0, s>>>(na);
+    mark(4);
     FinArgs fa;
     fa.n = n_queries;
     fa.offsets = d_offsets;
@@ -797,7 +1183,7 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     fa.out = out;
     const long long fin_blocks = std::max(1LL, std::min((long long)(n_queries + 255) / 256, (long long)cfg.n_sm * 16));
     k_finalize<<<(int)fin_blocks, 256, 0, s>>>(fa);
-    mark(4);
+    mark(5);
     EscArgs ea;
     ea.doms = d_doms;
     ea.src = src;
@@ -805,7 +1191,7 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     ea.counters = W.counters;
     ea.out = out;
     k_f64query<<<cfg.n_sm * 2, kEscThreads, 0, s>>>(ea);
-    mark(5);
+    mark(6);
     return cudaGetLastError();
 }
 

@@ -172,6 +172,25 @@ def test_stats_and_profiling(wn):
     t, n = wn.kernel_times()
     wn.set_profiling(False)
     st = wn.stats()
-    assert n == 1 and t["sweep"] > 0
+    assert n == 1 and t["sweep"] > 0 and t["bucket"] >= 0
     assert st["queries"] == sum(len(q) for q in qs)
     assert st["overflow"] == 0 and st["device_error"] == 0
+
+
+@pytest.mark.parametrize("tree,bucket", [(0, 0), (1, 0), (1, 1)])
+def test_sweep_modes(wn, tree, bucket):
+    """Flat sweep, cluster sweep without and with spatial bucketing: all
+    against the oracle on open planar, bi-periodic and mixed batched faces."""
+    wn.set_tuning(tree=tree, bucket=bucket)
+    try:
+        d2, q2 = ws.config2(n_domains=64, n_uniform=64 * 9000, n_near=64 * 1500, domain_subset=[7, 8, 9])
+        d3, q3 = ws.config3(n_faces=256, n_queries=256 * 3000, face_subset=[20, 21, 22, 23])
+        S, Q, kind = ws.config4_sizes()
+        pick = list(np.nonzero(kind < 0.1)[0][6:9]) + list(np.nonzero(kind >= 0.2)[0][20:30])
+        d4, q4 = ws.config4(face_subset=pick, query_scale=0.05)
+        doms, qs = d2 + d3 + d4, q2 + q3 + q4
+        res = run(wn, doms, qs, 1)
+        for d, q, (w, s) in zip(doms, qs, res):
+            compare(d, q, w, s, TOL_MIXED)
+    finally:
+        wn.set_tuning(tree=1, bucket=1)
