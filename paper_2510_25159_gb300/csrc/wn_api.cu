@@ -92,12 +92,12 @@ DevState *dev_state(wn_status &st)
             st = cuda_fail(e, "cudaDeviceGetAttribute");
             return nullptr;
         }
-        e = cudaMalloc(&S.W.counters, CNT_N * sizeof(unsigned int));
+        e = cudaMalloc(&S.W.counters, CNT_N * sizeof(unsigned long long));
         if (e != cudaSuccess) {
             st = cuda_fail(e, "cudaMalloc counters");
             return nullptr;
         }
-        cudaMemset(S.W.counters, 0, CNT_N * sizeof(unsigned int));
+        cudaMemset(S.W.counters, 0, CNT_N * sizeof(unsigned long long));
         S.init = true;
     }
     st = WN_OK;
@@ -310,7 +310,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             if ((e = cudaMemcpy(S->W.offsets, offsets, (n_domains + 1) * sizeof(int64_t),
                                 cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cuda_fail(e, "upload offsets");
-            // spatial buckets: about 256 queries per cell, cells over the domain's
+            // spatial buckets: about 64 queries per cell, cells over the domain's
             // box (the base tile on periodic axes)
             std::vector<int4> dcell(n_domains);
             std::vector<float4> dbox(n_domains);
@@ -318,7 +318,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             for (int d = 0; d < n_domains; d++) {
                 const DomDev &dv = domains[d]->dev;
                 const int64_t cnt = offsets[d + 1] - offsets[d];
-                const int G = (int)std::max<double>(1.0, std::floor(std::sqrt((double)cnt / 256.0)));
+                const int G = (int)std::min<double>(4096.0, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / 64.0))));
                 const double x0 = dv.Pu > 0 ? 0.0 : dv.ox - dv.M, wx = dv.Pu > 0 ? dv.Pu : 2.0 * dv.M;
                 const double y0 = dv.Pv > 0 ? 0.0 : dv.oy - dv.M, wy = dv.Pv > 0 ? dv.Pv : 2.0 * dv.M;
                 dcell[d] = make_int4((int)ncell, G, 0, 0);
@@ -447,7 +447,7 @@ wn_status wn_get_stats(wn_stats *out)
     wn_status st;
     DevState *S = dev_state(st);
     if (!S) return st;
-    unsigned int c[CNT_N];
+    unsigned long long c[CNT_N];
     cudaError_t e = cudaMemcpy(c, S->W.counters, sizeof c, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "read counters");
     out->queries = S->last.queries;

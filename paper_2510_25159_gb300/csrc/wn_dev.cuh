@@ -34,7 +34,7 @@ struct LoopDev {
     int s0, s1;                 // segments [s0, s1)
     int r0, r1;                 // FP32 records [r0, r1)
     int hp, hq;                 // homology
-    int cls, pad;               // 0 plain, 1 contractible, 2 extended
+    int cls, root;              // 0 plain, 1 contractible, 2 extended; record-tree root (-1: none)
     double vx, vy;              // lattice vector (hp Pu, hq Pv)
     double g0x, g0y;            // gamma(0)
     double g0vx, g0vy;          // gamma(0) + v
@@ -50,7 +50,6 @@ struct InstDev {
     int pair;                   // bi-periodic pair for the family window, -1 none
     int axes;                   // IT_BOX: bit0 window x, bit1 window y
     int r0, r1;                 // FP32 records swept for this instance
-    int c0, c1;                 // record clusters covering [r0, r1)
     double Tx, Ty;              // query shift: p' = p - (Tx, Ty)
     double Fx, Fy;              // family shift for the slab / line: x_f = p - (Fx, Fy)
     long long I, J;             // lattice units of (Fx, Fy)
@@ -85,26 +84,38 @@ struct DomDev {
     const double2 *rec_a64;     // [n_rec] exact chord start
     const double2 *rec_b64;     // [n_rec] exact chord end
     const double2 *rec_n64;     // [n_rec] exact next vertex
-    const float4 *clu;          // [kCluF4 * n_clusters] record clusters, see below
-    int n_clusters, pad3;
+    const float4 *nodes;        // [kCluF4 * n_nodes] record tree, see below
+    int n_nodes, pad3;
 };
 
-// Record clusters: runs of at most kCluRecs consecutive records of one loop.
-// Per cluster, kCluF4 float4 (FP32, relative to the domain origin):
+// Record tree: per loop, leaves over runs of at most kCluRecs consecutive
+// records and internal nodes over kTreeArity consecutive children.  Each node
+// covers a contiguous record range; per node, kCluF4 float4 (FP32, relative
+// to the domain origin):
 //   [0] near box (xmin, xmax, ymin, ymax): outside it, by the query's error
-//       band, a query is outside every record's circle (so far from every
-//       segment's ellipse and eps discs);
-//   [1] (ymin, ymax, xmax) of every vertex of its pieces, and (rho r_c)^2;
+//       band, a query is outside every record's circle below the node (so far
+//       from every segment's ellipse and eps discs);
+//   [1] (ymin, ymax, xmax) of every vertex of its pieces (a query above,
+//       below or right of them cannot meet them with its +x ray), and the
+//       squared distance from z_c beyond which the gap-angle expansion is used;
 //   [2] expansion centre z_c, hi and lo parts;
-//   [3] (r_c, gap flag, first record, end record) -- the last two as int bits;
-//   [4 ..] kCluTerms complex coefficients c_k of the Laurent expansion of the
+//   [3] (r_c, flags: bit 0 gaps, bit 1 leaf, first, end) -- the last three as
+//       int bits; first/end index records (leaf) or child nodes;
+//   [4] squared distances beyond which 4, 8, 12, 16 terms suffice;
+//   [5] squared distances beyond which 20, 24, 28 terms suffice;
+//   [6 ..] kCluTerms complex coefficients c_k of the Laurent expansion of the
 //       sum of the cluster's gap angles:
 //         sum_gaps theta = Im sum_k c_k w^k,   w = r_c / (z_c - p),
-//       valid for |z_c - p| >= rho r_c.
+//       truncated after K terms with error at most C |w|^(K+1) / (1 - |w|),
+//       C = max_k |c_k| <= sum |gap| / r_c; the distances in [1], [4], [5]
+//       keep that below kCluTol radians.
 constexpr int kCluRecs = 16;
-constexpr int kCluTerms = 12;
-constexpr int kCluF4 = 4 + kCluTerms / 2;
-constexpr double kCluRho = 4.0;
+constexpr int kTreeArity = 4;
+constexpr int kTreeMaxLevels = 16;
+constexpr int kCluTerms = 32;
+constexpr int kCluCoef = 6;                 // first float4 of the coefficients
+constexpr int kCluF4 = kCluCoef + (kCluTerms + 1) / 2;
+constexpr double kCluTol = 2e-9;
 
 // Near / FP64 work item.
 struct Item {
@@ -112,6 +123,17 @@ struct Item {
     uint32_t dom;               // batch entry
     uint32_t inst;
     uint32_t rec;
+};
+
+// FP64 work item: the sub-interval [a, b] of a near pair whose FP32 error
+// band could not settle a decision, with the signs (bit 0: gamma(a) above
+// the query, bit 1: gamma(b) above) that the FP32 chain already used for
+// its end points.
+struct SubItem {
+    Item it;
+    float a, b;
+    uint32_t signs;
+    uint32_t pad;
 };
 
 // ---------------------------------------------------------------- exact FP64
@@ -296,6 +318,61 @@ __device__ bool alg1_fp64(const double *P, int n, double B, double px, double py
         }
         if (d >= kDepthCap64) return true;
         double m = 0.5 * (a + b), mx, my;
+        bez_eval<double>(cx, cy, n, m, mx, my);
+        st_d[sp - 1] = d + 1;
+        st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;
+        sp++;
+    }
+    return false;
+}
+
+// Algorithm 1 in FP64 on the sub-interval [a0, b0] of one segment, adding
+// the signed crossings of the +x ray from (px, py) by its chords; the end
+// points take the given signs (those of the FP32 chain around it).
+// Returns true when the query is on the boundary.
+__device__ inline bool alg1_fp64_sub(const double *P, int n, double B, double px, double py,
+                                     double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
+{
+    double cx[kNcp], cy[kNcp];
+#pragma unroll
+    for (int i = 0; i < kNcp; i++) {
+        cx[i] = (i <= n) ? P[2 * i] : 0.0;
+        cy[i] = (i <= n) ? P[2 * i + 1] : 0.0;
+    }
+    double st_t[kDepthCap64 + 2], st_x[kDepthCap64 + 2], st_y[kDepthCap64 + 2];
+    int st_d[kDepthCap64 + 2];
+    double gx, gy;
+    if (a0 == 0.0) { gx = cx[0]; gy = cy[0]; }
+    else bez_eval<double>(cx, cy, n, a0, gx, gy);
+    double a = a0, ax = gx - px, ay = gy - py;
+    bool sa = sa0;
+    double ra = sqrt(ax * ax + ay * ay);
+    if (b0 == 1.0) { gx = cx[n]; gy = cy[n]; }
+    else bez_eval<double>(cx, cy, n, b0, gx, gy);
+    int d0 = 0;
+    for (double w = b0 - a0; w < 1.0 && d0 < kDepthCap64; w *= 2.0) d0++;
+    st_t[0] = b0; st_x[0] = gx - px; st_y[0] = gy - py; st_d[0] = d0;
+    int sp = 1;
+    cnt = 0;
+    while (sp > 0) {
+        const double b = st_t[sp - 1], bx = st_x[sp - 1], by = st_y[sp - 1];
+        const int d = st_d[sp - 1];
+        const double rb = sqrt(bx * bx + by * by);
+        if (ra < eps || rb < eps) return true;
+        const bool sb = (b == b0) ? sb0 : (by > 0.0);
+        if (ra + rb > B * (b - a)) {
+            if (sa != sb) {
+                const double D = ax * by - ay * bx;
+                if (!sa && sb && D > 0) cnt++;
+                else if (sa && !sb && D < 0) cnt--;
+            }
+            a = b; ax = bx; ay = by; ra = rb; sa = sb;
+            sp--;
+            continue;
+        }
+        if (d >= kDepthCap64) return true;
+        const double m = 0.5 * (a + b);
+        double mx, my;
         bez_eval<double>(cx, cy, n, m, mx, my);
         st_d[sp - 1] = d + 1;
         st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;

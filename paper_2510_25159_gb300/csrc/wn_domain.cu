@@ -320,101 +320,137 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         loop_r1[l] = (int)rec_seg.size();
     }
 
-    // ---- record clusters: per loop, runs of kCluRecs records
-    std::vector<float4> clu;
-    std::vector<int> loop_c0(n_loops), loop_c1(n_loops);
+    // ---- record tree: per loop, leaves of kCluRecs consecutive records and
+    // internal nodes over kTreeArity consecutive children; every node covers a
+    // contiguous record range and carries its near box, ray extent and the
+    // expansion of its gap angles
+    std::vector<float4> nodes;
+    std::vector<int> loop_root(n_loops, -1);
     {
         auto dn = [](double x) { return std::nextafter((float)x, -INFINITY); };
         auto upf = [](double x) { return std::nextafter((float)x, INFINITY); };
-        for (int l = 0; l < n_loops; l++) {
-            loop_c0[l] = (int)(clu.size() / kCluF4);
-            for (int r0 = loop_r0[l]; r0 < loop_r1[l]; r0 += kCluRecs) {
-                const int r1 = std::min(r0 + kCluRecs, loop_r1[l]);
-                double nb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
-                double yr0 = INFINITY, yr1 = -INFINITY, xr1 = -INFINITY;
-                double gb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
-                bool gaps = false;
-                for (int r = r0; r < r1; r++) {
-                    const double2 a = ra64[r], b = rb64[r], n = rn64[r];
-                    for (const double2 &v : {a, b, n}) {
-                        yr0 = std::fmin(yr0, v.y); yr1 = std::fmax(yr1, v.y); xr1 = std::fmax(xr1, v.x);
+        auto make_node = [&](int R0, int R1, bool leaf, int first, int end) {
+            double nb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
+            double yr0 = INFINITY, yr1 = -INFINITY, xr1 = -INFINITY;
+            double gb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
+            bool gaps = false;
+            for (int r = R0; r < R1; r++) {
+                const double2 a = ra64[r], b = rb64[r], n = rn64[r];
+                for (const double2 &v : {a, b, n}) {
+                    yr0 = std::fmin(yr0, v.y); yr1 = std::fmax(yr1, v.y); xr1 = std::fmax(xr1, v.x);
+                }
+                uint32_t fl;
+                std::memcpy(&fl, &rec[4 * r + 1].w, 4);
+                if (!(fl & RF_CHORD)) {
+                    const int sg = rec_seg[r];
+                    const double cx = 0.5 * (a.x + b.x), cy = 0.5 * (a.y + b.y);
+                    const double R = (0.5 * segB[sg] + eps) * (1.0 + std::ldexp(1.0, -20)) + 4.0 * Trec;
+                    nb[0] = std::fmin(nb[0], cx - R); nb[1] = std::fmax(nb[1], cx + R);
+                    nb[2] = std::fmin(nb[2], cy - R); nb[3] = std::fmax(nb[3], cy + R);
+                }
+                if (fl & RF_GAP) {
+                    gaps = true;
+                    for (const double2 &v : {b, n}) {
+                        gb[0] = std::fmin(gb[0], v.x); gb[1] = std::fmax(gb[1], v.x);
+                        gb[2] = std::fmin(gb[2], v.y); gb[3] = std::fmax(gb[3], v.y);
                     }
+                }
+            }
+            float4 c[kCluF4];
+            std::memset(c, 0, sizeof c);
+            if (nb[0] <= nb[1]) c[0] = make_float4(dn(nb[0] - ox), upf(nb[1] - ox), dn(nb[2] - oy), upf(nb[3] - oy));
+            else c[0] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);   // closing chords only
+            c[1] = make_float4(dn(yr0 - oy), upf(yr1 - oy), upf(xr1 - ox), 0.f);
+            double zx = 0, zy = 0, rc = 0;
+            if (gaps) {
+                zx = 0.5 * (gb[0] + gb[1]);
+                zy = 0.5 * (gb[2] + gb[3]);
+                double Cb = 0.0;
+                for (int r = R0; r < R1; r++) {
                     uint32_t fl;
                     std::memcpy(&fl, &rec[4 * r + 1].w, 4);
-                    if (!(fl & RF_CHORD)) {
-                        const int sg = rec_seg[r];
-                        const double cx = 0.5 * (a.x + b.x), cy = 0.5 * (a.y + b.y);
-                        const double R = (0.5 * segB[sg] + eps) * (1.0 + std::ldexp(1.0, -20)) + 4.0 * Trec;
-                        nb[0] = std::fmin(nb[0], cx - R); nb[1] = std::fmax(nb[1], cx + R);
-                        nb[2] = std::fmin(nb[2], cy - R); nb[3] = std::fmax(nb[3], cy + R);
-                    }
-                    if (fl & RF_GAP) {
-                        gaps = true;
-                        for (const double2 &v : {b, n}) {
-                            gb[0] = std::fmin(gb[0], v.x); gb[1] = std::fmax(gb[1], v.x);
-                            gb[2] = std::fmin(gb[2], v.y); gb[3] = std::fmax(gb[3], v.y);
+                    if (!(fl & RF_GAP)) continue;
+                    rc = std::fmax(rc, std::hypot(rb64[r].x - zx, rb64[r].y - zy));
+                    rc = std::fmax(rc, std::hypot(rn64[r].x - zx, rn64[r].y - zy));
+                }
+                rc = std::fmax(rc, 1e-300);
+                // M_k = sum_gaps (n - z)^k - (b - z)^k ;  c_k = (-1)^(k+1) M_k / (k rc^k)
+                double Mre[kCluTerms + 1] = {}, Mim[kCluTerms + 1] = {};
+                for (int r = R0; r < R1; r++) {
+                    uint32_t fl;
+                    std::memcpy(&fl, &rec[4 * r + 1].w, 4);
+                    if (!(fl & RF_GAP)) continue;
+                    Cb += std::hypot(rn64[r].x - rb64[r].x, rn64[r].y - rb64[r].y) / rc;
+                    for (int side = 0; side < 2; side++) {
+                        const double2 v = side ? rn64[r] : rb64[r];
+                        const double sg = side ? 1.0 : -1.0;
+                        const double ux = (v.x - zx) / rc, uy = (v.y - zy) / rc;
+                        double pr = 1.0, pi = 0.0;
+                        for (int k = 1; k <= kCluTerms; k++) {
+                            const double t = pr * ux - pi * uy;
+                            pi = pr * uy + pi * ux;
+                            pr = t;
+                            Mre[k] += sg * pr;
+                            Mim[k] += sg * pi;
                         }
                     }
                 }
-                float4 c[kCluF4];
-                std::memset(c, 0, sizeof c);
-                if (nb[0] <= nb[1]) {
-                    c[0] = make_float4(dn(nb[0] - ox), upf(nb[1] - ox), dn(nb[2] - oy), upf(nb[3] - oy));
-                } else {   // closing chords only: an empty box
-                    c[0] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+                for (int k = 1; k <= kCluTerms; k++) {
+                    const double f = ((k & 1) ? 1.0 : -1.0) / (double)k;
+                    float *dst = reinterpret_cast<float *>(&c[kCluCoef]) + 2 * (k - 1);
+                    dst[0] = (float)(f * Mre[k]);
+                    dst[1] = (float)(f * Mim[k]);
                 }
-                c[1] = make_float4(dn(yr0 - oy), upf(yr1 - oy), upf(xr1 - ox), 0.f);
-                double zx = 0, zy = 0, rc = 0;
-                if (gaps) {
-                    zx = 0.5 * (gb[0] + gb[1]);
-                    zy = 0.5 * (gb[2] + gb[3]);
-                    for (int r = r0; r < r1; r++) {
-                        uint32_t fl;
-                        std::memcpy(&fl, &rec[4 * r + 1].w, 4);
-                        if (!(fl & RF_GAP)) continue;
-                        rc = std::fmax(rc, std::hypot(rb64[r].x - zx, rb64[r].y - zy));
-                        rc = std::fmax(rc, std::hypot(rn64[r].x - zx, rn64[r].y - zy));
+                // C >= |c_k| for every k: each gap adds at most |g| / r_c.  The
+                // largest |w| with C |w|^(K+1) / (1 - |w|) <= tol, by bisection.
+                auto dist2 = [&](int K) {
+                    double lo = 0.0, hi = 0.999;
+                    for (int it = 0; it < 80; it++) {
+                        const double m = 0.5 * (lo + hi);
+                        if (Cb * std::pow(m, K + 1) / (1.0 - m) <= kCluTol) lo = m;
+                        else hi = m;
                     }
-                    rc = std::fmax(rc, 1e-300);
-                    // M_k = sum_gaps (n - z)^k - (b - z)^k ; c_k = (-1)^(k+1) M_k / (k rc^k)
-                    double Mre[kCluTerms + 1] = {}, Mim[kCluTerms + 1] = {};
-                    for (int r = r0; r < r1; r++) {
-                        uint32_t fl;
-                        std::memcpy(&fl, &rec[4 * r + 1].w, 4);
-                        if (!(fl & RF_GAP)) continue;
-                        for (int side = 0; side < 2; side++) {
-                            const double2 v = side ? rn64[r] : rb64[r];
-                            const double sg = side ? 1.0 : -1.0;
-                            const double ux = (v.x - zx) / rc, uy = (v.y - zy) / rc;
-                            double pr = 1.0, pi = 0.0;
-                            for (int k = 1; k <= kCluTerms; k++) {
-                                const double t = pr * ux - pi * uy;
-                                pi = pr * uy + pi * ux;
-                                pr = t;
-                                Mre[k] += sg * pr;
-                                Mim[k] += sg * pi;
-                            }
-                        }
-                    }
-                    for (int k = 1; k <= kCluTerms; k++) {
-                        const double f = ((k & 1) ? 1.0 : -1.0) / (double)k;
-                        float *dst = reinterpret_cast<float *>(&c[4]) + 2 * (k - 1);
-                        dst[0] = (float)(f * Mre[k]);
-                        dst[1] = (float)(f * Mim[k]);
-                    }
-                    const double racc = kCluRho * rc;
-                    c[1].w = upf(racc * racc);
-                }
-                const float zxh = (float)(zx - ox), zyh = (float)(zy - oy);
-                c[2] = make_float4(zxh, zyh, (float)((zx - ox) - (double)zxh), (float)((zy - oy) - (double)zyh));
-                float r0f, r1f;
-                int r0i = r0, r1i = r1;
-                std::memcpy(&r0f, &r0i, 4);
-                std::memcpy(&r1f, &r1i, 4);
-                c[3] = make_float4((float)rc, gaps ? 1.f : 0.f, r0f, r1f);
-                for (int i = 0; i < kCluF4; i++) clu.push_back(c[i]);
+                    const double d = lo > 0 ? rc / lo : INFINITY;
+                    return upf(d * d * (1.0 + 1e-6));
+                };
+                c[1].w = dist2(kCluTerms);
+                c[4] = make_float4(dist2(4), dist2(8), dist2(12), dist2(16));
+                c[5] = make_float4(dist2(20), dist2(24), dist2(28), dist2(kCluTerms));
             }
-            loop_c1[l] = (int)(clu.size() / kCluF4);
+            const float zxh = (float)(zx - ox), zyh = (float)(zy - oy);
+            c[2] = make_float4(zxh, zyh, (float)((zx - ox) - (double)zxh), (float)((zy - oy) - (double)zyh));
+            const int flags = (gaps ? 1 : 0) | (leaf ? 2 : 0);
+            float ff, f0, f1;
+            std::memcpy(&ff, &flags, 4);
+            std::memcpy(&f0, &first, 4);
+            std::memcpy(&f1, &end, 4);
+            c[3] = make_float4((float)rc, ff, f0, f1);
+            const int id = (int)(nodes.size() / kCluF4);
+            for (int i = 0; i < kCluF4; i++) nodes.push_back(c[i]);
+            return id;
+        };
+        for (int l = 0; l < n_loops; l++) {
+            if (loop_r1[l] == loop_r0[l]) continue;
+            std::vector<int> level, lr0, lr1;       // node ids and their record ranges
+            for (int r0 = loop_r0[l]; r0 < loop_r1[l]; r0 += kCluRecs) {
+                const int r1 = std::min(r0 + kCluRecs, loop_r1[l]);
+                level.push_back(make_node(r0, r1, true, r0, r1));
+                lr0.push_back(r0);
+                lr1.push_back(r1);
+            }
+            while (level.size() > 1) {
+                std::vector<int> up_level, u0, u1;
+                for (size_t i = 0; i < level.size(); i += kTreeArity) {
+                    const size_t j = std::min(level.size(), i + kTreeArity);
+                    up_level.push_back(make_node(lr0[i], lr1[j - 1], false, level[i], level[j - 1] + 1));
+                    u0.push_back(lr0[i]);
+                    u1.push_back(lr1[j - 1]);
+                }
+                level.swap(up_level);
+                lr0.swap(u0);
+                lr1.swap(u1);
+            }
+            loop_root[l] = level[0];
         }
     }
 
@@ -440,6 +476,7 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         o.smin = L.smin; o.smax = L.smax; o.vv = L.vv;
         for (int i = 0; i < 4; i++) o.box[i] = L.box[i];
         o.nlo = L.nlo; o.nhi = L.nhi;
+        o.root = loop_root[l];
     }
     DomDev &dv = D->dev;
     std::memset(&dv, 0, sizeof dv);
@@ -459,8 +496,8 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     dv.rec_a64 = up.up(ra64);
     dv.rec_b64 = up.up(rb64);
     dv.rec_n64 = up.up(rn64);
-    dv.n_clusters = (int)(clu.size() / kCluF4);
-    dv.clu = up.up(clu);
+    dv.n_nodes = (int)(nodes.size() / kCluF4);
+    dv.nodes = up.up(nodes);
     if (up.err != cudaSuccess) return fail(up.err == cudaErrorMemoryAllocation ? 4 : 3,
                                            std::string("CUDA: ") + cudaGetErrorString(up.err));
     {
@@ -556,8 +593,6 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         in.pair = -1;
         in.r0 = loop_r0[l];
         in.r1 = loop_r1[l];
-        in.c0 = loop_c0[l];
-        in.c1 = loop_c1[l];
         return in;
     };
     const double tile_x[2] = {0.0, (Pu > 0) ? Pu : 0.0}, tile_y[2] = {0.0, (Pv > 0) ? Pv : 0.0};
@@ -570,7 +605,6 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         if (!(Pv > 0)) ln.Fy = 0.0;
         ln.I = I; ln.J = J; ln.pair = pair; ln.c = c;
         ln.r0 = ln.r1 = 0;
-        ln.c0 = ln.c1 = 0;
         inst.push_back(ln);
         // sp range over the base tile (a cylinder tile is unbounded across the
         // axis, but v has no component along it)
@@ -597,8 +631,6 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             InstDev in = base_inst(IT_ALL, 0);
             in.r0 = 0;
             in.r1 = (int)rec_seg.size();
-            in.c0 = 0;
-            in.c1 = (int)(clu.size() / kCluF4);
             inst.push_back(in);
         }
     } else {

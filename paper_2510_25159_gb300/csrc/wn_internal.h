@@ -41,9 +41,9 @@ struct Work {
     float *theta = nullptr;    // sum of gap angles, per query
     uint32_t *flags = nullptr; // QF_*, per query
     Item *near_items = nullptr;
-    Item *f64_items = nullptr;
+    SubItem *f64_items = nullptr;
     uint2 *esc_q = nullptr;    // (query, batch entry) recomputed in FP64
-    unsigned int *counters = nullptr;  // see CNT_*
+    unsigned long long *counters = nullptr;  // see CNT_*
     int4 *units = nullptr;     // (dom, q0, count, 0)
     DomDev *doms = nullptr;
     int64_t *offsets = nullptr;  // device copy of point offsets

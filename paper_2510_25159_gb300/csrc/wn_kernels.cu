@@ -67,7 +67,7 @@ struct SweepArgs {
     uint32_t *flags;
     Item *near_items;
     long long cap_near;
-    unsigned int *counters;
+    unsigned long long *counters;
 };
 
 // Exact recomputation of one record's crossings and gap angle in FP64, for a
@@ -170,6 +170,47 @@ __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, c
     }
 }
 
+// One record against a query that is outside every circle of its cluster
+// (so no near pair can arise): chord crossing, gap crossing and gap angle.
+__device__ __forceinline__ void sweep_record_far(const float4 R0, const float4 R1, const float4 R2,
+                                                 const float4 R3, float fx, float fy, float fxl,
+                                                 float fyl, float T, int &c, float &dth, bool &slow)
+{
+    const float uy = R0.y - fy, wy = R0.w - fy;
+    const bool sa = uy > 0.f, sb = wy > 0.f;
+    slow = (fabsf(uy) <= T) | (fabsf(wy) <= T);
+    const uint32_t fl = __float_as_uint(R1.w);
+    const float wx = R0.z - fx;
+    c = 0;
+    dth = 0.f;
+    if (sa != sb) {
+        const float ux = R0.x - fx;
+        const float D = fmaf(ux, wy, -uy * wx);
+        const float TD = T * (fabsf(ux) + fabsf(uy) + fabsf(wx) + fabsf(wy)) +
+                         kTwoM22 * (fabsf(ux * wy) + fabsf(uy * wx));
+        slow |= fabsf(D) <= TD;
+        const bool pos = D > 0.f;
+        c = (!sa && sb && pos) ? 1 : ((sa && !sb && !pos) ? -1 : 0);
+    }
+    if (fl & RF_GAP) {
+        const float gx = R2.x, gy = R2.y;
+        const float ny = R2.w - fy;
+        const bool sn = ny > 0.f;
+        slow |= fabsf(ny) <= T;
+        const float bx = wx + (R3.x - fxl), by = wy + (R3.y - fyl);
+        const float vx = (R2.z - fx) + (R3.z - fxl), vy = ny + (R3.w - fyl);
+        const bool use_g = fmaf(gx, gx, gy * gy) <= fmaf(vx, vx, vy * vy);
+        const float ex = use_g ? gx : vx, ey = use_g ? gy : vy;
+        const float Dg = fmaf(bx, ey, -by * ex);
+        if (sb != sn) {
+            slow |= fabsf(Dg) <= 4.0f * kTwoM22 * (fabsf(bx) + fabsf(by)) * (fabsf(ex) + fabsf(ey));
+            const bool pos = Dg > 0.f;
+            c += (!sb && sn && pos) ? 1 : ((sb && !sn && !pos) ? -1 : 0);
+        }
+        dth = gap_angle(Dg, fmaf(bx, vx, by * vy));
+    }
+}
+
 // Compensated addition of a float into a (hi, lo) pair (Knuth's TwoSum).
 __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v)
 {
@@ -216,41 +257,43 @@ __device__ __forceinline__ void sweep_record_cross(const float4 R0, const float4
     }
 }
 
-// Sum of a cluster's gap angles at the query from its Laurent expansion
-// (valid at |z_c - p| >= rho r_c): Im sum_k c_k w^k, w = r_c / (z_c - p).
-__device__ __forceinline__ float cluster_gap_sum(const float4 *__restrict__ C, float fx, float fy,
-                                                 float fxl, float fyl)
+// Sum of a node's gap angles at the query from its Laurent expansion,
+// Im sum_{k<K} c_k w^k with w = r_c / (z_c - p); K is uniform across the warp.
+__device__ __forceinline__ float node_gap_sum(const float4 *__restrict__ N, float fx, float fy, float fxl,
+                                              float fyl, int K)
 {
-    const float dx = (C[2].x - fx) + (C[2].z - fxl);
-    const float dy = (C[2].y - fy) + (C[2].w - fyl);
-    const float inv = __fdividef(C[3].x, fmaf(dx, dx, dy * dy));
+    const float4 z = __ldg(N + 2);
+    const float dx = (z.x - fx) + (z.z - fxl);
+    const float dy = (z.y - fy) + (z.w - fyl);
+    const float inv = __fdividef(__ldg(&N[3].x), fmaf(dx, dx, dy * dy));
     const float wr = dx * inv, wi = -dy * inv;
-    const float *cf = reinterpret_cast<const float *>(C + 4);
-    float sr = cf[2 * (kCluTerms - 1)], si = cf[2 * (kCluTerms - 1) + 1];
-#pragma unroll
-    for (int k = kCluTerms - 2; k >= 0; k--) {
-        const float tr = fmaf(sr, wr, fmaf(-si, wi, cf[2 * k]));
-        const float ti = fmaf(sr, wi, fmaf(si, wr, cf[2 * k + 1]));
+    const float2 *cf = reinterpret_cast<const float2 *>(N + kCluCoef);
+    float2 c = __ldg(cf + (K - 1));
+    float sr = c.x, si = c.y;
+    for (int k = K - 2; k >= 0; k--) {
+        c = __ldg(cf + k);
+        const float tr = fmaf(sr, wr, fmaf(-si, wi, c.x));
+        const float ti = fmaf(sr, wi, fmaf(si, wr, c.y));
         sr = tr;
         si = ti;
     }
     return fmaf(sr, wi, si * wr);
 }
 
-constexpr int kChunkClu = 4;                            // clusters per shared-memory stage
-constexpr int kChunkRecs = kChunkClu * kCluRecs;
-
-// Tree sweep.  Per (query, cluster): outside the cluster's near box and at
-// least rho r_c away, the gap angles come from the cluster's expansion and
-// only crossings need the records (and only when the query's +x ray can
-// meet the cluster); otherwise the records are swept in full.  The choice
-// is made per query, so results do not depend on which queries share a
-// tile; tiles of spatially bucketed queries let whole warps skip clusters.
+// Warp-synchronous walk of the record trees of every loop an instance
+// covers.  Each query slot carries a status per tree level: 1 = full (gap
+// angles and near pairs still needed below), 2 = crossings only, 0 = done.
+// At a node, a full slot outside the near box whose distance accepts the
+// node's expansion takes the node's gap angles from it and keeps only the
+// crossings (if its +x ray can meet the node); a slot inside the box, or too
+// close, stays full.  Leaves sweep their records for the slots that still
+// need them.  The stack lives in the lanes' registers (entry i in lane i).
 template <int QPT>
-__global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep_tree(const SweepArgs A)
+__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs A)
 {
-    __shared__ float4 s_rec[4 * kChunkRecs];
-    __shared__ float4 s_clu[kCluF4 * kChunkClu];
+    constexpr int SB = 2 * QPT;                     // status bits per level
+    constexpr uint64_t SMASK = (1ull << SB) - 1ull;
+    static_assert(SB * kTreeMaxLevels <= 64, "level flags must fit 64 bits");
     __shared__ double2 s_p[QPT][kSweepThreads];
     __shared__ int s_unit;
     const int tid = threadIdx.x;
@@ -259,7 +302,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep_tre
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[CNT_UNIT], 1u);
+        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[CNT_UNIT], 1ULL);
         __syncthreads();
         const int u = s_unit;
         if (u >= A.n_units) return;
@@ -269,7 +312,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep_tre
         const float M = Dp->M, Mq = Dp->Mq;
         const int n_inst = Dp->n_inst;
         const float4 *__restrict__ rec = Dp->rec;
-        const float4 *__restrict__ clu = Dp->clu;
+        const float4 *__restrict__ nodes = Dp->nodes;
 
         float fx[QPT], fy[QPT], fxl[QPT], fyl[QPT], T[QPT], th[QPT], thl[QPT];
         int acc[QPT];
@@ -277,7 +320,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep_tre
         bool valid[QPT], inc[QPT];
 #pragma unroll
         for (int k = 0; k < QPT; k++) {
-            const int ql = tid + k * kSweepThreads;
+            const int ql = tid * QPT + k;           // a warp owns 32*QPT consecutive positions
             valid[k] = ql < U.z;
             qid[k] = 0;
             double x = 0.0, y = 0.0;
@@ -294,7 +337,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep_tre
         for (int j = 0; j < n_inst; j++) {
             const InstDev in = Dp->inst[j];
             const LoopDev &L = Dp->loops[in.loop];
-            int any = 0;
+            bool any = false;
 #pragma unroll
             for (int k = 0; k < QPT; k++) {
                 const double2 p = s_p[k][tid];
@@ -321,136 +364,188 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep_tre
                 T[k] = kTwoM22 * (M + mag);
                 any |= inc[k];
             }
-            if (!__syncthreads_or(any)) continue;
-            for (int cb = in.c0; cb < in.c1; cb += kChunkClu) {
-                const int ncl = min(kChunkClu, in.c1 - cb);
-                for (int i = tid; i < kCluF4 * ncl; i += kSweepThreads) s_clu[i] = __ldg(clu + kCluF4 * cb + i);
-                __syncthreads();
-                // per-query decisions for the clusters of this stage
-                uint32_t nfull[QPT], ncross[QPT], mpm[QPT];
-                float tc[QPT];
-                int need = 0;
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const int l0 = (in.type == IT_ALL) ? 0 : in.loop;
+            const int l1 = (in.type == IT_ALL) ? Dp->n_loops : in.loop + 1;
+            for (int l = l0; l < l1; l++) {
+                const int root = Dp->loops[l].root;
+                if (root < 0) continue;
+                uint64_t lf = 0;
 #pragma unroll
-                for (int k = 0; k < QPT; k++) {
-                    nfull[k] = ncross[k] = mpm[k] = 0u;
-                    tc[k] = 0.f;
-                }
-                for (int c = 0; c < ncl; c++) {
-                    const float4 *C = s_clu + kCluF4 * c;
-                    const float4 nb = C[0], yx = C[1];
-                    const bool gaps = C[3].y != 0.f;
+                for (int k = 0; k < QPT; k++)
+                    if (inc[k]) lf |= 1ull << (2 * k);
+                int st_cur = root, st_end = root + 1, st_lvl = 0;    // stack entry `lane`
+                int sp = 0;
+                while (sp >= 0) {
+                    const int cur = __shfl_sync(0xffffffffu, st_cur, sp);
+                    const int end = __shfl_sync(0xffffffffu, st_end, sp);
+                    const int lvl = __shfl_sync(0xffffffffu, st_lvl, sp);
+                    if (lane == sp) st_cur = cur + 1;
+                    if (cur + 1 >= end) sp--;
+                    const uint32_t f = (uint32_t)((lf >> (lvl * SB)) & SMASK);
+                    if (!__any_sync(0xffffffffu, f != 0u)) continue;
+                    const float4 *__restrict__ N = nodes + (size_t)kCluF4 * cur;
+                    const float4 nb = __ldg(N), yx = __ldg(N + 1), meta = __ldg(N + 3);
+                    const int nflags = __float_as_int(meta.y);
+                    const bool gaps = nflags & 1, leaf = (nflags & 2) != 0;
+                    uint32_t cf = 0u, nearb = 0u, mpb = 0u;
+                    int kneed = 0;
+                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (gaps) z = __ldg(N + 2);
 #pragma unroll
                     for (int k = 0; k < QPT; k++) {
+                        const uint32_t sk = (f >> (2 * k)) & 3u;
+                        if (!sk) continue;
                         const bool outside = (fx[k] < nb.x - T[k]) | (fx[k] > nb.y + T[k]) |
                                              (fy[k] < nb.z - T[k]) | (fy[k] > nb.w + T[k]);
                         const bool cross = !((fy[k] > yx.y + T[k]) | (fy[k] < yx.x - T[k]) | (fx[k] > yx.z + T[k]));
-                        bool mp = outside;
-                        if (gaps && outside) {
-                            const float dx = (C[2].x - fx[k]) + (C[2].z - fxl[k]);
-                            const float dy = (C[2].y - fy[k]) + (C[2].w - fyl[k]);
-                            mp = fmaf(dx, dx, dy * dy) >= yx.w;
-                        }
-                        if (inc[k]) {
-                            if (!mp) nfull[k] |= 1u << c;
-                            else mpm[k] |= 1u << c;
-                            if (cross) ncross[k] |= 1u << c;
-                        }
-                    }
-                    if (gaps) {
-#pragma unroll
-                        for (int k = 0; k < QPT; k++)
-                            if (inc[k] && (mpm[k] >> c & 1u)) tc[k] += cluster_gap_sum(C, fx[k], fy[k], fxl[k], fyl[k]);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < QPT; k++) need |= (int)(nfull[k] | ncross[k]);
-                if (__syncthreads_or(need)) {
-                    const int rb = __float_as_int(s_clu[3].z);
-                    const int re = __float_as_int(s_clu[kCluF4 * (ncl - 1) + 3].w);
-                    for (int i = tid; i < 4 * (re - rb); i += kSweepThreads) s_rec[i] = __ldg(rec + 4 * rb + i);
-                    __syncthreads();
-                    for (int c = 0; c < ncl; c++) {
-                        uint32_t wf = 0, wc = 0;
-#pragma unroll
-                        for (int k = 0; k < QPT; k++) {
-                            wf |= nfull[k];
-                            wc |= ncross[k];
-                        }
-                        wf = __reduce_or_sync(0xffffffffu, wf) >> c & 1u;
-                        wc = __reduce_or_sync(0xffffffffu, wc) >> c & 1u;
-                        if (!wf && !wc) continue;
-                        const int r0 = __float_as_int(s_clu[kCluF4 * c + 3].z);
-                        const int r1 = __float_as_int(s_clu[kCluF4 * c + 3].w);
-                        for (int r = r0; r < r1; r++) {
-                            const int sr = r - rb;
-                            const float4 R0 = s_rec[4 * sr], R1 = s_rec[4 * sr + 1], R2 = s_rec[4 * sr + 2];
-                            if (wf) {
-                                const float4 R3 = s_rec[4 * sr + 3];
-                                bool nr[QPT];
-                                bool any_near = false;
-#pragma unroll
-                                for (int k = 0; k < QPT; k++) {
-                                    int cc;
-                                    float dth;
-                                    bool slow;
-                                    sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, nr[k], slow);
-                                    if (slow && inc[k]) {
-                                        const double2 p = s_p[k][tid];
-                                        sweep_record_exact(r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
-                                                           xsub(p.y, in.Ty), cc, dth);
-                                    }
-                                    nr[k] = nr[k] && inc[k];
-                                    if (inc[k]) {
-                                        acc[k] += 2 * cc;
-                                        if (nfull[k] >> c & 1u) tc[k] += dth;
-                                    }
-                                    any_near |= nr[k];
-                                }
-                                if (__any_sync(0xffffffffu, any_near)) {
-#pragma unroll
-                                    for (int k = 0; k < QPT; k++) {
-                                        const unsigned m = __ballot_sync(0xffffffffu, nr[k]);
-                                        if (!m) continue;
-                                        const int leader = __ffs(m) - 1;
-                                        unsigned base = 0;
-                                        if (lane == leader) base = atomicAdd(&A.counters[CNT_NEAR], (unsigned)__popc(m));
-                                        base = __shfl_sync(0xffffffffu, base, leader);
-                                        if (nr[k]) {
-                                            const unsigned long long idx = (unsigned long long)base + __popc(m & lt_mask);
-                                            if (idx < (unsigned long long)A.cap_near) {
-                                                Item it;
-                                                it.q = qid[k];
-                                                it.dom = (uint32_t)U.x;
-                                                it.inst = (uint32_t)j;
-                                                it.rec = (uint32_t)r;
-                                                A.near_items[idx] = it;
-                                            } else {
-                                                fl[k] |= QF_ESCALATE;
-                                            }
-                                        }
-                                    }
-                                }
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < QPT; k++) {
-                                    int cc;
-                                    bool slow;
-                                    sweep_record_cross(R0, R1, R2, fx[k], fy[k], T[k], cc, slow);
-                                    if (slow && inc[k]) {
-                                        const double2 p = s_p[k][tid];
-                                        float dth;
-                                        sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
-                                                           xsub(p.y, in.Ty), cc, dth);
-                                    }
-                                    if (inc[k]) acc[k] += 2 * cc;
+                        uint32_t child = cross ? 2u : 0u;
+                        if (sk == 1u) {
+                            if (!outside) {
+                                child = 1u;
+                                nearb |= 1u << k;
+                            } else if (gaps) {
+                                const float dx = (z.x - fx[k]) + (z.z - fxl[k]);
+                                const float dy = (z.y - fy[k]) + (z.w - fyl[k]);
+                                const float d2 = fmaf(dx, dx, dy * dy);
+                                if (d2 >= yx.w) {
+                                    const float4 t0 = __ldg(N + 4), t1 = __ldg(N + 5);
+                                    const int kq = d2 >= t0.x ? 4 : d2 >= t0.y ? 8 : d2 >= t0.z ? 12 : d2 >= t0.w ? 16
+                                                 : d2 >= t1.x ? 20 : d2 >= t1.y ? 24 : d2 >= t1.z ? 28 : kCluTerms;
+                                    kneed = max(kneed, kq);
+                                    mpb |= 1u << k;
+                                } else {
+                                    child = 1u;
                                 }
                             }
                         }
+                        cf |= child << (2 * k);
                     }
-                }
+                    if (gaps) {
+                        const int K = __reduce_max_sync(0xffffffffu, kneed);
+                        if (K > 0) {
 #pragma unroll
-                for (int k = 0; k < QPT; k++) two_sum_add(th[k], thl[k], tc[k]);
-                __syncthreads();
+                            for (int k = 0; k < QPT; k++)
+                                if (mpb >> k & 1u) two_sum_add(th[k], thl[k], node_gap_sum(N, fx[k], fy[k], fxl[k], fyl[k], K));
+                        }
+                    }
+                    if (!leaf) {
+                        if (__any_sync(0xffffffffu, cf != 0u)) {
+                            sp++;
+                            if (lane == sp) {
+                                st_cur = __float_as_int(meta.z);
+                                st_end = __float_as_int(meta.w);
+                                st_lvl = lvl + 1;
+                            }
+                            const int sh = (lvl + 1) * SB;
+                            lf = (lf & ~(SMASK << sh)) | ((uint64_t)cf << sh);
+                        }
+                        continue;
+                    }
+                    // leaf: records [first, end) for the slots that still need them
+                    bool need_near = nearb != 0u, need_full = false, need_cross = false;
+#pragma unroll
+                    for (int k = 0; k < QPT; k++) {
+                        const uint32_t ck = (cf >> (2 * k)) & 3u;
+                        need_full |= ck == 1u;
+                        need_cross |= ck == 2u;
+                    }
+                    const bool wn = __any_sync(0xffffffffu, need_near);
+                    const bool we = __any_sync(0xffffffffu, need_full);
+                    const bool wc = __any_sync(0xffffffffu, need_cross);
+                    if (!we && !wc) continue;
+                    const int r0 = __float_as_int(meta.z), r1 = __float_as_int(meta.w);
+                    float tcl[QPT];
+#pragma unroll
+                    for (int k = 0; k < QPT; k++) tcl[k] = 0.f;
+                    for (int r = r0; r < r1; r++) {
+                        const float4 R0 = __ldg(rec + 4 * r), R1 = __ldg(rec + 4 * r + 1), R2 = __ldg(rec + 4 * r + 2);
+                        if (wn) {
+                            const float4 R3 = __ldg(rec + 4 * r + 3);
+                            bool nr[QPT];
+                            bool any_near = false;
+#pragma unroll
+                            for (int k = 0; k < QPT; k++) {
+                                const uint32_t ck = (cf >> (2 * k)) & 3u;
+                                int cc;
+                                float dth;
+                                bool slow;
+                                sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, nr[k], slow);
+                                if (slow && ck) {
+                                    const double2 p = s_p[k][tid];
+                                    sweep_record_exact(r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
+                                                       xsub(p.y, in.Ty), cc, dth);
+                                }
+                                nr[k] = nr[k] && ck == 1u;
+                                if (ck) {
+                                    acc[k] += 2 * cc;
+                                    if (ck == 1u) tcl[k] += dth;
+                                }
+                                any_near |= nr[k];
+                            }
+                            if (__any_sync(0xffffffffu, any_near)) {
+#pragma unroll
+                                for (int k = 0; k < QPT; k++) {
+                                    const unsigned m = __ballot_sync(0xffffffffu, nr[k]);
+                                    if (!m) continue;
+                                    const int leader = __ffs(m) - 1;
+                                    unsigned long long base = 0;
+                                    if (lane == leader) base = atomicAdd(&A.counters[CNT_NEAR], (unsigned long long)__popc(m));
+                                    base = __shfl_sync(0xffffffffu, base, leader);
+                                    if (nr[k]) {
+                                        const unsigned long long idx = base + __popc(m & lt_mask);
+                                        if (idx < (unsigned long long)A.cap_near) {
+                                            Item it;
+                                            it.q = qid[k];
+                                            it.dom = (uint32_t)U.x;
+                                            it.inst = (uint32_t)j;
+                                            it.rec = (uint32_t)r;
+                                            A.near_items[idx] = it;
+                                        } else {
+                                            fl[k] |= QF_ESCALATE;
+                                        }
+                                    }
+                                }
+                            }
+                        } else if (we) {
+                            const float4 R3 = __ldg(rec + 4 * r + 3);
+#pragma unroll
+                            for (int k = 0; k < QPT; k++) {
+                                const uint32_t ck = (cf >> (2 * k)) & 3u;
+                                int cc;
+                                float dth;
+                                bool slow;
+                                sweep_record_far(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, slow);
+                                if (slow && ck) {
+                                    const double2 p = s_p[k][tid];
+                                    sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
+                                                       xsub(p.y, in.Ty), cc, dth);
+                                }
+                                if (ck) {
+                                    acc[k] += 2 * cc;
+                                    if (ck == 1u) tcl[k] += dth;
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < QPT; k++) {
+                                const uint32_t ck = (cf >> (2 * k)) & 3u;
+                                int cc;
+                                bool slow;
+                                sweep_record_cross(R0, R1, R2, fx[k], fy[k], T[k], cc, slow);
+                                if (slow && ck) {
+                                    const double2 p = s_p[k][tid];
+                                    float dth;
+                                    sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
+                                                       xsub(p.y, in.Ty), cc, dth);
+                                }
+                                if (ck) acc[k] += 2 * cc;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < QPT; k++) two_sum_add(th[k], thl[k], tcl[k]);
+                }
             }
         }
 #pragma unroll
@@ -548,7 +643,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[CNT_UNIT], 1u);
+        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[CNT_UNIT], 1ULL);
         __syncthreads();
         const int u = s_unit;
         if (u >= A.n_units) return;
@@ -643,8 +738,8 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
                             const unsigned m = __ballot_sync(0xffffffffu, nr[k]);
                             if (!m) continue;
                             const int leader = __ffs(m) - 1;
-                            unsigned base = 0;
-                            if (lane == leader) base = atomicAdd(&A.counters[CNT_NEAR], (unsigned)__popc(m));
+                            unsigned long long base = 0;
+                            if (lane == leader) base = atomicAdd(&A.counters[CNT_NEAR], (unsigned long long)__popc(m));
                             base = __shfl_sync(0xffffffffu, base, leader);
                             if (nr[k]) {
                                 const unsigned long long idx = (unsigned long long)base + __popc(m & lt_mask);
@@ -679,72 +774,22 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
 }
 
 // ------------------------------------------------------------------ near pairs, FP32
-// Algorithm 1 in FP32 on query-relative control points.  E bounds the
-// absolute error of every evaluated point against the FP64 value.
-// Returns 0 (cnt valid), 1 (boundary), 2 (a band could not decide: redo in FP64).
-__device__ int near_fp32(const float *qx, const float *qy, int n, float B, float eps, float E,
-                         int &cnt)
-{
-    float st_t[kDepthCap32 + 2], st_x[kDepthCap32 + 2], st_y[kDepthCap32 + 2];
-    int st_d[kDepthCap32 + 2];
-    cnt = 0;
-    float a = 0.f, ax = qx[0], ay = qy[0];
-    float ra = sqrtf(fmaf(ax, ax, ay * ay));
-    {
-        const float er = E + ra * kTwoM22;
-        if (ra + er < eps) return 1;
-        if (ra - er < eps) return 2;
-    }
-    st_t[0] = 1.f;
-    st_x[0] = qx[n];
-    st_y[0] = qy[n];
-    st_d[0] = 0;
-    int sp = 1;
-    bool b_tested = false;
-    while (sp > 0) {
-        const float b = st_t[sp - 1], bx = st_x[sp - 1], by = st_y[sp - 1];
-        const int d = st_d[sp - 1];
-        const float rb = sqrtf(fmaf(bx, bx, by * by));
-        if (!b_tested) {
-            const float er = E + rb * kTwoM22;
-            if (rb + er < eps) return 1;
-            if (rb - er < eps) return 2;
-            b_tested = true;
-        }
-        const float lim = B * (b - a);
-        const float s = (ra + rb) - lim;
-        const float es = 2.f * E + (ra + rb + lim) * (2.f * kTwoM22);
-        if (s > es) {
-            const bool sa = ay > 0.f, sb = by > 0.f;
-            if (sa != sb) {
-                const float D = fmaf(ax, by, -ay * bx);
-                if (fabsf(D) <= kTwoM22 * (fabsf(ax * by) + fabsf(ay * bx))) return 2;
-                if (!sa && sb && D > 0.f) cnt++;
-                else if (sa && !sb && D < 0.f) cnt--;
-            }
-            a = b;
-            ax = bx;
-            ay = by;
-            ra = rb;
-            sp--;
-            b_tested = true;   // the next top was tested when it was pushed
-            continue;
-        }
-        if (s >= -es) return 2;
-        if (d >= kDepthCap32) return 2;
-        const float m = 0.5f * (a + b);
-        float mx, my;
-        bez_eval<float>(qx, qy, n, m, mx, my);
-        st_d[sp - 1] = d + 1;
-        st_t[sp] = m;
-        st_x[sp] = mx;
-        st_y[sp] = my;
-        st_d[sp] = d + 1;
-        sp++;
-        b_tested = false;
-    }
-    return 0;
-}
+// Algorithm 1 in FP32 on query-relative control points, one node per step,
+// with every test under an error band: E bounds the absolute error of each
+// evaluated point against its FP64 value.  When a band cannot settle a
+// decision (eps test, ellipse test, chord sign, depth) the pair becomes an
+// FP64 work item and its FP32 walk stops.
+struct NearWalk {                      // scalars and control points (registers)
+    float qx[kNcp], qy[kNcp];
+    float a, ax, ay, ra, B, E, eps;
+    int n, sp, cnt;
+    bool sa, b_tested;
+};
+
+struct NearStack {                     // the walk's stack (dynamically indexed: local memory)
+    float t[kDepthCap32 + 2], x[kDepthCap32 + 2], y[kDepthCap32 + 2];
+    int d[kDepthCap32 + 2];
+};
 
 struct NearArgs {
     const DomDev *doms;
@@ -753,9 +798,9 @@ struct NearArgs {
     long long cap_near;
     int32_t *acc2;
     uint32_t *flags;
-    Item *f64_items;
+    SubItem *f64_items;
     long long cap_f64;
-    unsigned int *counters;
+    unsigned long long *counters;
 };
 
 __device__ __forceinline__ void item_query(const DomDev *Dp, const PointSrc &src, const Item &it,
@@ -770,45 +815,159 @@ __device__ __forceinline__ void item_query(const DomDev *Dp, const PointSrc &src
     pyp = xsub(y, in.Ty);
 }
 
+__device__ __forceinline__ void emit_f64(const NearArgs &A, const Item &it, float a, float b, uint32_t signs)
+{
+    const unsigned long long idx = atomicAdd(&A.counters[CNT_F64], 1ULL);
+    if (idx < (unsigned long long)A.cap_f64) {
+        SubItem si;
+        si.it = it;
+        si.a = a;
+        si.b = b;
+        si.signs = signs;
+        si.pad = 0;
+        A.f64_items[idx] = si;
+    } else {
+        atomicOr(&A.flags[it.q], QF_ESCALATE);
+    }
+}
+
+// Set up the walk of one near pair.  Returns false when the item needs no
+// walk (already decided: *result 0 done, 1 boundary).
+__device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S,
+                                           int &result)
+{
+    const DomDev *Dp = A.doms + it.dom;
+    double pxp, pyp;
+    item_query(Dp, A.src, it, pxp, pyp);
+    const int s = __ldg(&Dp->rec_seg[it.rec]);
+    const int deg = __ldg(&Dp->seg_deg[s]);
+    const double *P = Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]);
+    float mq = 0.f;
+#pragma unroll
+    for (int k = 0; k < kNcp; k++) {
+        if (k <= deg) {
+            W.qx[k] = (float)(__ldg(P + 2 * k) - pxp);
+            W.qy[k] = (float)(__ldg(P + 2 * k + 1) - pyp);
+            mq = fmaxf(mq, fabsf(W.qx[k]) + fabsf(W.qy[k]));
+        } else {
+            W.qx[k] = 0.f;
+            W.qy[k] = 0.f;
+        }
+    }
+    W.n = deg;
+    W.B = (float)__ldg(&Dp->seg_B[s]);
+    W.E = (float)(2 * deg + 4) * kTwoM24 * mq;
+    W.eps = (float)Dp->eps;
+    W.cnt = 0;
+    W.a = 0.f;
+    W.ax = W.qx[0];
+    W.ay = W.qy[0];
+    W.sa = W.ay > 0.f;                      // exact: the sign of P0.y - p.y
+    W.ra = sqrtf(fmaf(W.ax, W.ax, W.ay * W.ay));
+    const float er = W.E + W.ra * kTwoM22;
+    if (W.ra + er < W.eps) {
+        result = 1;
+        return false;
+    }
+    if (W.ra - er < W.eps) {
+        emit_f64(A, it, 0.f, 1.f, (W.sa ? 1u : 0u) | (W.qy[deg] > 0.f ? 2u : 0u));
+        result = 0;
+        return false;
+    }
+    S.t[0] = 1.f;
+    S.x[0] = W.qx[deg];
+    S.y[0] = W.qy[deg];
+    S.d[0] = 0;
+    W.sp = 1;
+    W.b_tested = false;
+    return true;
+}
+
+// One node of the walk.  Returns 0 while walking, 1 when finished, 2 when the
+// query is certainly on the boundary.
+__device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S)
+{
+    const int sp = W.sp;
+    const float b = S.t[sp - 1], bx = S.x[sp - 1], by = S.y[sp - 1];
+    const int d = S.d[sp - 1];
+    const bool sb = by > 0.f;
+    const float rb = sqrtf(fmaf(bx, bx, by * by));
+    bool undecided = false;
+    if (!W.b_tested) {
+        const float er = W.E + rb * kTwoM22;
+        if (rb + er < W.eps) return 2;
+        undecided = rb - er < W.eps;
+        W.b_tested = true;
+    }
+    const float lim = W.B * (b - W.a);
+    const float s = (W.ra + rb) - lim;
+    const float es = 2.f * W.E + (W.ra + rb + lim) * (2.f * kTwoM22);
+    bool far = false;
+    if (!undecided) {
+        if (s > es) {
+            far = true;
+            if (W.sa != sb) {
+                const float D = fmaf(W.ax, by, -W.ay * bx);
+                if (fabsf(D) <= kTwoM22 * (fabsf(W.ax * by) + fabsf(W.ay * bx))) undecided = true;
+                else if (!W.sa && sb && D > 0.f) W.cnt++;
+                else if (W.sa && !sb && D < 0.f) W.cnt--;
+            }
+        } else if (s >= -es || d >= kDepthCap32) {
+            undecided = true;
+        }
+    }
+    if (undecided) {
+        // the whole pair goes to FP64 (handing over only [a, b] and walking on
+        // costs more: the walk then continues next to the query)
+        emit_f64(A, it, 0.f, 1.f, (W.qy[0] > 0.f ? 1u : 0u) | (W.qy[W.n] > 0.f ? 2u : 0u));
+        W.cnt = 0;
+        W.sp = 0;
+        return 1;
+    }
+    if (far) {
+        W.a = b;
+        W.ax = bx;
+        W.ay = by;
+        W.ra = rb;
+        W.sa = sb;
+        W.sp = sp - 1;
+        W.b_tested = true;  // the next top was tested when it was pushed
+        return W.sp == 0 ? 1 : 0;
+    }
+    const float m = 0.5f * (W.a + b);
+    float mx, my;
+    bez_eval<float>(W.qx, W.qy, W.n, m, mx, my);
+    S.d[sp - 1] = d + 1;
+    S.t[sp] = m;
+    S.x[sp] = mx;
+    S.y[sp] = my;
+    S.d[sp] = d + 1;
+    W.sp = sp + 1;
+    W.b_tested = false;
+    return 0;
+}
+
+// One thread per pair, grid-stride: consecutive queue entries come from
+// neighbouring queries of one tile, so a warp's walks stay similar.
 __global__ void __launch_bounds__(256) k_near(const NearArgs A)
 {
     unsigned long long n = A.counters[CNT_NEAR];
     if (n > (unsigned long long)A.cap_near) n = (unsigned long long)A.cap_near;
+    NearWalk W;
+    NearStack S;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const Item it = A.items[i];
-        const DomDev *Dp = A.doms + it.dom;
-        double pxp, pyp;
-        item_query(Dp, A.src, it, pxp, pyp);
-        const int s = __ldg(&Dp->rec_seg[it.rec]);
-        const int deg = __ldg(&Dp->seg_deg[s]);
-        const double *P = Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]);
-        float qx[kNcp], qy[kNcp];
-        float mq = 0.f;
-#pragma unroll
-        for (int k = 0; k < kNcp; k++) {
-            if (k <= deg) {
-                qx[k] = (float)(__ldg(P + 2 * k) - pxp);
-                qy[k] = (float)(__ldg(P + 2 * k + 1) - pyp);
-                mq = fmaxf(mq, fabsf(qx[k]) + fabsf(qy[k]));
-            } else {
-                qx[k] = 0.f;
-                qy[k] = 0.f;
-            }
+        int res = 0;
+        if (!near_start(A, it, W, S, res)) {
+            if (res == 1) atomicOr(&A.flags[it.q], QF_BOUNDARY);
+            continue;
         }
-        const float B = (float)__ldg(&Dp->seg_B[s]);
-        const float E = (float)(2 * deg + 4) * kTwoM24 * mq;
-        int cnt = 0;
-        const int r = near_fp32(qx, qy, deg, B, (float)Dp->eps, E, cnt);
-        if (r == 2) {
-            const unsigned idx = atomicAdd(&A.counters[CNT_F64], 1u);
-            if (idx < (unsigned long long)A.cap_f64) A.f64_items[idx] = it;
-            else atomicOr(&A.flags[it.q], QF_ESCALATE);
-        } else if (r == 1) {
-            atomicOr(&A.flags[it.q], QF_BOUNDARY);
-        } else if (cnt) {
-            atomicAdd(&A.acc2[it.q], 2 * cnt);
+        int r;
+        while ((r = near_step(A, it, W, S)) == 0) {
         }
+        if (r == 2) atomicOr(&A.flags[it.q], QF_BOUNDARY);
+        else if (W.cnt) atomicAdd(&A.acc2[it.q], 2 * W.cnt);
     }
 }
 
@@ -819,16 +978,18 @@ __global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
     if (n > (unsigned long long)A.cap_f64) n = (unsigned long long)A.cap_f64;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const Item it = A.f64_items[i];
+        const SubItem si = A.f64_items[i];
+        const Item &it = si.it;
         const DomDev *Dp = A.doms + it.dom;
         double pxp, pyp;
         item_query(Dp, A.src, it, pxp, pyp);
         const int s = Dp->rec_seg[it.rec];
-        FarCross fc;
-        const bool bnd = alg1_fp64(Dp->cp + 2 * (size_t)Dp->seg_cp[s], Dp->seg_deg[s], Dp->seg_B[s],
-                                   pxp, pyp, Dp->eps, fc);
+        int cnt = 0;
+        const bool bnd = alg1_fp64_sub(Dp->cp + 2 * (size_t)Dp->seg_cp[s], Dp->seg_deg[s], Dp->seg_B[s],
+                                       pxp, pyp, Dp->eps, (double)si.a, (double)si.b, (si.signs & 1u) != 0,
+                                       (si.signs & 2u) != 0, cnt);
         if (bnd) atomicOr(&A.flags[it.q], QF_BOUNDARY);
-        else if (fc.cnt) atomicAdd(&A.acc2[it.q], 2 * fc.cnt);
+        else if (cnt) atomicAdd(&A.acc2[it.q], 2 * cnt);
     }
 }
 
@@ -905,7 +1066,7 @@ struct FinArgs {
     const float *theta;
     const uint32_t *flags;
     uint2 *esc;
-    unsigned int *counters;
+    unsigned long long *counters;
     OutDst out;
 };
 
@@ -943,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs A)
                 st = om >= 0.5 ? 1 : 0;
             }
             if (esc) {
-                const unsigned idx = atomicAdd(&A.counters[CNT_ESC], 1u);
+                const unsigned long long idx = atomicAdd(&A.counters[CNT_ESC], 1ULL);
                 A.esc[idx] = make_uint2(q, find_dom(A.offsets, A.n_doms, (long long)q));
             } else {
                 write_out(A.out, q, om, st, false);
@@ -964,7 +1125,7 @@ struct EscArgs {
     const DomDev *doms;
     PointSrc src;
     const uint2 *esc;
-    const unsigned int *counters;
+    const unsigned long long *counters;
     OutDst out;
 };
 
@@ -978,8 +1139,8 @@ __global__ void __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
     __shared__ double s_ang[kEscThreads];
     __shared__ int s_bnd[kEscThreads];
     const int tid = threadIdx.x;
-    const unsigned n = A.counters[CNT_ESC];
-    for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
+    const unsigned long long n = A.counters[CNT_ESC];
+    for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
         const uint2 e = A.esc[i];
         const DomDev *Dp = A.doms + e.y;
         double x0, y0;
@@ -1093,7 +1254,7 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
                          int n_units, const int64_t *d_offsets, int64_t n_queries, PointSrc src,
                          OutDst out, const LaunchCfg &cfg, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(W.counters, 0, CNT_N * sizeof(unsigned int), s);
+    cudaError_t e = cudaMemsetAsync(W.counters, 0, CNT_N * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     cudaEvent_t ev[kProfEvents] = {};
     if (cfg.events) {
@@ -1144,11 +1305,8 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     const int sweep_grid = max(1, min(n_units, cfg.n_sm * cfg.tun.sweep_ctas_per_sm));
     mark(1);
     if (cfg.tun.tree) {
-        switch (cfg.tun.qpt) {
-        case 1: k_sweep_tree<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
-        case 4: k_sweep_tree<4><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
-        default: k_sweep_tree<2><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
-        }
+        if (cfg.tun.qpt == 1) k_sweep_tree<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+        else k_sweep_tree<2><<<sweep_grid, kSweepThreads, 0, s>>>(sa);     // the level flags fit 2 slots
     } else {
         switch (cfg.tun.qpt) {
         case 1: k_sweep<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;
@@ -1169,7 +1327,7 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     mark(2);
     k_near<<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
     mark(3);
-    k_f64items<<<cfg.n_sm * 4, 128, 0, s>>>(na);
+    k_f64items<<<cfg.n_sm * 16, 128, 0, s>>>(na);
     mark(4);
     FinArgs fa;
     fa.n = n_queries;

@@ -29,7 +29,7 @@ constexpr int64_t kF64Cap = kMaxQ;
 // byte offsets inside the scratch array (each 256-byte aligned)
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffCounters = 0;
-constexpr size_t kOffUnits = align256(kOffCounters + CNT_N * sizeof(unsigned int));
+constexpr size_t kOffUnits = align256(kOffCounters + CNT_N * sizeof(unsigned long long));
 constexpr size_t kOffOffsets = align256(kOffUnits + kMaxUnits * sizeof(int4));
 constexpr size_t kOffAcc2 = align256(kOffOffsets + 2 * sizeof(int64_t));
 constexpr size_t kOffTheta = align256(kOffAcc2 + kMaxQ * sizeof(int32_t));
@@ -37,7 +37,7 @@ constexpr size_t kOffFlags = align256(kOffTheta + kMaxQ * sizeof(float));
 constexpr size_t kOffEsc = align256(kOffFlags + kMaxQ * sizeof(uint32_t));
 constexpr size_t kOffNear = align256(kOffEsc + kMaxQ * sizeof(uint2));
 constexpr size_t kOffF64 = align256(kOffNear + kNearCap * sizeof(Item));
-constexpr size_t kScratchBytes = align256(kOffF64 + kF64Cap * sizeof(Item));
+constexpr size_t kScratchBytes = align256(kOffF64 + kF64Cap * sizeof(SubItem));
 
 // The scratch itself.  In host code this name is only a stand-in for the
 // symbol: its device address comes from cudaGetSymbolAddress below.
@@ -100,7 +100,7 @@ extern "C" wn_status wn_query_noalloc(const wn_domain *domain, const double *poi
     if (e != cudaSuccess) return WN_ERR_CUDA;
     unsigned char *base = g_addr[dev];
     Work W;
-    W.counters = reinterpret_cast<unsigned int *>(base + kOffCounters);
+    W.counters = reinterpret_cast<unsigned long long *>(base + kOffCounters);
     W.units = reinterpret_cast<int4 *>(base + kOffUnits);
     W.offsets = reinterpret_cast<int64_t *>(base + kOffOffsets);
     W.acc2 = reinterpret_cast<int32_t *>(base + kOffAcc2);
@@ -108,7 +108,7 @@ extern "C" wn_status wn_query_noalloc(const wn_domain *domain, const double *poi
     W.flags = reinterpret_cast<uint32_t *>(base + kOffFlags);
     W.esc_q = reinterpret_cast<uint2 *>(base + kOffEsc);
     W.near_items = reinterpret_cast<Item *>(base + kOffNear);
-    W.f64_items = reinterpret_cast<Item *>(base + kOffF64);
+    W.f64_items = reinterpret_cast<SubItem *>(base + kOffF64);
     W.cap_q = kMaxQ;
     W.cap_near = kNearCap;
     W.cap_f64 = kF64Cap;

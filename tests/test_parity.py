@@ -161,8 +161,10 @@ def test_host_buffers_match_device(wn):
     a = run(wn, doms, qs, 1, host=False)
     b = run(wn, doms, qs, 1, host=True)
     for (w1, s1), (w2, s2) in zip(a, b):
+        # the series length of a far cluster is chosen per warp, so omega may
+        # differ in its last bits with the grouping of queries; states may not
         assert np.array_equal(s1, s2)
-        assert np.array_equal(np.nan_to_num(w1, nan=7.0), np.nan_to_num(w2, nan=7.0))
+        assert np.max(np.abs(np.nan_to_num(w1, nan=7.0) - np.nan_to_num(w2, nan=7.0))) <= 1e-7
 
 
 def test_stats_and_profiling(wn):
