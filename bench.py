@@ -280,7 +280,7 @@ def main():
                 traffic = t.get("bytes_per_launch")
         except Exception:
             traffic = None
-    roof = {"bound": "alu", "kernel": "k_sweep", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+    roof = {"bound": "alu", "kernel": "k_sweep_tree", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
             "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {f_max:.0f} MHz (sm_max_mhz)",
             "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs,
