@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the queries (profiling cases)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -221,7 +222,14 @@ def main():
         n_q = 64 * 4096 * 4096
         pairs = float(sum(ws.n_segments(d) for d in doms)) * 4096 * 4096
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)          # a non-default stream, so calls can replay a graph
+    torch.cuda.set_stream(stream)
+    tuning = None
+    if not grid and not args.no_autotune:
+        tune_ms, tuning = wn.autotune(handles, pts, off, iterations=2, stream=stream)
+    # per-kernel CUDA events in the timed region need direct launches (no graph replay)
+    wn.set_tuning(use_graph=0)
+    tuning = wn.get_tuning()
 
     def step(prec=wn.MIXED):
         if grid:
@@ -356,7 +364,7 @@ def main():
                            "l2": "inputs (16 B/query) larger than L2; 256 MB L2 flush between steps outside the events",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-                "clocks": clocks, "parity": parity,
+                "clocks": clocks, "parity": parity, "tuning": tuning,
                 "escalation": {"near_pairs": st["near_pairs"], "fp64_pairs": st["fp64_pairs"],
                                "fp64_queries": st["fp64_queries"], "overflow": st["overflow"]}}
         line.update(extra)

@@ -175,6 +175,28 @@ wn_status wn_set_tuning(int32_t tile_queries_per_thread, int32_t sweep_ctas_per_
                         int32_t near_ctas_per_sm, int32_t use_graph, int32_t tree,
                         int32_t bucket);
 
+/*
+ * Autotuner of the mixed path.  Times candidate launch shapes on the
+ * caller's own batch and keeps the fastest for the following calls:
+ * coordinate descent from the current setting over queries per sweep thread
+ * {1, 2}, sweep CTAs per SM {2, 3, 4, 6}, near-pair CTAs per SM {4, 8, 16} and
+ * the spatial bucket size {32, 64, 128} queries; each candidate runs one
+ * warm-up call and `iterations` timed calls (CUDA events on `stream`).
+ *   domains, n_domains, point_offsets, points: as in wn_query_batched, with
+ *                points in DEVICE memory (results go to library scratch).
+ *   iterations   timed calls per candidate, 1..100.
+ *   best_ms      host double[1] or NULL: mean time per call of the kept shape.
+ * Synchronises `stream`.  Errors as wn_query_batched.
+ */
+wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains,
+                      const int64_t *point_offsets, const double *points, int32_t iterations,
+                      double *best_ms, wn_stream stream);
+
+/* Current tuning: out6 (host int32[6]) = queries per sweep thread, sweep
+ * CTAs per SM, near-pair CTAs per SM, graph replay, tree sweep, bucket cell
+ * size in queries. */
+wn_status wn_get_tuning(int32_t *out6);
+
 /* Counters of the last mixed call on this thread's device, read after the
  * stream is synchronised: queries, near pairs, pairs escalated to FP64,
  * queries recomputed in FP64, near-queue overflows, device error word. */

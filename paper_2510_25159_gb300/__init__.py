@@ -65,10 +65,13 @@ def lib():
         L.wn_version.restype = ctypes.c_char_p
         L.wn_query_noalloc.argtypes = [P, P, I64, P, P, P]
         L.wn_query_noalloc.restype = ctypes.c_int
+        L.wn_autotune.argtypes = [P, I32, P, P, I32, P, P]
+        L.wn_get_tuning.argtypes = [P]
         L.wn_set_profiling.argtypes = [I32]
         L.wn_kernel_times.argtypes = [P, P]
         for f in ("wn_create_domain", "wn_query", "wn_query_batched", "wn_query_grid_bitmask",
-                  "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times"):
+                  "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times", "wn_autotune",
+                  "wn_get_tuning"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -187,6 +190,23 @@ def query_grid_bitmask(domain, nu, nv, precision=MIXED, stream=None):
     _check(lib().wn_query_grid_bitmask(domain.handle, int(nu), int(nv), _ptr(bits), _ptr(nb),
                                        int(precision), _stream(stream)))
     return bits, nb
+
+
+def autotune(domains, points, offsets, iterations=3, stream=None):
+    """Time candidate launch shapes on this batch (device points) and keep
+    the fastest; returns (best ms per call, tuning dict)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    arr = (ctypes.c_void_p * len(domains))(*[d.handle.value for d in domains])
+    ms = np.zeros(1)
+    _check(lib().wn_autotune(ctypes.cast(arr, ctypes.c_void_p), len(domains), _ptr(off), _ptr(points),
+                             int(iterations), _ptr(ms), _stream(stream)))
+    return float(ms[0]), get_tuning()
+
+
+def get_tuning():
+    t = np.zeros(6, dtype=np.int32)
+    _check(lib().wn_get_tuning(_ptr(t)))
+    return dict(zip(["qpt", "sweep_ctas_per_sm", "near_ctas_per_sm", "use_graph", "tree", "cell_q"], t.tolist()))
 
 
 def set_tuning(qpt=0, sweep_ctas_per_sm=0, near_ctas_per_sm=0, use_graph=-1, tree=-1, bucket=-1):

@@ -36,8 +36,25 @@ struct DevState {
     wn_stats last{};
     bool profiling = false;
     std::vector<cudaEvent_t> events;
+    // CUDA graph of the last captured mixed call, replayed while its launch
+    // parameters (batch layout, buffers, stream, tuning) are unchanged
+    std::vector<uintptr_t> graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;
 };
 DevState g_dev[64];
+
+// A captured graph names buffers and tables by address: any reallocation
+// drops it.
+void drop_graphs()
+{
+    for (DevState &S : g_dev)
+        if (S.graph_exec) {
+            cudaGraphExecDestroy(S.graph_exec);
+            S.graph_exec = nullptr;
+            S.graph_key.clear();
+        }
+}
 
 wn_status fail(wn_status s, const std::string &m)
 {
@@ -62,10 +79,13 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+void drop_graphs();
+
 template <typename T>
 cudaError_t grow(T *&p, int64_t &cap, int64_t need)
 {
     if (need <= cap && p) return cudaSuccess;
+    drop_graphs();
     if (p) {
         cudaDeviceSynchronize();
         cudaFree(p);
@@ -167,6 +187,7 @@ void wn_destroy_domain(wn_domain *d)
     cudaDeviceSynchronize();
     for (void *p : d->allocs) cudaFree(p);
     if (cur != d->device) cudaSetDevice(cur);
+    drop_graphs();
     // batch tables that name this domain must be rebuilt
     for (DevState &S : g_dev)
         for (const wn_domain *k : S.key_doms)
@@ -181,6 +202,7 @@ wn_status wn_set_tuning(int32_t qpt, int32_t sweep_ctas_per_sm, int32_t near_cta
                         int32_t use_graph, int32_t tree, int32_t bucket)
 {
     std::lock_guard<std::mutex> lk(g_mu);
+    drop_graphs();
     if (qpt != 0 && qpt != 1 && qpt != 2 && qpt != 4) return fail(WN_ERR_ARG, "qpt must be 1, 2 or 4");
     if (sweep_ctas_per_sm < 0 || sweep_ctas_per_sm > 8) return fail(WN_ERR_ARG, "sweep_ctas_per_sm 1..8");
     if (near_ctas_per_sm < 0 || near_ctas_per_sm > 16) return fail(WN_ERR_ARG, "near_ctas_per_sm 1..16");
@@ -267,9 +289,11 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                 return cuda_fail(e, "plain kernel");
         }
     } else {
-        const int qpt = g_tun.qpt;
-        const int64_t tile = 256LL * qpt;
-        const bool same = S->key_qpt == qpt && S->key_doms.size() == (size_t)n_domains &&
+        const int qpt = g_tun.tree ? std::min(g_tun.qpt, 2) : g_tun.qpt;
+        // the tree sweep gives each warp its own unit, the flat sweep each CTA
+        const int64_t tile = (g_tun.tree ? 32LL : 256LL) * qpt;
+        const int key = (qpt * 2 + (g_tun.tree ? 1 : 0)) * 4096 + g_tun.cell_q;
+        const bool same = S->key_qpt == key && S->key_doms.size() == (size_t)n_domains &&
                           std::equal(S->key_doms.begin(), S->key_doms.end(), domains) &&
                           S->key_offsets.size() == (size_t)n_domains + 1 &&
                           std::equal(S->key_offsets.begin(), S->key_offsets.end(), offsets);
@@ -310,7 +334,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             if ((e = cudaMemcpy(S->W.offsets, offsets, (n_domains + 1) * sizeof(int64_t),
                                 cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cuda_fail(e, "upload offsets");
-            // spatial buckets: about 64 queries per cell, cells over the domain's
+            // spatial buckets: about cell_q queries per cell, cells over the domain's
             // box (the base tile on periodic axes)
             std::vector<int4> dcell(n_domains);
             std::vector<float4> dbox(n_domains);
@@ -318,7 +342,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             for (int d = 0; d < n_domains; d++) {
                 const DomDev &dv = domains[d]->dev;
                 const int64_t cnt = offsets[d + 1] - offsets[d];
-                const int G = (int)std::min<double>(4096.0, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / 64.0))));
+                const int G = (int)std::min<double>(4096.0, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
                 const double x0 = dv.Pu > 0 ? 0.0 : dv.ox - dv.M, wx = dv.Pu > 0 ? dv.Pu : 2.0 * dv.M;
                 const double y0 = dv.Pv > 0 ? 0.0 : dv.oy - dv.M, wy = dv.Pv > 0 ? dv.Pv : 2.0 * dv.M;
                 dcell[d] = make_int4((int)ncell, G, 0, 0);
@@ -341,13 +365,51 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                 return cuda_fail(e, "upload cells");
             S->key_doms.assign(domains, domains + n_domains);
             S->key_offsets.assign(offsets, offsets + n_domains + 1);
-            S->key_qpt = qpt;
+            S->key_qpt = key;
+            drop_graphs();
         }
         if ((e = ensure_work(S->W, n)) != cudaSuccess) return cuda_fail(e, "scratch");
         LaunchCfg cfg{S->n_sm, g_tun, S->profiling ? &S->events : nullptr};
-        if ((e = launch_mixed(S->W, S->W.doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src,
-                              out, cfg, stream)) != cudaSuccess)
+        // graph replay: only for device buffers on a non-default stream, not while profiling
+        const bool graph = g_tun.use_graph && !S->profiling && stream != nullptr && !h_pts && !h_w && !h_st;
+        if (graph) {
+            std::vector<uintptr_t> gk = {(uintptr_t)stream, (uintptr_t)src.pts, (uintptr_t)out.w,
+                                         (uintptr_t)out.st, (uintptr_t)out.bits, (uintptr_t)out.nbound,
+                                         (uintptr_t)n, (uintptr_t)src.nu, (uintptr_t)src.nv,
+                                         (uintptr_t)S->key_qpt, (uintptr_t)g_tun.sweep_ctas_per_sm,
+                                         (uintptr_t)g_tun.near_ctas_per_sm, (uintptr_t)g_tun.bucket,
+                                         (uintptr_t)S->W.acc2, (uintptr_t)S->W.near_items, (uintptr_t)S->W.perm,
+                                         (uintptr_t)S->W.units, (uintptr_t)S->W.cell_cnt};
+            for (int d = 0; d < n_domains; d++) gk.push_back((uintptr_t)domains[d]);
+            if (!S->graph_exec || gk != S->graph_key) {
+                if (S->graph_exec) {
+                    cudaGraphExecDestroy(S->graph_exec);
+                    S->graph_exec = nullptr;
+                }
+                cudaGraph_t g = nullptr;
+                if ((e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                    return cuda_fail(e, "begin capture");
+                e = launch_mixed(S->W, S->W.doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src, out,
+                                 cfg, stream);
+                cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+                if (e != cudaSuccess || e2 != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return cuda_fail(e != cudaSuccess ? e : e2, "capture");
+                }
+                e = cudaGraphInstantiate(&S->graph_exec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    S->graph_exec = nullptr;
+                    return cuda_fail(e, "graph instantiate");
+                }
+                S->graph_key = gk;
+            }
+            if ((e = cudaGraphLaunch(S->graph_exec, stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+            S->graph_launches++;
+        } else if ((e = launch_mixed(S->W, S->W.doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src,
+                                     out, cfg, stream)) != cudaSuccess) {
             return cuda_fail(e, "mixed kernels");
+        }
         S->last.queries = n;
     }
     if (h_w && (e = cudaMemcpyAsync(out_w, S->st_w, n * sizeof(double), cudaMemcpyDeviceToHost,
@@ -399,6 +461,101 @@ wn_status wn_query_grid_bitmask(const wn_domain *domain, int32_t nu, int32_t nv,
     g.sv = domain->dev.Pv > 0 ? domain->dev.Pv : 1.0;
     return query_impl(&domain, 1, off, nullptr, nullptr, nullptr, precision, (cudaStream_t)stream, g,
                       out_bits, out_boundary);
+}
+
+wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains, const int64_t *point_offsets,
+                      const double *points, int32_t iterations, double *best_ms, wn_stream stream)
+{
+    if (iterations < 1 || iterations > 100) return fail(WN_ERR_ARG, "iterations must be 1..100");
+    if (!point_offsets || n_domains < 0) return fail(WN_ERR_ARG, "bad domain list");
+    if (!points || !is_device_ptr(points)) return fail(WN_ERR_ARG, "autotune needs device points");
+    const int64_t n = point_offsets[n_domains];
+    if (n <= 0) return WN_OK;
+    double *w = nullptr;
+    uint8_t *st = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&w, n * sizeof(double))) != cudaSuccess) return cuda_fail(e, "autotune buffers");
+    if ((e = cudaMalloc(&st, n)) != cudaSuccess) {
+        cudaFree(w);
+        return cuda_fail(e, "autotune buffers");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaStream_t s = (cudaStream_t)stream;
+    Tuning best, saved;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        best = saved = g_tun;
+    }
+    auto trial = [&](const Tuning &t, double &ms) -> wn_status {
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            g_tun = t;
+            g_tun.use_graph = 0;
+        }
+        PointSrc g{};
+        wn_status r = query_impl(domains, n_domains, point_offsets, points, w, st, WN_PREC_MIXED, s, g,
+                                 nullptr, nullptr);
+        if (r != WN_OK) return r;
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < iterations; i++) {
+            r = query_impl(domains, n_domains, point_offsets, points, w, st, WN_PREC_MIXED, s, g, nullptr,
+                           nullptr);
+            if (r != WN_OK) return r;
+        }
+        cudaEventRecord(e1, s);
+        cudaError_t ee = cudaEventSynchronize(e1);
+        if (ee != cudaSuccess) return cuda_fail(ee, "autotune timing");
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        ms = (double)f / iterations;
+        return WN_OK;
+    };
+    double best_t = 0.0;
+    wn_status r = trial(best, best_t);
+    const int qpts[] = {1, 2}, sweeps[] = {2, 3, 4, 6}, nears[] = {4, 8, 16}, cells[] = {32, 64, 128};
+    for (int knob = 0; knob < 4 && r == WN_OK; knob++) {
+        const int *vals = knob == 0 ? qpts : knob == 1 ? sweeps : knob == 2 ? nears : cells;
+        const int nv = knob == 0 ? 2 : knob == 1 ? 4 : 3;
+        for (int i = 0; i < nv && r == WN_OK; i++) {
+            Tuning t = best;
+            int &field = knob == 0 ? t.qpt : knob == 1 ? t.sweep_ctas_per_sm : knob == 2 ? t.near_ctas_per_sm : t.cell_q;
+            if (field == vals[i]) continue;
+            field = vals[i];
+            double ms = 0.0;
+            r = trial(t, ms);
+            if (r == WN_OK && ms < best_t) {
+                best_t = ms;
+                best = t;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_tun = (r == WN_OK) ? best : saved;
+        g_tun.use_graph = saved.use_graph;
+        drop_graphs();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(w);
+    cudaFree(st);
+    if (r == WN_OK && best_ms) *best_ms = best_t;
+    return r;
+}
+
+wn_status wn_get_tuning(int32_t *out6)
+{
+    if (!out6) return fail(WN_ERR_ARG, "out is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    out6[0] = g_tun.qpt;
+    out6[1] = g_tun.sweep_ctas_per_sm;
+    out6[2] = g_tun.near_ctas_per_sm;
+    out6[3] = g_tun.use_graph;
+    out6[4] = g_tun.tree;
+    out6[5] = g_tun.cell_q;
+    return WN_OK;
 }
 
 wn_status wn_set_profiling(int32_t on)

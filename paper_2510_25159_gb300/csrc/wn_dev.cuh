@@ -64,7 +64,7 @@ struct PairDev {
 // Everything a kernel needs about one domain (copied per batch entry).
 struct DomDev {
     int kind, n_loops, n_segs, n_inst, n_rec, n_pairs;
-    int total_cp, pad0;
+    int total_cp, max_deg;              // largest segment degree
     double Pu, Pv, eps;
     double ox, oy;              // origin of the FP32 coordinates
     double nx, ny, PP;          // family normal and Pu*Pv (bi-periodic)
@@ -230,21 +230,22 @@ __device__ __forceinline__ int line_side(const DomDev &D, const InstDev &in, con
 }
 
 // ---------------------------------------------------------------- Bezier
-// gamma(t) by repeated linear interpolation of the control points.
-template <typename T>
-__device__ __forceinline__ void bez_eval(const T *cx, const T *cy, int n, T t, T &ox, T &oy)
+// gamma(t) by repeated linear interpolation of the control points, unrolled
+// for degrees up to NM (lanes with a lower degree n mask the extra steps).
+template <typename T, int NM>
+__device__ __forceinline__ void bez_eval_n(const T *cx, const T *cy, int n, T t, T &ox, T &oy)
 {
-    T qx[kNcp], qy[kNcp];
+    T qx[NM + 1], qy[NM + 1];
 #pragma unroll
-    for (int i = 0; i < kNcp; i++) {
+    for (int i = 0; i <= NM; i++) {
         qx[i] = cx[i];
         qy[i] = cy[i];
     }
-    T s = T(1) - t;
+    const T s = T(1) - t;
 #pragma unroll
-    for (int r = 1; r < kNcp; r++) {
+    for (int r = 1; r <= NM; r++) {
 #pragma unroll
-        for (int i = 0; i < kNcp - r; i++) {
+        for (int i = 0; i <= NM - r; i++) {
             if (i <= n - r) {
                 qx[i] = s * qx[i] + t * qx[i + 1];
                 qy[i] = s * qy[i] + t * qy[i + 1];
@@ -253,6 +254,22 @@ __device__ __forceinline__ void bez_eval(const T *cx, const T *cy, int n, T t, T
     }
     ox = qx[0];
     oy = qy[0];
+}
+
+// Dispatch on an upper bound of the degree (the domain's largest degree,
+// the same for every lane that works on one domain).
+template <typename T>
+__device__ __forceinline__ void bez_eval(const T *cx, const T *cy, int n, int nmax, T t, T &ox, T &oy)
+{
+    switch (nmax) {
+    case 1: bez_eval_n<T, 1>(cx, cy, n, t, ox, oy); break;
+    case 2: bez_eval_n<T, 2>(cx, cy, n, t, ox, oy); break;
+    case 3: bez_eval_n<T, 3>(cx, cy, n, t, ox, oy); break;
+    case 4: bez_eval_n<T, 4>(cx, cy, n, t, ox, oy); break;
+    case 5: bez_eval_n<T, 5>(cx, cy, n, t, ox, oy); break;
+    case 6: bez_eval_n<T, 6>(cx, cy, n, t, ox, oy); break;
+    default: bez_eval_n<T, kMaxDeg>(cx, cy, n, t, ox, oy); break;
+    }
 }
 
 // ---------------------------------------------------------------- Alg. 1, FP64
@@ -285,7 +302,7 @@ struct FarCross {
 // true when the query is on the boundary (an evaluated point closer than eps,
 // or the depth cap).
 template <class Far>
-__device__ bool alg1_fp64(const double *P, int n, double B, double px, double py, double eps,
+__device__ bool alg1_fp64(const double *P, int n, int nmax, double B, double px, double py, double eps,
                           Far &far)
 {
     double cx[kNcp], cy[kNcp];
@@ -318,7 +335,7 @@ __device__ bool alg1_fp64(const double *P, int n, double B, double px, double py
         }
         if (d >= kDepthCap64) return true;
         double m = 0.5 * (a + b), mx, my;
-        bez_eval<double>(cx, cy, n, m, mx, my);
+        bez_eval<double>(cx, cy, n, nmax, m, mx, my);
         st_d[sp - 1] = d + 1;
         st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;
         sp++;
@@ -330,7 +347,7 @@ __device__ bool alg1_fp64(const double *P, int n, double B, double px, double py
 // the signed crossings of the +x ray from (px, py) by its chords; the end
 // points take the given signs (those of the FP32 chain around it).
 // Returns true when the query is on the boundary.
-__device__ inline bool alg1_fp64_sub(const double *P, int n, double B, double px, double py,
+__device__ inline bool alg1_fp64_sub(const double *P, int n, int nmax, double B, double px, double py,
                                      double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
 {
     double cx[kNcp], cy[kNcp];
@@ -343,12 +360,12 @@ __device__ inline bool alg1_fp64_sub(const double *P, int n, double B, double px
     int st_d[kDepthCap64 + 2];
     double gx, gy;
     if (a0 == 0.0) { gx = cx[0]; gy = cy[0]; }
-    else bez_eval<double>(cx, cy, n, a0, gx, gy);
+    else bez_eval<double>(cx, cy, n, nmax, a0, gx, gy);
     double a = a0, ax = gx - px, ay = gy - py;
     bool sa = sa0;
     double ra = sqrt(ax * ax + ay * ay);
     if (b0 == 1.0) { gx = cx[n]; gy = cy[n]; }
-    else bez_eval<double>(cx, cy, n, b0, gx, gy);
+    else bez_eval<double>(cx, cy, n, nmax, b0, gx, gy);
     int d0 = 0;
     for (double w = b0 - a0; w < 1.0 && d0 < kDepthCap64; w *= 2.0) d0++;
     st_t[0] = b0; st_x[0] = gx - px; st_y[0] = gy - py; st_d[0] = d0;
@@ -373,7 +390,7 @@ __device__ inline bool alg1_fp64_sub(const double *P, int n, double B, double px
         if (d >= kDepthCap64) return true;
         const double m = 0.5 * (a + b);
         double mx, my;
-        bez_eval<double>(cx, cy, n, m, mx, my);
+        bez_eval<double>(cx, cy, n, nmax, m, mx, my);
         st_d[sp - 1] = d + 1;
         st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;
         sp++;

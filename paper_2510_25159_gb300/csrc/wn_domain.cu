@@ -481,6 +481,8 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     DomDev &dv = D->dev;
     std::memset(&dv, 0, sizeof dv);
     dv.kind = kind; dv.n_loops = n_loops; dv.n_segs = ns; dv.total_cp = (int)ncp;
+    dv.max_deg = 1;
+    for (int sgi = 0; sgi < ns; sgi++) dv.max_deg = std::max(dv.max_deg, seg_deg[sgi]);
     dv.Pu = Pu; dv.Pv = Pv; dv.eps = eps; dv.ox = ox; dv.oy = oy;
     dv.nx = nx; dv.ny = ny; dv.PP = PP;
     dv.M = (float)M;

@@ -68,6 +68,7 @@ struct Tuning {
     int use_graph = 0;
     int tree = 1;              // 1: cluster sweep with gap-angle expansions; 0: flat sweep
     int bucket = 1;            // 1: bucket queries spatially before the sweep
+    int cell_q = 64;           // target queries per bucket cell
 };
 
 constexpr int kProfEvents = 7;   // events per profiled mixed call (6 intervals)

@@ -295,16 +295,15 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
     constexpr uint64_t SMASK = (1ull << SB) - 1ull;
     static_assert(SB * kTreeMaxLevels <= 64, "level flags must fit 64 bits");
     __shared__ double2 s_p[QPT][kSweepThreads];
-    __shared__ int s_unit;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
 
+    // every warp works on its own units (32*QPT queries): no block barrier
     for (;;) {
-        __syncthreads();
-        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[CNT_UNIT], 1ULL);
-        __syncthreads();
-        const int u = s_unit;
+        unsigned long long uu = 0;
+        if (lane == 0) uu = atomicAdd(&A.counters[CNT_UNIT], 1ULL);
+        const int u = (int)__shfl_sync(0xffffffffu, uu, 0);
         if (u >= A.n_units) return;
         const int4 U = __ldg(&A.units[u]);
         const DomDev *__restrict__ Dp = A.doms + U.x;
@@ -320,7 +319,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
         bool valid[QPT], inc[QPT];
 #pragma unroll
         for (int k = 0; k < QPT; k++) {
-            const int ql = tid * QPT + k;           // a warp owns 32*QPT consecutive positions
+            const int ql = lane * QPT + k;          // the warp owns the unit's 32*QPT positions
             valid[k] = ql < U.z;
             qid[k] = 0;
             double x = 0.0, y = 0.0;
@@ -565,8 +564,9 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
 // the same in any order.
 struct BinArgs {
     const DomDev *doms;
-    const int4 *units;
-    int n_units;
+    const int64_t *offsets;     // per domain: first query
+    int n_doms;
+    long long n;
     PointSrc src;
     const int4 *dcell;          // per domain: first cell, G
     const float4 *dbox;         // per domain: x0, y0, G / width, G / height
@@ -576,16 +576,18 @@ struct BinArgs {
     int n_cells;
 };
 
+__device__ __forceinline__ uint32_t find_dom(const int64_t *off, int n_doms, long long q);
+
 __global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
 {
-    const int4 U = A.units[blockIdx.x];
-    const DomDev *Dp = A.doms + U.x;
-    const int4 dc = A.dcell[U.x];
-    const float4 bx = A.dbox[U.x];
-    for (int i = threadIdx.x; i < U.z; i += blockDim.x) {
-        const uint32_t q = (uint32_t)(U.y + i);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < A.n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const uint32_t d = find_dom(A.offsets, A.n_doms, q);
+        const DomDev *Dp = A.doms + d;
+        const int4 dc = A.dcell[d];
+        const float4 bx = A.dbox[d];
         double x, y;
-        get_point(A.src, q, x, y);
+        get_point(A.src, (uint32_t)q, x, y);
         x = reduce_period(x, Dp->Pu);
         y = reduce_period(y, Dp->Pv);
         int cx = (int)floorf(((float)x - bx.x) * bx.z), cy = (int)floorf(((float)y - bx.y) * bx.w);
@@ -624,11 +626,9 @@ __global__ void __launch_bounds__(1024) k_bin_scan(const BinArgs A)
 
 __global__ void __launch_bounds__(256) k_bin_scatter(const BinArgs A)
 {
-    const int4 U = A.units[blockIdx.x];
-    for (int i = threadIdx.x; i < U.z; i += blockDim.x) {
-        const int q = U.y + i;
-        A.perm[atomicAdd(&A.cnt[A.cell_of[q]], 1)] = q;
-    }
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < A.n;
+         q += (long long)gridDim.x * blockDim.x)
+        A.perm[atomicAdd(&A.cnt[A.cell_of[q]], 1)] = (int)q;
 }
 
 template <int QPT>
@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
 struct NearWalk {                      // scalars and control points (registers)
     float qx[kNcp], qy[kNcp];
     float a, ax, ay, ra, B, E, eps;
-    int n, sp, cnt;
+    int n, nmax, sp, cnt;
     bool sa, b_tested;
 };
 
@@ -855,6 +855,7 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
         }
     }
     W.n = deg;
+    W.nmax = Dp->max_deg;
     W.B = (float)__ldg(&Dp->seg_B[s]);
     W.E = (float)(2 * deg + 4) * kTwoM24 * mq;
     W.eps = (float)Dp->eps;
@@ -936,7 +937,7 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
     }
     const float m = 0.5f * (W.a + b);
     float mx, my;
-    bez_eval<float>(W.qx, W.qy, W.n, m, mx, my);
+    bez_eval<float>(W.qx, W.qy, W.n, W.nmax, m, mx, my);
     S.d[sp - 1] = d + 1;
     S.t[sp] = m;
     S.x[sp] = mx;
@@ -985,7 +986,7 @@ __global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
         item_query(Dp, A.src, it, pxp, pyp);
         const int s = Dp->rec_seg[it.rec];
         int cnt = 0;
-        const bool bnd = alg1_fp64_sub(Dp->cp + 2 * (size_t)Dp->seg_cp[s], Dp->seg_deg[s], Dp->seg_B[s],
+        const bool bnd = alg1_fp64_sub(Dp->cp + 2 * (size_t)Dp->seg_cp[s], Dp->seg_deg[s], Dp->max_deg, Dp->seg_B[s],
                                        pxp, pyp, Dp->eps, (double)si.a, (double)si.b, (si.signs & 1u) != 0,
                                        (si.signs & 2u) != 0, cnt);
         if (bnd) atomicOr(&A.flags[it.q], QF_BOUNDARY);
@@ -1017,7 +1018,7 @@ __device__ void plain_query(const DomDev *Dp, double x0, double y0, double &om, 
         // the planar instance covers every loop of the domain
         const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
         for (int s = sb; s < se && !bnd; s++)
-            bnd = alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]), __ldg(&Dp->seg_deg[s]),
+            bnd = alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]), __ldg(&Dp->seg_deg[s]), Dp->max_deg,
                             __ldg(&Dp->seg_B[s]), qx, qy, eps, fa);
         if (in.type == IT_PE && !bnd) {
             const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
@@ -1164,7 +1165,7 @@ __global__ void __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
             const double qx = xsub(x, in.Tx), qy = xsub(y, in.Ty);
             const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
             for (int sg = sb + tid; sg < se && !bnd; sg += kEscThreads)
-                bnd |= alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[sg]), __ldg(&Dp->seg_deg[sg]),
+                bnd |= alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[sg]), __ldg(&Dp->seg_deg[sg]), Dp->max_deg,
                                  __ldg(&Dp->seg_B[sg]), qx, qy, Dp->eps, fa);
             if (in.type == IT_PE && tid == 0) {
                 const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
@@ -1218,7 +1219,7 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
         cy[k] = k <= deg ? P[2 * k + 1] : 0.0;
     }
     double mx, my;
-    bez_eval<double>(cx, cy, deg, t, mx, my);
+    bez_eval<double>(cx, cy, deg, Dp->max_deg, t, mx, my);
     const double Pu = Dp->Pu, Pv = Dp->Pv;
     const double x = xadd(mx, xmul((double)R.IB, Pu)), y = xadd(my, xmul((double)R.JB, Pv));
     const LoopDev &L = Dp->loops[R.a];
@@ -1237,7 +1238,7 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
         const double qx = (Pu > 0) ? xsub(x, xmul((double)(R.IA + kk * L.hp), Pu)) : x;
         const double qy = (Pv > 0) ? xsub(y, xmul((double)(R.JA + kk * L.hq), Pv)) : y;
         for (int sg = L.s0; sg < L.s1; sg++) {
-            if (alg1_fp64(Dp->cp + 2 * (size_t)Dp->seg_cp[sg], Dp->seg_deg[sg], Dp->seg_B[sg], qx, qy,
+            if (alg1_fp64(Dp->cp + 2 * (size_t)Dp->seg_cp[sg], Dp->seg_deg[sg], Dp->max_deg, Dp->seg_B[sg], qx, qy,
                           Dp->eps, fa)) {
                 out[i] = __longlong_as_double(0x7ff8000000000000ULL);
                 return;
@@ -1276,8 +1277,9 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     if (bucket) {
         BinArgs ba;
         ba.doms = d_doms;
-        ba.units = d_units;
-        ba.n_units = n_units;
+        ba.offsets = d_offsets;
+        ba.n_doms = n_doms;
+        ba.n = n_queries;
         ba.src = src;
         ba.dcell = W.dcell;
         ba.dbox = W.dbox;
@@ -1286,9 +1288,10 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
         ba.perm = W.perm;
         ba.n_cells = W.n_cells;
         if ((e = cudaMemsetAsync(W.cell_cnt, 0, (size_t)W.n_cells * sizeof(int), s)) != cudaSuccess) return e;
-        k_bin_count<<<n_units, 256, 0, s>>>(ba);
+        const int bin_blocks = (int)std::min<long long>((n_queries + 255) / 256, (long long)cfg.n_sm * 32);
+        k_bin_count<<<bin_blocks, 256, 0, s>>>(ba);
         k_bin_scan<<<1, 1024, 0, s>>>(ba);
-        k_bin_scatter<<<n_units, 256, 0, s>>>(ba);
+        k_bin_scatter<<<bin_blocks, 256, 0, s>>>(ba);
     }
     SweepArgs sa;
     sa.doms = d_doms;

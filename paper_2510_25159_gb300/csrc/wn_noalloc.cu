@@ -22,7 +22,7 @@ using namespace wn;
 namespace {
 
 constexpr int64_t kMaxQ = WN_NOALLOC_MAX_QUERIES;
-constexpr int64_t kMaxUnits = (kMaxQ + 255) / 256;        // tiles of at least 256 queries
+constexpr int64_t kMaxUnits = (kMaxQ + 31) / 32;          // tiles of at least 32 queries
 constexpr int64_t kNearCap = 4 * kMaxQ;                   // near pairs; overflow recomputes in FP64
 constexpr int64_t kF64Cap = kMaxQ;
 
@@ -112,9 +112,10 @@ extern "C" wn_status wn_query_noalloc(const wn_domain *domain, const double *poi
     W.cap_q = kMaxQ;
     W.cap_near = kNearCap;
     W.cap_f64 = kF64Cap;
-    Tuning tun;                       // fixed shape: 2 queries per thread
+    Tuning tun;                       // fixed shape: tree sweep, 2 queries per thread
     tun.qpt = 2;
-    const int tile = 256 * tun.qpt;
+    tun.tree = 1;
+    const int tile = 32 * tun.qpt;    // the tree sweep gives each warp one unit
     const int n_units = (int)((n + tile - 1) / tile);
     cudaStream_t s = (cudaStream_t)stream;
     k_fill_units<<<(n_units + 127) / 128, 128, 0, s>>>(W.units, W.offsets, n_units, tile, (int)n);

@@ -196,3 +196,38 @@ def test_sweep_modes(wn, tree, bucket):
             compare(d, q, w, s, TOL_MIXED)
     finally:
         wn.set_tuning(tree=1, bucket=1)
+
+
+def test_graph_replay_and_autotune(wn):
+    """Autotuning keeps results within tolerance; a captured graph replays the
+    same launches on new contents of the same buffers."""
+    import torch
+    doms, qs = ws.config2(n_domains=64, n_uniform=64 * 6000, n_near=64 * 600, domain_subset=[11, 12, 13])
+    handles = [wn.Domain.from_dict(d) for d in doms]
+    pts_h = np.concatenate(qs)
+    off = np.concatenate([[0], np.cumsum([len(q) for q in qs])]).astype(np.int64)
+    stream = torch.cuda.Stream()
+    saved = wn.get_tuning()
+    try:
+        with torch.cuda.stream(stream):
+            pts = torch.from_numpy(pts_h).cuda()
+            ms, tun = wn.autotune(handles, pts, off, iterations=1)
+            assert ms > 0 and tun["qpt"] in (1, 2)
+            wn.set_tuning(use_graph=1)
+            w = torch.empty(len(pts_h), dtype=torch.float64, device="cuda")
+            s = torch.empty(len(pts_h), dtype=torch.uint8, device="cuda")
+            rng = np.random.default_rng(5)
+            for rep in range(3):
+                new = pts_h if rep == 0 else np.concatenate(
+                    [rng.uniform(0, 1, (len(q), 2)) for q in qs])
+                pts.copy_(torch.from_numpy(new))
+                wn.query_batched(handles, pts, off, out_winding=w, out_inside=s)
+                stream.synchronize()
+                wh, sh = w.cpu().numpy(), s.cpu().numpy()
+                for d, a, b in zip(doms, off[:-1], off[1:]):
+                    compare(d, new[a:b], wh[a:b], sh[a:b], TOL_MIXED)
+    finally:
+        wn.set_tuning(qpt=saved["qpt"], sweep_ctas_per_sm=saved["sweep_ctas_per_sm"],
+                      near_ctas_per_sm=saved["near_ctas_per_sm"], use_graph=0)
+        for h in handles:
+            h.close()
