@@ -265,7 +265,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = n_q * world / (ms / 1e3)
-    launches_per_step = 5 * (64 if grid else 1)
+    launches_per_step = int(st["kernels"]) * (len(handles) if grid else 1)
 
     # roofline of the dominant kernel (the sweep): algorithmic FP32 flops / its event time
     props = torch.cuda.get_device_properties(dev)

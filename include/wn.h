@@ -199,7 +199,8 @@ wn_status wn_get_tuning(int32_t *out6);
 
 /* Counters of the last mixed call on this thread's device, read after the
  * stream is synchronised: queries, near pairs, pairs escalated to FP64,
- * queries recomputed in FP64, near-queue overflows, device error word. */
+ * queries recomputed in FP64, near-queue overflows, device error word; and
+ * the number of kernels the last query call (mixed or plain) launched. */
 typedef struct {
     int64_t queries;
     int64_t near_pairs;
@@ -207,6 +208,7 @@ typedef struct {
     int64_t fp64_queries;
     int64_t overflow;
     int64_t device_error;
+    int64_t kernels;
 } wn_stats;
 
 wn_status wn_get_stats(wn_stats *out);

@@ -36,7 +36,8 @@ class WnError(RuntimeError):
 class WnStats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
                 ("fp64_pairs", ctypes.c_int64), ("fp64_queries", ctypes.c_int64),
-                ("overflow", ctypes.c_int64), ("device_error", ctypes.c_int64)]
+                ("overflow", ctypes.c_int64), ("device_error", ctypes.c_int64),
+                ("kernels", ctypes.c_int64)]
 
 
 def library_path() -> str:

@@ -283,11 +283,14 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             return cuda_fail(e, "memset bits");
         if (nbound && (e = cudaMemsetAsync(nbound, 0, 8, stream)) != cudaSuccess)
             return cuda_fail(e, "memset");
+        int64_t kernels = 0;
         for (int d = 0; d < n_domains; d++) {
             const int64_t q0 = offsets[d], cnt = offsets[d + 1] - offsets[d];
             if ((e = launch_plain(domains[d]->d_self, q0, cnt, src, out, stream)) != cudaSuccess)
                 return cuda_fail(e, "plain kernel");
+            kernels += cnt > 0 ? 1 : 0;
         }
+        S->last.kernels = kernels;
     } else {
         const int qpt = g_tun.tree ? std::min(g_tun.qpt, 2) : g_tun.qpt;
         // the tree sweep gives each warp its own unit, the flat sweep each CTA
@@ -411,6 +414,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             return cuda_fail(e, "mixed kernels");
         }
         S->last.queries = n;
+        S->last.kernels = mixed_kernel_count(S->W, cfg);
     }
     if (h_w && (e = cudaMemcpyAsync(out_w, S->st_w, n * sizeof(double), cudaMemcpyDeviceToHost,
                                     stream)) != cudaSuccess)
@@ -613,6 +617,7 @@ wn_status wn_get_stats(wn_stats *out)
     out->fp64_queries = c[CNT_ESC];
     out->overflow = (c[CNT_NEAR] > (unsigned long long)S->W.cap_near) ? (int64_t)(c[CNT_NEAR] - S->W.cap_near) : 0;
     out->device_error = c[CNT_ERR];
+    out->kernels = S->last.kernels;
     return WN_OK;
 }
 

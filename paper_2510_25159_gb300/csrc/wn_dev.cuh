@@ -103,7 +103,12 @@ struct DomDev {
 //       int bits; first/end index records (leaf) or child nodes;
 //   [4] squared distances beyond which 4, 8, 12, 16 terms suffice;
 //   [5] squared distances beyond which 20, 24, 28 terms suffice;
-//   [6 ..] kCluTerms complex coefficients c_k of the Laurent expansion of the
+//   [6] (xmin of every vertex, y of the first record's start, y of the last
+//       record's next vertex, first record as int bits): the pieces below the
+//       node form one polyline from that start to that end, so a query left
+//       of xmin sees crossings = [end above] - [start above];
+//   [7] (end record as int bits, 0, 0, 0);
+//   [8 ..] kCluTerms complex coefficients c_k of the Laurent expansion of the
 //       sum of the cluster's gap angles:
 //         sum_gaps theta = Im sum_k c_k w^k,   w = r_c / (z_c - p),
 //       truncated after K terms with error at most C |w|^(K+1) / (1 - |w|),
@@ -113,7 +118,7 @@ constexpr int kCluRecs = 16;
 constexpr int kTreeArity = 4;
 constexpr int kTreeMaxLevels = 16;
 constexpr int kCluTerms = 32;
-constexpr int kCluCoef = 6;                 // first float4 of the coefficients
+constexpr int kCluCoef = 8;                 // first float4 of the coefficients
 constexpr int kCluF4 = kCluCoef + (kCluTerms + 1) / 2;
 constexpr double kCluTol = 2e-9;
 

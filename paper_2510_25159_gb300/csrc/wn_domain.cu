@@ -331,13 +331,14 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         auto upf = [](double x) { return std::nextafter((float)x, INFINITY); };
         auto make_node = [&](int R0, int R1, bool leaf, int first, int end) {
             double nb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
-            double yr0 = INFINITY, yr1 = -INFINITY, xr1 = -INFINITY;
+            double yr0 = INFINITY, yr1 = -INFINITY, xr1 = -INFINITY, xr0 = INFINITY;
             double gb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
             bool gaps = false;
             for (int r = R0; r < R1; r++) {
                 const double2 a = ra64[r], b = rb64[r], n = rn64[r];
                 for (const double2 &v : {a, b, n}) {
-                    yr0 = std::fmin(yr0, v.y); yr1 = std::fmax(yr1, v.y); xr1 = std::fmax(xr1, v.x);
+                    yr0 = std::fmin(yr0, v.y); yr1 = std::fmax(yr1, v.y);
+                    xr1 = std::fmax(xr1, v.x); xr0 = std::fmin(xr0, v.x);
                 }
                 uint32_t fl;
                 std::memcpy(&fl, &rec[4 * r + 1].w, 4);
@@ -425,6 +426,13 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             std::memcpy(&f0, &first, 4);
             std::memcpy(&f1, &end, 4);
             c[3] = make_float4((float)rc, ff, f0, f1);
+            // the chain's start (record R0's a) and end (record R1-1's next
+            // vertex): the same FP32 values the records hold
+            float rb0, rb1;
+            std::memcpy(&rb0, &R0, 4);
+            std::memcpy(&rb1, &R1, 4);
+            c[6] = make_float4(dn(xr0 - ox), rec[4 * R0].y, rec[4 * (R1 - 1) + 2].w, rb0);
+            c[7] = make_float4(rb1, 0.f, 0.f, 0.f);
             const int id = (int)(nodes.size() / kCluF4);
             for (int i = 0; i < kCluF4; i++) nodes.push_back(c[i]);
             return id;

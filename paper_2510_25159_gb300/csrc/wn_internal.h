@@ -80,6 +80,8 @@ struct LaunchCfg {
 };
 
 // Kernels (wn_kernels.cu)
+bool mixed_buckets(const Work &W, const LaunchCfg &cfg);        // bucketing kernels run
+int mixed_kernel_count(const Work &W, const LaunchCfg &cfg);    // kernels one launch_mixed issues
 cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const int4 *d_units,
                          int n_units, const int64_t *d_offsets, int64_t n_queries, PointSrc src,
                          OutDst out, const LaunchCfg &cfg, cudaStream_t s);

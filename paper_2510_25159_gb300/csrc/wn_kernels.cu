@@ -96,6 +96,15 @@ __device__ __noinline__ void sweep_record_exact(int ridx, uint32_t fl, bool near
     }
 }
 
+// Signed crossings of the +x ray from p by a node's whole polyline when the
+// polyline lies right of p: [end above p] - [start above p], with the exact
+// FP64 comparison for a sign inside its band.  Out of line.
+__device__ __noinline__ int node_span_exact(const DomDev *__restrict__ Dp, int R0, int R1, double pyp)
+{
+    const bool s0 = Dp->rec_a64[R0].y > pyp, s1 = Dp->rec_n64[R1 - 1].y > pyp;
+    return (s1 ? 1 : 0) - (s0 ? 1 : 0);
+}
+
 __device__ __noinline__ float atan2_wide(float y, float x) { return atan2f(y, x); }
 
 // Signed angle atan2(y, x) of a gap seen from the query.  For |y| <= x/4 the
@@ -384,7 +393,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                     const uint32_t f = (uint32_t)((lf >> (lvl * SB)) & SMASK);
                     if (!__any_sync(0xffffffffu, f != 0u)) continue;
                     const float4 *__restrict__ N = nodes + (size_t)kCluF4 * cur;
-                    const float4 nb = __ldg(N), yx = __ldg(N + 1), meta = __ldg(N + 3);
+                    const float4 nb = __ldg(N), yx = __ldg(N + 1), meta = __ldg(N + 3), sp6 = __ldg(N + 6);
                     const int nflags = __float_as_int(meta.y);
                     const bool gaps = nflags & 1, leaf = (nflags & 2) != 0;
                     uint32_t cf = 0u, nearb = 0u, mpb = 0u;
@@ -397,11 +406,12 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                         if (!sk) continue;
                         const bool outside = (fx[k] < nb.x - T[k]) | (fx[k] > nb.y + T[k]) |
                                              (fy[k] < nb.z - T[k]) | (fy[k] > nb.w + T[k]);
-                        const bool cross = !((fy[k] > yx.y + T[k]) | (fy[k] < yx.x - T[k]) | (fx[k] > yx.z + T[k]));
-                        uint32_t child = cross ? 2u : 0u;
+                        // does the +x ray from p meet the node's extent at all?
+                        const bool meets = !((fy[k] > yx.y + T[k]) | (fy[k] < yx.x - T[k]) | (fx[k] > yx.z + T[k]));
+                        bool full = false;     // stays in full mode: descend, crossings at the leaves
                         if (sk == 1u) {
                             if (!outside) {
-                                child = 1u;
+                                full = true;
                                 nearb |= 1u << k;
                             } else if (gaps) {
                                 const float dx = (z.x - fx[k]) + (z.z - fxl[k]);
@@ -414,8 +424,25 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                     kneed = max(kneed, kq);
                                     mpb |= 1u << k;
                                 } else {
-                                    child = 1u;
+                                    full = true;
                                 }
+                            }
+                        }
+                        uint32_t child = full ? 1u : 0u;
+                        if (!full && meets) {
+                            if (fx[k] < sp6.x - T[k]) {
+                                // the node lies right of p: its polyline's crossings
+                                // telescope to [end above] - [start above]
+                                const float d0 = sp6.y - fy[k], d1 = sp6.z - fy[k];
+                                int span = (d1 > 0.f ? 1 : 0) - (d0 > 0.f ? 1 : 0);
+                                if ((fabsf(d0) <= T[k]) | (fabsf(d1) <= T[k])) {
+                                    const double2 p = s_p[k][tid];
+                                    span = node_span_exact(Dp, __float_as_int(sp6.w), __float_as_int(__ldg(&N[7].x)),
+                                                           xsub(p.y, in.Ty));
+                                }
+                                acc[k] += 2 * span;
+                            } else {
+                                child = 2u;    // crossings only, below
                             }
                         }
                         cf |= child << (2 * k);
@@ -1251,6 +1278,17 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
 }
 
 // ------------------------------------------------------------------ launchers
+bool mixed_buckets(const Work &W, const LaunchCfg &cfg)
+{
+    return cfg.tun.tree && cfg.tun.bucket && W.perm && W.cell_of && W.cell_cnt && W.dcell && W.dbox &&
+           W.n_cells > 0;
+}
+
+int mixed_kernel_count(const Work &W, const LaunchCfg &cfg)
+{
+    return 5 + (mixed_buckets(W, cfg) ? 3 : 0);
+}
+
 cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const int4 *d_units,
                          int n_units, const int64_t *d_offsets, int64_t n_queries, PointSrc src,
                          OutDst out, const LaunchCfg &cfg, cudaStream_t s)
@@ -1271,8 +1309,7 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
         e = cudaMemsetAsync(out.nbound, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
-    const bool bucket = cfg.tun.tree && cfg.tun.bucket && W.perm && W.cell_of && W.cell_cnt && W.dcell &&
-                        W.dbox && W.n_cells > 0;
+    const bool bucket = mixed_buckets(W, cfg);
     mark(0);
     if (bucket) {
         BinArgs ba;
