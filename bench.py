@@ -35,9 +35,23 @@ import wn_synth as ws  # noqa: E402
 
 METRIC = "containment queries/s, batched FP32+FP64-fallback vs plain, 0 oracle mismatches"
 UNIT = "queries/s"
-# algorithmic FP32 work of one top-level (query, segment) test of the sweep:
-# ellipse far test ~7 flops + chord angle ~27 flops (atan2 counted as 20)
+# Algorithmic FP32 work, counted by convention (add/sub/mul/compare 1, FMA 2,
+# atan2 20).  A brute-force (query, segment) test: ellipse far test ~7 flops +
+# chord angle ~27 flops.
 FLOPS_PER_PAIR = 34.0
+# Per unit of the tree sweep's work tallies (wn_sweep_work):
+#   node test: near-box test 8, ray-extent test 6, expansion distance and
+#     series-length choice 14, right-of-p test 2
+#   telescoped node: two end signs and their bands 8
+#   expansion sum: w = r_c/(z_c - p) 12, Horner step 8 per term, Im part 3,
+#     compensated add 6
+#   record test with the near check: circle test 7 + chord crossing 10 +
+#     gap-chord crossing 10 + gap angle 17 (odd series, 6 FMA + divide)
+#   record test with crossings and gap angle: 37
+#   record test with crossings only: 20
+WORK_FLOPS = {"node_tests": 30.0, "telescoped_nodes": 8.0, "expansions": 21.0, "expansion_terms": 8.0,
+              "record_tests_near": 44.0, "record_tests_far": 37.0, "record_tests_cross": 20.0,
+              "exact_fp64": 0.0}
 FP32_LANES_PER_SM = 128
 
 
@@ -277,8 +291,18 @@ def main():
         pass
     f_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * f_max * 1e6 / 1e12
-    sweep_ms = ktimes["sweep"] / max(1, ncalls)
-    achieved = pairs * FLOPS_PER_PAIR / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
+    sweep_ms = ktimes["sweep"] / max(1, ncalls)               # per sweep launch
+    launches_sweep = ncalls / max(1, args.steps)                # sweep launches per step
+    # one more step with the counting build of the sweep (outside the timed
+    # region; same decisions, so the same work as each timed step)
+    wn.set_work_counting(True)
+    step()
+    torch.cuda.synchronize()
+    work = wn.sweep_work()
+    wn.set_work_counting(False)
+    flops_launch = sum(WORK_FLOPS[k] * v for k, v in work.items()) / max(1.0, launches_sweep)
+    achieved = flops_launch / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 and flops_launch > 0 else None
+    brute = pairs / max(1.0, launches_sweep) * FLOPS_PER_PAIR / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
     traffic = None
     tf = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if os.path.exists(tf):
@@ -291,7 +315,9 @@ def main():
     roof = {"bound": "alu", "kernel": "k_sweep_tree", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
             "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {f_max:.0f} MHz (sm_max_mhz)",
-            "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs,
+            "algorithmic_flops_per_launch": flops_launch, "work_per_step": work, "flops_per_unit": WORK_FLOPS,
+            "brute_force_equiv": {"tflops": brute, "flops_per_pair": FLOPS_PER_PAIR,
+                                  "pairs_per_step": pairs},
             "kernel_ms": {k: v / max(1, ncalls) for k, v in ktimes.items()}}
 
     extra = {}

@@ -70,9 +70,11 @@ def lib():
         L.wn_get_tuning.argtypes = [P]
         L.wn_set_profiling.argtypes = [I32]
         L.wn_kernel_times.argtypes = [P, P]
+        L.wn_set_work_counting.argtypes = [I32]
+        L.wn_sweep_work.argtypes = [P]
         for f in ("wn_create_domain", "wn_query", "wn_query_batched", "wn_query_grid_bitmask",
                   "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times", "wn_autotune",
-                  "wn_get_tuning"):
+                  "wn_get_tuning", "wn_set_work_counting", "wn_sweep_work"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -235,6 +237,22 @@ def kernel_times():
     n = np.zeros(1, dtype=np.int64)
     _check(lib().wn_kernel_times(_ptr(ms), _ptr(n)))
     return dict(zip(KERNELS, ms.tolist())), int(n[0])
+
+
+WORK = ("node_tests", "telescoped_nodes", "expansions", "expansion_terms", "record_tests_near",
+        "record_tests_far", "record_tests_cross", "exact_fp64")
+
+
+def set_work_counting(on=True):
+    """Run the counting build of the tree sweep in the following mixed calls."""
+    _check(lib().wn_set_work_counting(1 if on else 0))
+
+
+def sweep_work():
+    """Work tallies of the tree sweep since the last read (see WORK)."""
+    c = np.zeros(len(WORK), dtype=np.int64)
+    _check(lib().wn_sweep_work(_ptr(c)))
+    return dict(zip(WORK, c.tolist()))
 
 
 def version():

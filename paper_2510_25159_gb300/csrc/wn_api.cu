@@ -36,6 +36,9 @@ struct DevState {
     wn_stats last{};
     bool profiling = false;
     std::vector<cudaEvent_t> events;
+    // work tallies of the counting build of the tree sweep
+    bool counting = false;
+    unsigned long long *d_work = nullptr;
     // CUDA graph of the last captured mixed call, replayed while its launch
     // parameters (batch layout, buffers, stream, tuning) are unchanged
     std::vector<uintptr_t> graph_key;
@@ -373,8 +376,10 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
         }
         if ((e = ensure_work(S->W, n)) != cudaSuccess) return cuda_fail(e, "scratch");
         LaunchCfg cfg{S->n_sm, g_tun, S->profiling ? &S->events : nullptr};
-        // graph replay: only for device buffers on a non-default stream, not while profiling
-        const bool graph = g_tun.use_graph && !S->profiling && stream != nullptr && !h_pts && !h_w && !h_st;
+        if (S->counting) cfg.work = S->d_work;
+        // graph replay: only for device buffers on a non-default stream, not while profiling or counting
+        const bool graph = g_tun.use_graph && !S->profiling && !S->counting && stream != nullptr && !h_pts &&
+                           !h_w && !h_st;
         if (graph) {
             std::vector<uintptr_t> gk = {(uintptr_t)stream, (uintptr_t)src.pts, (uintptr_t)out.w,
                                          (uintptr_t)out.st, (uintptr_t)out.bits, (uintptr_t)out.nbound,
@@ -572,6 +577,43 @@ wn_status wn_set_profiling(int32_t on)
     for (cudaEvent_t e : S->events) cudaEventDestroy(e);
     S->events.clear();
     S->profiling = on != 0;
+    return WN_OK;
+}
+
+wn_status wn_set_work_counting(int32_t on)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    wn_status st;
+    DevState *S = dev_state(st);
+    if (!S) return st;
+    cudaError_t e;
+    if (on && !S->d_work) {
+        if ((e = cudaMalloc(&S->d_work, WK_N * sizeof(unsigned long long))) != cudaSuccess) {
+            S->d_work = nullptr;
+            return cuda_fail(e, "work tallies");
+        }
+    }
+    if (S->d_work && (e = cudaMemset(S->d_work, 0, WK_N * sizeof(unsigned long long))) != cudaSuccess)
+        return cuda_fail(e, "work tallies");
+    S->counting = on != 0;
+    return WN_OK;
+}
+
+wn_status wn_sweep_work(int64_t *out8)
+{
+    if (!out8) return fail(WN_ERR_ARG, "out8 is NULL");
+    std::lock_guard<std::mutex> lk(g_mu);
+    wn_status st;
+    DevState *S = dev_state(st);
+    if (!S) return st;
+    unsigned long long c[WK_N] = {};
+    cudaError_t e;
+    if (S->d_work) {
+        if ((e = cudaMemcpy(c, S->d_work, sizeof c, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "read work tallies");
+        if ((e = cudaMemset(S->d_work, 0, sizeof c)) != cudaSuccess) return cuda_fail(e, "work tallies");
+    }
+    for (int i = 0; i < WK_N; i++) out8[i] = (int64_t)c[i];
     return WN_OK;
 }
 

@@ -61,6 +61,14 @@ struct Work {
 enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_ERR = 4, CNT_OVF = 5,
        CNT_NEAR_TAKEN = 6, CNT_N = 8 };
 
+// Work tallies of the counting build of the tree sweep (per query slot):
+// node tests, nodes whose crossings telescoped, expansion evaluations and
+// their terms, record tests with the near check (Alg. 1's root step), record
+// tests for crossings and gap angle, record tests for crossings only, exact
+// FP64 recomputations.
+enum { WK_NODE = 0, WK_TELE = 1, WK_EXPANSION = 2, WK_TERMS = 3, WK_REC_NEAR = 4, WK_REC_FAR = 5,
+       WK_REC_CROSS = 6, WK_EXACT = 7, WK_N = 8 };
+
 struct Tuning {
     int qpt = 2;               // queries per sweep thread
     int sweep_ctas_per_sm = 4;
@@ -77,6 +85,7 @@ struct LaunchCfg {
     int n_sm;
     Tuning tun;
     std::vector<cudaEvent_t> *events;  // non-null: record kProfEvents events per call
+    unsigned long long *work = nullptr; // non-null: counting build of the tree sweep adds WK_* here
 };
 
 // Kernels (wn_kernels.cu)

@@ -68,6 +68,7 @@ struct SweepArgs {
     Item *near_items;
     long long cap_near;
     unsigned long long *counters;
+    unsigned long long *work;   // WK_* tallies of the counting build, or null
 };
 
 // Exact recomputation of one record's crossings and gap angle in FP64, for a
@@ -297,7 +298,11 @@ __device__ __forceinline__ float node_gap_sum(const float4 *__restrict__ N, floa
 // crossings (if its +x ray can meet the node); a slot inside the box, or too
 // close, stays full.  Leaves sweep their records for the slots that still
 // need them.  The stack lives in the lanes' registers (entry i in lane i).
-template <int QPT>
+//
+// The CNT build adds per-lane tallies of the work done (WK_*), summed per
+// warp into A.work when the warp runs out of units; its decisions and
+// arithmetic are those of the plain build.
+template <int QPT, bool CNT>
 __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs A)
 {
     constexpr int SB = 2 * QPT;                     // status bits per level
@@ -307,13 +312,25 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    uint32_t wk[WK_N];
+#pragma unroll
+    for (int i = 0; i < WK_N; i++) wk[i] = 0u;
 
     // every warp works on its own units (32*QPT queries): no block barrier
     for (;;) {
         unsigned long long uu = 0;
         if (lane == 0) uu = atomicAdd(&A.counters[CNT_UNIT], 1ULL);
         const int u = (int)__shfl_sync(0xffffffffu, uu, 0);
-        if (u >= A.n_units) return;
+        if (u >= A.n_units) {
+            if constexpr (CNT) {
+#pragma unroll
+                for (int i = 0; i < WK_N; i++) {
+                    const unsigned s = __reduce_add_sync(0xffffffffu, wk[i]);
+                    if (lane == 0 && s) atomicAdd(&A.work[i], (unsigned long long)s);
+                }
+            }
+            return;
+        }
         const int4 U = __ldg(&A.units[u]);
         const DomDev *__restrict__ Dp = A.doms + U.x;
         const double Pu = Dp->Pu, Pv = Dp->Pv, ox = Dp->ox, oy = Dp->oy;
@@ -404,6 +421,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                     for (int k = 0; k < QPT; k++) {
                         const uint32_t sk = (f >> (2 * k)) & 3u;
                         if (!sk) continue;
+                        if constexpr (CNT) wk[WK_NODE]++;
                         const bool outside = (fx[k] < nb.x - T[k]) | (fx[k] > nb.y + T[k]) |
                                              (fy[k] < nb.z - T[k]) | (fy[k] > nb.w + T[k]);
                         // does the +x ray from p meet the node's extent at all?
@@ -439,7 +457,9 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                     const double2 p = s_p[k][tid];
                                     span = node_span_exact(Dp, __float_as_int(sp6.w), __float_as_int(__ldg(&N[7].x)),
                                                            xsub(p.y, in.Ty));
+                                    if constexpr (CNT) wk[WK_EXACT]++;
                                 }
+                                if constexpr (CNT) wk[WK_TELE]++;
                                 acc[k] += 2 * span;
                             } else {
                                 child = 2u;    // crossings only, below
@@ -452,7 +472,13 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                         if (K > 0) {
 #pragma unroll
                             for (int k = 0; k < QPT; k++)
-                                if (mpb >> k & 1u) two_sum_add(th[k], thl[k], node_gap_sum(N, fx[k], fy[k], fxl[k], fyl[k], K));
+                                if (mpb >> k & 1u) {
+                                    two_sum_add(th[k], thl[k], node_gap_sum(N, fx[k], fy[k], fxl[k], fyl[k], K));
+                                    if constexpr (CNT) {
+                                        wk[WK_EXPANSION]++;
+                                        wk[WK_TERMS] += (uint32_t)K;
+                                    }
+                                }
                         }
                     }
                     if (!leaf) {
@@ -501,6 +527,11 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                     const double2 p = s_p[k][tid];
                                     sweep_record_exact(r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
                                                        xsub(p.y, in.Ty), cc, dth);
+                                    if constexpr (CNT) wk[WK_EXACT]++;
+                                }
+                                if constexpr (CNT) {
+                                    if (ck == 1u) wk[WK_REC_NEAR]++;
+                                    else if (ck == 2u) wk[WK_REC_CROSS]++;
                                 }
                                 nr[k] = nr[k] && ck == 1u;
                                 if (ck) {
@@ -546,6 +577,11 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                     const double2 p = s_p[k][tid];
                                     sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
                                                        xsub(p.y, in.Ty), cc, dth);
+                                    if constexpr (CNT) wk[WK_EXACT]++;
+                                }
+                                if constexpr (CNT) {
+                                    if (ck == 1u) wk[WK_REC_FAR]++;
+                                    else if (ck == 2u) wk[WK_REC_CROSS]++;
                                 }
                                 if (ck) {
                                     acc[k] += 2 * cc;
@@ -564,6 +600,10 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                     float dth;
                                     sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
                                                        xsub(p.y, in.Ty), cc, dth);
+                                    if constexpr (CNT) wk[WK_EXACT]++;
+                                }
+                                if constexpr (CNT) {
+                                    if (ck) wk[WK_REC_CROSS]++;
                                 }
                                 if (ck) acc[k] += 2 * cc;
                             }
@@ -1342,11 +1382,18 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     sa.near_items = W.near_items;
     sa.cap_near = W.cap_near;
     sa.counters = W.counters;
+    sa.work = cfg.work;
     const int sweep_grid = max(1, min(n_units, cfg.n_sm * cfg.tun.sweep_ctas_per_sm));
     mark(1);
     if (cfg.tun.tree) {
-        if (cfg.tun.qpt == 1) k_sweep_tree<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
-        else k_sweep_tree<2><<<sweep_grid, kSweepThreads, 0, s>>>(sa);     // the level flags fit 2 slots
+        // the level flags fit 2 slots
+        if (cfg.work) {
+            if (cfg.tun.qpt == 1) k_sweep_tree<1, true><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            else k_sweep_tree<2, true><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+        } else {
+            if (cfg.tun.qpt == 1) k_sweep_tree<1, false><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            else k_sweep_tree<2, false><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+        }
     } else {
         switch (cfg.tun.qpt) {
         case 1: k_sweep<1><<<sweep_grid, kSweepThreads, 0, s>>>(sa); break;

@@ -57,6 +57,7 @@ def test_validation_codes_without_gpu(wnlib):
     assert L.wn_create_domain(P(lo), 1, P(np.array([1], np.int32)), P(np.array([0.0, 0, np.nan, 1])),
                               0.0, 0.0, 0.0, ctypes.byref(h)) == 1
     assert L.wn_set_tuning(3, 0, 0, -1, -1, -1) == 1
+    assert L.wn_sweep_work(None) == 1
     assert L.wn_query(None, None, 0, None, None, 1, None) == 1
     assert L.wn_query_grid_bitmask(None, 4, 4, None, None, 1, None) == 1
 

@@ -179,6 +179,30 @@ def test_stats_and_profiling(wn):
     assert st["overflow"] == 0 and st["device_error"] == 0
 
 
+def test_work_counting_build(wn):
+    """The counting build of the tree sweep decides as the plain build (same
+    states; omega to the last bits, which depend on the order in which near
+    pairs add their angles) and its tallies are consistent: every telescoped
+    node and expansion sum follows a node test, and records are tested."""
+    doms, qs = ws.config2(n_domains=64, n_uniform=64 * 4000, n_near=64 * 500, domain_subset=[3, 4])
+    a = run(wn, doms, qs, 1)
+    wn.set_work_counting(True)
+    try:
+        b = run(wn, doms, qs, 1)
+        work = wn.sweep_work()
+    finally:
+        wn.set_work_counting(False)
+    for (w1, s1), (w2, s2) in zip(a, b):
+        assert np.array_equal(s1, s2)
+        assert np.max(np.abs(np.nan_to_num(w1, nan=7.0) - np.nan_to_num(w2, nan=7.0))) <= 1e-7
+    n_q = sum(len(q) for q in qs)
+    assert work["node_tests"] >= n_q
+    assert work["telescoped_nodes"] + work["expansions"] <= 2 * work["node_tests"]
+    assert 4 * work["expansions"] <= work["expansion_terms"] <= 32 * work["expansions"]
+    assert work["record_tests_near"] > 0 and work["telescoped_nodes"] > 0
+    assert wn.sweep_work()["node_tests"] == 0      # read clears
+
+
 @pytest.mark.parametrize("tree,bucket", [(0, 0), (1, 0), (1, 1)])
 def test_sweep_modes(wn, tree, bucket):
     """Flat sweep, cluster sweep without and with spatial bucketing: all
