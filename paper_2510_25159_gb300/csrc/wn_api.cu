@@ -280,6 +280,11 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
     out.nbound = reinterpret_cast<unsigned long long *>(nbound);
     PointSrc src = grid;
     src.pts = grid.nu ? nullptr : d_pts;
+    // a grid swept by the tree kernel walks 8 x 8 tiles of cells (spatially
+    // coherent warps without the bucketing kernels)
+    const bool grid_tiled = grid.nu > 0 && precision != WN_PREC_PLAIN_FP64 && g_tun.tree &&
+                            (int64_t)((grid.nu + 7) / 8) * ((grid.nv + 7) / 8) * 64 <= (int64_t)INT32_MAX;
+    src.tiles_x = grid_tiled ? (grid.nu + 7) / 8 : 0;
 
     if (precision == WN_PREC_PLAIN_FP64) {
         if (bits && (e = cudaMemsetAsync(bits, 0, (size_t)((n + 31) / 32) * 4, stream)) != cudaSuccess)
@@ -298,9 +303,11 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
         const int qpt = g_tun.tree ? std::min(g_tun.qpt, 2) : g_tun.qpt;
         // the tree sweep gives each warp its own unit, the flat sweep each CTA
         const int64_t tile = (g_tun.tree ? 32LL : 256LL) * qpt;
-        const int key = (qpt * 2 + (g_tun.tree ? 1 : 0)) * 4096 + g_tun.cell_q;
+        const int key = ((qpt * 2 + (g_tun.tree ? 1 : 0)) * 4096 + g_tun.cell_q) * 2 + (grid_tiled ? 1 : 0);
+        // the tables of a one-domain call do not depend on the domain (its
+        // kernels read the domain's own device copy)
         const bool same = S->key_qpt == key && S->key_doms.size() == (size_t)n_domains &&
-                          std::equal(S->key_doms.begin(), S->key_doms.end(), domains) &&
+                          (n_domains == 1 || std::equal(S->key_doms.begin(), S->key_doms.end(), domains)) &&
                           S->key_offsets.size() == (size_t)n_domains + 1 &&
                           std::equal(S->key_offsets.begin(), S->key_offsets.end(), offsets);
         if (!same) {
@@ -308,7 +315,9 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             std::vector<std::pair<double, int4>> u;
             for (int d = 0; d < n_domains; d++) {
                 S->h_doms[d] = domains[d]->dev;
-                const int64_t cnt = offsets[d + 1] - offsets[d];
+                // positions to sweep: the queries, or the cells of every tile of the grid
+                const int64_t cnt = grid_tiled ? (int64_t)src.tiles_x * ((grid.nv + 7) / 8) * 64
+                                               : offsets[d + 1] - offsets[d];
                 // sweep cost of one query of this domain: records of every instance
                 const double work = (double)std::max<int64_t>(domains[d]->sweep_records, 1);
                 for (int64_t q0 = 0; q0 < cnt; q0 += tile) {
@@ -340,33 +349,21 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             if ((e = cudaMemcpy(S->W.offsets, offsets, (n_domains + 1) * sizeof(int64_t),
                                 cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cuda_fail(e, "upload offsets");
-            // spatial buckets: about cell_q queries per cell, cells over the domain's
-            // box (the base tile on periodic axes)
+            // spatial buckets: about cell_q queries per cell; G x G cells per
+            // domain (the bucketing kernel lays them over the domain's box)
             std::vector<int4> dcell(n_domains);
-            std::vector<float4> dbox(n_domains);
             int64_t ncell = 0;
             for (int d = 0; d < n_domains; d++) {
-                const DomDev &dv = domains[d]->dev;
                 const int64_t cnt = offsets[d + 1] - offsets[d];
                 const int G = (int)std::min<double>(4096.0, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
-                const double x0 = dv.Pu > 0 ? 0.0 : dv.ox - dv.M, wx = dv.Pu > 0 ? dv.Pu : 2.0 * dv.M;
-                const double y0 = dv.Pv > 0 ? 0.0 : dv.oy - dv.M, wy = dv.Pv > 0 ? dv.Pv : 2.0 * dv.M;
                 dcell[d] = make_int4((int)ncell, G, 0, 0);
-                dbox[d] = make_float4((float)x0, (float)y0, (float)(G / wx), (float)(G / wy));
                 ncell += (int64_t)G * G;
             }
             if (ncell > INT32_MAX) return fail(WN_ERR_LIMIT, "too many query cells");
-            {
-                int64_t c1 = S->W.cap_dbin, c2 = S->W.cap_dbin;
-                if ((e = grow(S->W.dcell, c1, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
-                if ((e = grow(S->W.dbox, c2, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
-                S->W.cap_dbin = std::min(c1, c2);
-            }
+            if ((e = grow(S->W.dcell, S->W.cap_dbin, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
             if ((e = grow(S->W.cell_cnt, S->W.cap_cells, ncell)) != cudaSuccess) return cuda_fail(e, "cells");
             S->W.n_cells = (int)ncell;
             if ((e = cudaMemcpy(S->W.dcell, dcell.data(), n_domains * sizeof(int4), cudaMemcpyHostToDevice)) !=
-                    cudaSuccess ||
-                (e = cudaMemcpy(S->W.dbox, dbox.data(), n_domains * sizeof(float4), cudaMemcpyHostToDevice)) !=
                     cudaSuccess)
                 return cuda_fail(e, "upload cells");
             S->key_doms.assign(domains, domains + n_domains);
@@ -377,6 +374,8 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
         if ((e = ensure_work(S->W, n)) != cudaSuccess) return cuda_fail(e, "scratch");
         LaunchCfg cfg{S->n_sm, g_tun, S->profiling ? &S->events : nullptr};
         if (S->counting) cfg.work = S->d_work;
+        cfg.grid_tiled = grid_tiled;
+        const DomDev *d_doms = n_domains == 1 ? domains[0]->d_self : S->W.doms;
         // graph replay: only for device buffers on a non-default stream, not while profiling or counting
         const bool graph = g_tun.use_graph && !S->profiling && !S->counting && stream != nullptr && !h_pts &&
                            !h_w && !h_st;
@@ -397,7 +396,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                 cudaGraph_t g = nullptr;
                 if ((e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                     return cuda_fail(e, "begin capture");
-                e = launch_mixed(S->W, S->W.doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src, out,
+                e = launch_mixed(S->W, d_doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src, out,
                                  cfg, stream);
                 cudaError_t e2 = cudaStreamEndCapture(stream, &g);
                 if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -414,7 +413,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             }
             if ((e = cudaGraphLaunch(S->graph_exec, stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
             S->graph_launches++;
-        } else if ((e = launch_mixed(S->W, S->W.doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src,
+        } else if ((e = launch_mixed(S->W, d_doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src,
                                      out, cfg, stream)) != cudaSuccess) {
             return cuda_fail(e, "mixed kernels");
         }

@@ -85,7 +85,8 @@ struct DomDev {
     const double2 *rec_b64;     // [n_rec] exact chord end
     const double2 *rec_n64;     // [n_rec] exact next vertex
     const float4 *nodes;        // [kCluF4 * n_nodes] record tree, see below
-    int n_nodes, pad3;
+    int n_nodes;
+    int all_root;               // planar: root over every loop (-1: per-loop roots)
 };
 
 // Record tree: per loop, leaves over runs of at most kCluRecs consecutive
@@ -120,7 +121,11 @@ constexpr int kTreeMaxLevels = 16;
 constexpr int kCluTerms = 32;
 constexpr int kCluCoef = 8;                 // first float4 of the coefficients
 constexpr int kCluF4 = kCluCoef + (kCluTerms + 1) / 2;
-constexpr double kCluTol = 2e-9;
+// Truncation error allowed per expansion sum, radians.  Even a query that
+// takes 150 expansion sums stays below 1.5e-5 rad (2.4e-6 in omega): inside
+// the 1e-5 omega tolerance of the mixed path and far inside its 1e-4
+// classification band.
+constexpr double kCluTol = 1e-7;
 
 // Near / FP64 work item.
 struct Item {

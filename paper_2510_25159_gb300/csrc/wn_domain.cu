@@ -326,15 +326,23 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     // expansion of its gap angles
     std::vector<float4> nodes;
     std::vector<int> loop_root(n_loops, -1);
+    int all_root = -1;          // planar: root of the tree over all loops
     {
         auto dn = [](double x) { return std::nextafter((float)x, -INFINITY); };
         auto upf = [](double x) { return std::nextafter((float)x, INFINITY); };
-        auto make_node = [&](int R0, int R1, bool leaf, int first, int end) {
+        // one node over the records of `ranges`; a group node (several whole
+        // loops, each a closed chain) has no chain ends: its crossings of a ray
+        // that passes right of all its vertices cancel, so its end values are
+        // +inf (both above every query)
+        auto make_node_r = [&](const std::vector<std::pair<int, int>> &ranges, bool leaf, int first, int end,
+                               bool group) {
+            const int R0 = ranges.front().first, R1 = ranges.back().second;
             double nb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
             double yr0 = INFINITY, yr1 = -INFINITY, xr1 = -INFINITY, xr0 = INFINITY;
             double gb[4] = {INFINITY, -INFINITY, INFINITY, -INFINITY};
             bool gaps = false;
-            for (int r = R0; r < R1; r++) {
+            for (const auto &rg : ranges)
+            for (int r = rg.first; r < rg.second; r++) {
                 const double2 a = ra64[r], b = rb64[r], n = rn64[r];
                 for (const double2 &v : {a, b, n}) {
                     yr0 = std::fmin(yr0, v.y); yr1 = std::fmax(yr1, v.y);
@@ -367,7 +375,8 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
                 zx = 0.5 * (gb[0] + gb[1]);
                 zy = 0.5 * (gb[2] + gb[3]);
                 double Cb = 0.0;
-                for (int r = R0; r < R1; r++) {
+                for (const auto &rg : ranges)
+                for (int r = rg.first; r < rg.second; r++) {
                     uint32_t fl;
                     std::memcpy(&fl, &rec[4 * r + 1].w, 4);
                     if (!(fl & RF_GAP)) continue;
@@ -377,7 +386,8 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
                 rc = std::fmax(rc, 1e-300);
                 // M_k = sum_gaps (n - z)^k - (b - z)^k ;  c_k = (-1)^(k+1) M_k / (k rc^k)
                 double Mre[kCluTerms + 1] = {}, Mim[kCluTerms + 1] = {};
-                for (int r = R0; r < R1; r++) {
+                for (const auto &rg : ranges)
+                for (int r = rg.first; r < rg.second; r++) {
                     uint32_t fl;
                     std::memcpy(&fl, &rec[4 * r + 1].w, 4);
                     if (!(fl & RF_GAP)) continue;
@@ -431,12 +441,17 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             float rb0, rb1;
             std::memcpy(&rb0, &R0, 4);
             std::memcpy(&rb1, &R1, 4);
-            c[6] = make_float4(dn(xr0 - ox), rec[4 * R0].y, rec[4 * (R1 - 1) + 2].w, rb0);
+            if (group) c[6] = make_float4(dn(xr0 - ox), INFINITY, INFINITY, 0.f);
+            else c[6] = make_float4(dn(xr0 - ox), rec[4 * R0].y, rec[4 * (R1 - 1) + 2].w, rb0);
             c[7] = make_float4(rb1, 0.f, 0.f, 0.f);
             const int id = (int)(nodes.size() / kCluF4);
             for (int i = 0; i < kCluF4; i++) nodes.push_back(c[i]);
             return id;
         };
+        auto make_node = [&](int R0, int R1, bool leaf, int first, int end) {
+            return make_node_r({{R0, R1}}, leaf, first, end, false);
+        };
+        int max_depth = 0;
         for (int l = 0; l < n_loops; l++) {
             if (loop_r1[l] == loop_r0[l]) continue;
             std::vector<int> level, lr0, lr1;       // node ids and their record ranges
@@ -446,7 +461,9 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
                 lr0.push_back(r0);
                 lr1.push_back(r1);
             }
+            int depth = 1;
             while (level.size() > 1) {
+                depth++;
                 std::vector<int> up_level, u0, u1;
                 for (size_t i = 0; i < level.size(); i += kTreeArity) {
                     const size_t j = std::min(level.size(), i + kTreeArity);
@@ -459,6 +476,56 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
                 lr1.swap(u1);
             }
             loop_root[l] = level[0];
+            max_depth = std::max(max_depth, depth);
+        }
+        // planar domains: a tree over the loops themselves, so that a query
+        // far from a group of loops (holes, islands) tests the group once.
+        // Loops in Morton order of their box centres; the loop roots are
+        // copied into one contiguous run to serve as the first level.
+        std::vector<int> live;
+        for (int l = 0; l < n_loops; l++)
+            if (loop_root[l] >= 0) live.push_back(l);
+        int group_levels = 0;
+        for (size_t m = live.size(); m > 1; m = (m + kTreeArity - 1) / kTreeArity) group_levels++;
+        if (kind == DK_PLANAR && live.size() == 1) {
+            all_root = loop_root[live[0]];
+        } else if (kind == DK_PLANAR && live.size() > 1 && max_depth + group_levels <= kTreeMaxLevels) {
+            auto morton = [&](int l) {
+                const HostLoop &L = loops[l];
+                const double cx = 0.5 * (L.box[0] + L.box[1]), cy = 0.5 * (L.box[2] + L.box[3]);
+                const double w = std::fmax(bx1 - bx0, 1e-300), h = std::fmax(by1 - by0, 1e-300);
+                const uint32_t ix = (uint32_t)std::fmin(65535.0, std::fmax(0.0, (cx - bx0) / w * 65536.0));
+                const uint32_t iy = (uint32_t)std::fmin(65535.0, std::fmax(0.0, (cy - by0) / h * 65536.0));
+                uint64_t code = 0;
+                for (int bit = 0; bit < 16; bit++)
+                    code |= (uint64_t)((ix >> bit) & 1u) << (2 * bit) | (uint64_t)((iy >> bit) & 1u) << (2 * bit + 1);
+                return code;
+            };
+            std::vector<uint64_t> key(n_loops, 0);
+            for (int l : live) key[l] = morton(l);
+            std::stable_sort(live.begin(), live.end(), [&](int x, int y) { return key[x] < key[y]; });
+            std::vector<int> level;
+            std::vector<std::vector<std::pair<int, int>>> lrng;
+            for (int l : live) {
+                const int id = (int)(nodes.size() / kCluF4);
+                for (int i = 0; i < kCluF4; i++) nodes.push_back(nodes[(size_t)kCluF4 * loop_root[l] + i]);
+                level.push_back(id);
+                lrng.push_back({{loop_r0[l], loop_r1[l]}});
+            }
+            while (level.size() > 1) {
+                std::vector<int> up_level;
+                std::vector<std::vector<std::pair<int, int>>> urng;
+                for (size_t i = 0; i < level.size(); i += kTreeArity) {
+                    const size_t j = std::min(level.size(), i + kTreeArity);
+                    std::vector<std::pair<int, int>> rg;
+                    for (size_t t = i; t < j; t++) rg.insert(rg.end(), lrng[t].begin(), lrng[t].end());
+                    up_level.push_back(make_node_r(rg, false, level[i], level[j - 1] + 1, true));
+                    urng.push_back(rg);
+                }
+                level.swap(up_level);
+                lrng.swap(urng);
+            }
+            all_root = level[0];
         }
     }
 
@@ -507,6 +574,7 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     dv.rec_b64 = up.up(rb64);
     dv.rec_n64 = up.up(rn64);
     dv.n_nodes = (int)(nodes.size() / kCluF4);
+    dv.all_root = all_root;
     dv.nodes = up.up(nodes);
     if (up.err != cudaSuccess) return fail(up.err == cudaErrorMemoryAllocation ? 4 : 3,
                                            std::string("CUDA: ") + cudaGetErrorString(up.err));

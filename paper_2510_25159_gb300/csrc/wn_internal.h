@@ -25,6 +25,7 @@ struct PointSrc {
     const double *pts;         // x,y interleaved, indexed by global query index
     int32_t nu, nv;            // grid mode when pts == nullptr
     double su, sv;             // grid scale (period or 1)
+    int32_t tiles_x;           // grid mode, tree sweep: positions walk 8 x 8 tiles, this many per row
 };
 
 // Output of a query call.
@@ -52,7 +53,6 @@ struct Work {
     int *perm = nullptr;       // per query
     int *cell_cnt = nullptr;   // per cell
     int4 *dcell = nullptr;     // per domain: first cell, G
-    float4 *dbox = nullptr;    // per domain: x0, y0, G / width, G / height
     int n_cells = 0;
     int64_t cap_bin_q = 0, cap_cells = 0, cap_dbin = 0;
     int64_t cap_q = 0, cap_near = 0, cap_f64 = 0, cap_units = 0, cap_doms = 0, cap_off = 0;
@@ -86,6 +86,7 @@ struct LaunchCfg {
     Tuning tun;
     std::vector<cudaEvent_t> *events;  // non-null: record kProfEvents events per call
     unsigned long long *work = nullptr; // non-null: counting build of the tree sweep adds WK_* here
+    bool grid_tiled = false;            // grid positions in 8 x 8 tiles instead of bucketing
 };
 
 // Kernels (wn_kernels.cu)

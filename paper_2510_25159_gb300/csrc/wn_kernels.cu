@@ -32,7 +32,9 @@ namespace wn {
 constexpr float kTwoM22 = 2.384185791015625e-7f;   // 2^-22
 constexpr float kTwoM24 = 5.9604644775390625e-8f;  // 2^-24
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr double kOmegaBand = 1e-4;                 // classification band of the mixed path
+constexpr float kOmegaBandF = 1e-4f;               // classification band of the mixed path
+constexpr double kInv2Pi = 0.15915494309189533576888376337251;
+constexpr float kInv2PiF = 0.15915494309189533577f;
 constexpr int kSweepThreads = 256;
 constexpr int kChunk = 64;                          // records per shared-memory stage
 
@@ -267,28 +269,47 @@ __device__ __forceinline__ void sweep_record_cross(const float4 R0, const float4
     }
 }
 
-// Sum of a node's gap angles at the query from its Laurent expansion,
-// Im sum_{k<K} c_k w^k with w = r_c / (z_c - p); K is uniform across the warp.
-__device__ __forceinline__ float node_gap_sum(const float4 *__restrict__ N, float fx, float fy, float fxl,
-                                              float fyl, int K)
+// Sum of a node's gap angles at each of the QPT queries of a thread from the
+// node's Laurent expansion, Im sum_{k<K} c_k w^k with w = r_c / (z_c - p),
+// by Horner's rule; slot k only when use[k] (uniform across the warp).  One
+// coefficient load per term serves every slot; K is a multiple of 4 and
+// uniform across the warp.
+template <int QPT>
+__device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, const float *fx, const float *fy,
+                                              const float *fxl, const float *fyl, const bool *use, int K,
+                                              float *out)
 {
     const float4 z = __ldg(N + 2);
-    const float dx = (z.x - fx) + (z.z - fxl);
-    const float dy = (z.y - fy) + (z.w - fyl);
-    const float inv = __fdividef(__ldg(&N[3].x), fmaf(dx, dx, dy * dy));
-    const float wr = dx * inv, wi = -dy * inv;
+    const float rc = __ldg(&N[3].x);
+    float wr[QPT], wi[QPT], sr[QPT], si[QPT];
     const float2 *cf = reinterpret_cast<const float2 *>(N + kCluCoef);
-    float2 c = __ldg(cf + (K - 1));
-    float sr = c.x, si = c.y;
-    for (int k = K - 2; k >= 0; k--) {
-        c = __ldg(cf + k);
-        const float tr = fmaf(sr, wr, fmaf(-si, wi, c.x));
-        const float ti = fmaf(sr, wi, fmaf(si, wr, c.y));
-        sr = tr;
-        si = ti;
+    const float2 cl = __ldg(cf + (K - 1));
+#pragma unroll
+    for (int k = 0; k < QPT; k++) {
+        const float dx = (z.x - fx[k]) + (z.z - fxl[k]);
+        const float dy = (z.y - fy[k]) + (z.w - fyl[k]);
+        const float inv = __fdividef(rc, fmaf(dx, dx, dy * dy));
+        wr[k] = dx * inv;
+        wi[k] = -dy * inv;
+        sr[k] = cl.x;
+        si[k] = cl.y;
     }
-    return fmaf(sr, wi, si * wr);
+#pragma unroll 4
+    for (int t = K - 2; t >= 0; t--) {
+        const float2 c = __ldg(cf + t);
+#pragma unroll
+        for (int k = 0; k < QPT; k++) {
+            if (!use[k]) continue;
+            const float tr = fmaf(sr[k], wr[k], fmaf(-si[k], wi[k], c.x));
+            const float ti = fmaf(sr[k], wi[k], fmaf(si[k], wr[k], c.y));
+            sr[k] = tr;
+            si[k] = ti;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < QPT; k++) out[k] = fmaf(sr[k], wi[k], si[k] * wr[k]);
 }
+
 
 // Warp-synchronous walk of the record trees of every loop an instance
 // covers.  Each query slot carries a status per tree level: 1 = full (gap
@@ -350,8 +371,20 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
             qid[k] = 0;
             double x = 0.0, y = 0.0;
             if (valid[k]) {
-                qid[k] = A.perm ? (uint32_t)__ldg(&A.perm[U.y + ql]) : (uint32_t)(U.y + ql);
-                get_point(A.src, qid[k], x, y);
+                const uint32_t pos = (uint32_t)(U.y + ql);
+                if (A.perm) {
+                    qid[k] = (uint32_t)__ldg(&A.perm[pos]);
+                } else if (A.src.tiles_x) {
+                    // grid in 8 x 8 tiles, row-major: position -> cell
+                    const uint32_t t = pos >> 6, j = pos & 63u;
+                    const uint32_t ci = (t % (uint32_t)A.src.tiles_x) * 8u + (j & 7u);
+                    const uint32_t cj = (t / (uint32_t)A.src.tiles_x) * 8u + (j >> 3);
+                    valid[k] = ci < (uint32_t)A.src.nu && cj < (uint32_t)A.src.nv;
+                    qid[k] = valid[k] ? cj * (uint32_t)A.src.nu + ci : 0u;
+                } else {
+                    qid[k] = pos;
+                }
+                if (valid[k]) get_point(A.src, qid[k], x, y);
             }
             s_p[k][tid] = make_double2(reduce_period(x, Pu), reduce_period(y, Pv));
             acc[k] = 0;
@@ -390,10 +423,13 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                 any |= inc[k];
             }
             if (!__any_sync(0xffffffffu, any)) continue;
+            // a planar domain's loops hang below one root; otherwise each
+            // loop the instance covers is walked from its own root
+            const bool one_root = in.type == IT_ALL && Dp->all_root >= 0;
             const int l0 = (in.type == IT_ALL) ? 0 : in.loop;
-            const int l1 = (in.type == IT_ALL) ? Dp->n_loops : in.loop + 1;
+            const int l1 = one_root ? 1 : (in.type == IT_ALL) ? Dp->n_loops : in.loop + 1;
             for (int l = l0; l < l1; l++) {
-                const int root = Dp->loops[l].root;
+                const int root = one_root ? Dp->all_root : Dp->loops[l].root;
                 if (root < 0) continue;
                 uint64_t lf = 0;
 #pragma unroll
@@ -470,10 +506,15 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                     if (gaps) {
                         const int K = __reduce_max_sync(0xffffffffu, kneed);
                         if (K > 0) {
+                            bool use[QPT];
+#pragma unroll
+                            for (int k = 0; k < QPT; k++) use[k] = __any_sync(0xffffffffu, (mpb >> k) & 1u);
+                            float gs[QPT];
+                            node_gap_sums<QPT>(N, fx, fy, fxl, fyl, use, K, gs);
 #pragma unroll
                             for (int k = 0; k < QPT; k++)
                                 if (mpb >> k & 1u) {
-                                    two_sum_add(th[k], thl[k], node_gap_sum(N, fx[k], fy[k], fxl[k], fyl[k], K));
+                                    two_sum_add(th[k], thl[k], gs[k]);
                                     if constexpr (CNT) {
                                         wk[WK_EXPANSION]++;
                                         wk[WK_TERMS] += (uint32_t)K;
@@ -636,7 +677,6 @@ struct BinArgs {
     long long n;
     PointSrc src;
     const int4 *dcell;          // per domain: first cell, G
-    const float4 *dbox;         // per domain: x0, y0, G / width, G / height
     int *cell_of;               // per query
     int *cnt;                   // per cell: count, then cursor
     int *perm;
@@ -652,7 +692,13 @@ __global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
         const uint32_t d = find_dom(A.offsets, A.n_doms, q);
         const DomDev *Dp = A.doms + d;
         const int4 dc = A.dcell[d];
-        const float4 bx = A.dbox[d];
+        // G x G cells over the domain's box (the base tile on periodic axes);
+        // FP32 is enough to choose a cell
+        const float x0 = Dp->Pu > 0 ? 0.f : (float)Dp->ox - Dp->M;
+        const float y0 = Dp->Pv > 0 ? 0.f : (float)Dp->oy - Dp->M;
+        const float wx = Dp->Pu > 0 ? (float)Dp->Pu : 2.f * Dp->M;
+        const float wy = Dp->Pv > 0 ? (float)Dp->Pv : 2.f * Dp->M;
+        const float4 bx = make_float4(x0, y0, __fdividef((float)dc.y, wx), __fdividef((float)dc.y, wy));
         double x, y;
         get_point(A.src, (uint32_t)q, x, y);
         x = reduce_period(x, Dp->Pu);
@@ -1167,9 +1213,15 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs A)
                 st = 2;
                 om = __longlong_as_double(0x7ff8000000000000ULL);
             } else {
-                om = 0.5 * (double)A.acc2[q] - (double)A.theta[q] / kTwoPi;
-                if (fabs(om - 0.5) < kOmegaBand) esc = true;
-                st = om >= 0.5 ? 1 : 0;
+                // classify in FP32 (its error, ~1e-7 of the terms, is far
+                // inside the band); omega itself in FP64 only when asked for
+                const int a2 = A.acc2[q];
+                const float th = A.theta[q];
+                const float om32 = fmaf(-th, kInv2PiF, 0.5f * (float)a2);
+                const float band = kOmegaBandF + 1e-6f * (fabsf(0.5f * (float)a2) + fabsf(th) * kInv2PiF);
+                if (fabsf(om32 - 0.5f) < band) esc = true;
+                st = om32 >= 0.5f ? 1 : 0;
+                if (A.out.w) om = 0.5 * (double)a2 - (double)th * kInv2Pi;
             }
             if (esc) {
                 const unsigned long long idx = atomicAdd(&A.counters[CNT_ESC], 1ULL);
@@ -1320,7 +1372,7 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
 // ------------------------------------------------------------------ launchers
 bool mixed_buckets(const Work &W, const LaunchCfg &cfg)
 {
-    return cfg.tun.tree && cfg.tun.bucket && W.perm && W.cell_of && W.cell_cnt && W.dcell && W.dbox &&
+    return cfg.tun.tree && cfg.tun.bucket && !cfg.grid_tiled && W.perm && W.cell_of && W.cell_cnt && W.dcell &&
            W.n_cells > 0;
 }
 
@@ -1359,7 +1411,6 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
         ba.n = n_queries;
         ba.src = src;
         ba.dcell = W.dcell;
-        ba.dbox = W.dbox;
         ba.cell_of = W.cell_of;
         ba.cnt = W.cell_cnt;
         ba.perm = W.perm;

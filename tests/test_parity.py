@@ -92,10 +92,12 @@ def test_workload4_batched_mixed_kinds(wn, name, prec, tol):
         compare(d, q, w, s, tol)
 
 
-def test_grid_bitmask(wn):
+@pytest.mark.parametrize("nu,nv", [(200, 137), (203, 61), (1, 9), (8, 8)])
+def test_grid_bitmask(wn, nu, nv):
+    """Cell-centre grids (ragged against the 8 x 8 tiles of the tree sweep),
+    mixed and plain, bit for bit against the oracle."""
     import torch
     dom = ws.config5_face(0, levels=8, n_holes=25, hole_segs=24)
-    nu, nv = 200, 137
     pts = ws.grid_points(nu, nv)
     from oracle import query
     ow, osd = query(dom, pts)
@@ -109,6 +111,31 @@ def test_grid_bitmask(wn):
         assert np.array_equal(got, (osd != 0).astype(np.uint32))
         assert int(nb.item()) == int((osd == 2).sum())
         h.close()
+
+
+def test_workload5_full_face_sampled(wn):
+    """One face of the tessellation workload at full size (~100k cubics,
+    4096 x 4096 cells): the bitmask on sampled cells, on cells next to the
+    curves, and the boundary count's consistency."""
+    import torch
+    dom = ws.config5_face(3)
+    h = wn.Domain.from_dict(dom)
+    bits, nb = wn.query_grid_bitmask(h, 4096, 4096, precision=1)
+    torch.cuda.synchronize()
+    b = bits.cpu().numpy().view(np.uint32)
+    h.close()
+    rng = np.random.default_rng(11)
+    cells = rng.choice(4096 * 4096, 600, replace=False)
+    # cells whose centre is within two cells of a control point (near the curves)
+    cp = dom["cps"][rng.choice(len(dom["cps"]), 200, replace=False)]
+    ij = np.clip(np.floor(cp * 4096).astype(np.int64) + rng.integers(-2, 3, cp.shape), 0, 4095)
+    cells = np.unique(np.concatenate([cells, ij[:, 1] * 4096 + ij[:, 0]]))
+    pts = np.stack([((cells % 4096) + 0.5) / 4096, ((cells // 4096) + 0.5) / 4096], axis=1)
+    from oracle import query
+    ow, osd = query(dom, pts)
+    got = (b[cells >> 5] >> (cells & 31).astype(np.uint32)) & 1
+    assert np.array_equal(got, (osd != 0).astype(np.uint32))
+    assert 0 <= int(nb.item()) < 4096 * 4096
 
 
 def test_edge_cases(wn):
