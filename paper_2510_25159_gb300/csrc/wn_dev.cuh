@@ -61,6 +61,18 @@ struct PairDev {
     double plo, phi;            // hull of the n-extents of alpha and shifted beta
 };
 
+// Where in query space (reduced to the base tile) an instance can see a
+// query: a box, a strip along the family normal n and a strip along the
+// loop's lattice vector v (each +-inf where it does not constrain), widened
+// so that every query its exact test accepts lies inside.  Used to skip an
+// instance for a whole warp of queries at once.
+struct InstCull {
+    double x0, x1, y0, y1;      // box
+    double n0, n1;              // n.p range (family window)
+    double v0, v1;              // v.p range (copy slab)
+    double vx, vy;              // v (0 when the instance has no slab)
+};
+
 // Everything a kernel needs about one domain (copied per batch entry).
 struct DomDev {
     int kind, n_loops, n_segs, n_inst, n_rec, n_pairs;
@@ -78,6 +90,7 @@ struct DomDev {
     const double *seg_B;        // [n_segs]
     const LoopDev *loops;       // [n_loops]
     const InstDev *inst;        // [n_inst]
+    const InstCull *cull;       // [n_inst]
     const PairDev *pairs;       // [n_pairs]
     const float4 *rec;          // [4 * n_rec]: (a, b), (centre, R^2, flags), (gap, next), (b low)
     const int *rec_seg;         // [n_rec] segment, -1 for a closing chord
@@ -226,6 +239,20 @@ __device__ __forceinline__ bool inst_sees(const DomDev &D, const InstDev &in, co
     double klo = ceil(xsub(sp, L.smax)), khi = floor(xsub(sp, L.smin));
     double k = (double)in.k;
     return k >= klo && k <= khi;
+}
+
+// Can an instance see any query in the box [bx0, bx1] x [by0, by1]?  True
+// whenever the exact test (inst_sees) accepts some query of the box.
+__device__ __forceinline__ bool cull_sees(const InstCull &c, double nx, double ny, double bx0, double bx1,
+                                          double by0, double by1)
+{
+    if (bx1 < c.x0 || bx0 > c.x1 || by1 < c.y0 || by0 > c.y1) return false;
+    const double n_lo = nx * (nx >= 0 ? bx0 : bx1) + ny * (ny >= 0 ? by0 : by1);
+    const double n_hi = nx * (nx >= 0 ? bx1 : bx0) + ny * (ny >= 0 ? by1 : by0);
+    if (n_hi < c.n0 || n_lo > c.n1) return false;
+    const double v_lo = c.vx * (c.vx >= 0 ? bx0 : bx1) + c.vy * (c.vy >= 0 ? by0 : by1);
+    const double v_hi = c.vx * (c.vx >= 0 ? bx1 : bx0) + c.vy * (c.vy >= 0 ? by1 : by0);
+    return !(v_hi < c.v0 || v_lo > c.v1);
 }
 
 // Line term of Eq. 9 (+1 on the left of L, -1 on the right, 0 on L) for the

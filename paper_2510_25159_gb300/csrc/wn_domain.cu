@@ -756,6 +756,56 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     }
     std::vector<PairDev> hp_dev;
     for (const Pair &pr : pairs) hp_dev.push_back({pr.plo, pr.phi});
+    // per instance, the query region its exact test can accept (inst_sees),
+    // widened far beyond the rounding of that test
+    std::vector<InstCull> cull(inst.size());
+    for (size_t j = 0; j < inst.size(); j++) {
+        const InstDev &in = inst[j];
+        InstCull c;
+        c.x0 = c.y0 = c.n0 = c.v0 = -INFINITY;
+        c.x1 = c.y1 = c.n1 = c.v1 = INFINITY;
+        c.vx = c.vy = 0.0;
+        auto widen = [](double &lo, double &hi, double mag) {
+            const double sl = 1e-9 * (mag + 1.0);
+            lo -= sl;
+            hi += sl;
+        };
+        if (in.type == IT_BOX) {
+            const HostLoop &L = loops[in.loop];
+            if (in.axes & 1) {
+                c.x0 = L.box[0] + in.Tx;
+                c.x1 = L.box[1] + in.Tx;
+                widen(c.x0, c.x1, std::fabs(L.box[0]) + std::fabs(L.box[1]) + std::fabs(in.Tx));
+            }
+            if (in.axes & 2) {
+                c.y0 = L.box[2] + in.Ty;
+                c.y1 = L.box[3] + in.Ty;
+                widen(c.y0, c.y1, std::fabs(L.box[2]) + std::fabs(L.box[3]) + std::fabs(in.Ty));
+            }
+        } else if (in.type == IT_LINE || in.type == IT_PE) {
+            if (in.pair >= 0) {
+                const Pair &pr = pairs[in.pair];
+                const double cp = (double)in.c * PP;
+                c.n0 = cp + pr.plo;
+                c.n1 = cp + pr.phi;
+                widen(c.n0, c.n1, std::fabs(cp) + std::fabs(pr.plo) + std::fabs(pr.phi) +
+                                      (std::fabs(nx) + std::fabs(ny)) * (Pu + Pv));
+            }
+            if (in.type == IT_PE) {
+                const HostLoop &L = loops[in.loop];
+                const double fx = (Pu > 0) ? in.Fx : 0.0, fy = (Pv > 0) ? in.Fy : 0.0;
+                const double off = fx * L.v[0] + fy * L.v[1];
+                c.vx = L.v[0];
+                c.vy = L.v[1];
+                c.v0 = ((double)in.k + L.smin) * L.vv + off;
+                c.v1 = ((double)in.k + L.smax) * L.vv + off;
+                widen(c.v0, c.v1, std::fabs(c.v0) + std::fabs(c.v1) + std::fabs(off) +
+                                      (std::fabs(L.v[0]) + std::fabs(L.v[1])) * (Pu + Pv + 1.0));
+            }
+        }
+        cull[j] = c;
+    }
+    dv.cull = up.up(cull);
     dv.n_inst = (int)inst.size();
     dv.n_pairs = (int)pairs.size();
     dv.inst = up.up(inst);

@@ -392,266 +392,292 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
             thl[k] = 0.f;
             fl[k] = 0u;
         }
-        for (int j = 0; j < n_inst; j++) {
-            const InstDev in = Dp->inst[j];
-            const LoopDev &L = Dp->loops[in.loop];
-            bool any = false;
+        // warp box of the reduced queries: instances whose window misses it
+        // are skipped by the whole warp (32 instances tested per round)
+        double wb0 = INFINITY, wb1 = -INFINITY, wb2 = INFINITY, wb3 = -INFINITY;
 #pragma unroll
-            for (int k = 0; k < QPT; k++) {
+        for (int k = 0; k < QPT; k++)
+            if (valid[k]) {
                 const double2 p = s_p[k][tid];
-                inc[k] = valid[k] && !(fl[k] & (QF_BOUNDARY | QF_ESCALATE)) && inst_sees(*Dp, in, L, p.x, p.y);
-                if (in.type == IT_LINE) {
-                    if (inc[k]) {
-                        const int sd = line_side(*Dp, in, L, p.x, p.y);
-                        if (sd == 0) fl[k] |= QF_BOUNDARY;
-                        acc[k] += sd;
-                    }
-                    inc[k] = false;
-                    continue;
-                }
-                const double dx = xsub(p.x, in.Tx) - ox, dy = xsub(p.y, in.Ty) - oy;
-                fx[k] = (float)dx;
-                fy[k] = (float)dy;
-                fxl[k] = (float)(dx - (double)fx[k]);
-                fyl[k] = (float)(dy - (double)fy[k]);
-                const float mag = fmaxf(fabsf(fx[k]), fabsf(fy[k]));
-                if (inc[k] && !(mag <= Mq)) {
-                    fl[k] |= QF_ESCALATE;
-                    inc[k] = false;
-                }
-                T[k] = kTwoM22 * (M + mag);
-                any |= inc[k];
+                wb0 = fmin(wb0, p.x);
+                wb1 = fmax(wb1, p.x);
+                wb2 = fmin(wb2, p.y);
+                wb3 = fmax(wb3, p.y);
             }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            // a planar domain's loops hang below one root; otherwise each
-            // loop the instance covers is walked from its own root
-            const bool one_root = in.type == IT_ALL && Dp->all_root >= 0;
-            const int l0 = (in.type == IT_ALL) ? 0 : in.loop;
-            const int l1 = one_root ? 1 : (in.type == IT_ALL) ? Dp->n_loops : in.loop + 1;
-            for (int l = l0; l < l1; l++) {
-                const int root = one_root ? Dp->all_root : Dp->loops[l].root;
-                if (root < 0) continue;
-                uint64_t lf = 0;
 #pragma unroll
-                for (int k = 0; k < QPT; k++)
-                    if (inc[k]) lf |= 1ull << (2 * k);
-                int st_cur = root, st_end = root + 1, st_lvl = 0;    // stack entry `lane`
-                int sp = 0;
-                while (sp >= 0) {
-                    const int cur = __shfl_sync(0xffffffffu, st_cur, sp);
-                    const int end = __shfl_sync(0xffffffffu, st_end, sp);
-                    const int lvl = __shfl_sync(0xffffffffu, st_lvl, sp);
-                    if (lane == sp) st_cur = cur + 1;
-                    if (cur + 1 >= end) sp--;
-                    const uint32_t f = (uint32_t)((lf >> (lvl * SB)) & SMASK);
-                    if (!__any_sync(0xffffffffu, f != 0u)) continue;
-                    const float4 *__restrict__ N = nodes + (size_t)kCluF4 * cur;
-                    const float4 nb = __ldg(N), yx = __ldg(N + 1), meta = __ldg(N + 3), sp6 = __ldg(N + 6);
-                    const int nflags = __float_as_int(meta.y);
-                    const bool gaps = nflags & 1, leaf = (nflags & 2) != 0;
-                    uint32_t cf = 0u, nearb = 0u, mpb = 0u;
-                    int kneed = 0;
-                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (gaps) z = __ldg(N + 2);
+        for (int o = 16; o > 0; o >>= 1) {
+            wb0 = fmin(wb0, __shfl_xor_sync(0xffffffffu, wb0, o));
+            wb1 = fmax(wb1, __shfl_xor_sync(0xffffffffu, wb1, o));
+            wb2 = fmin(wb2, __shfl_xor_sync(0xffffffffu, wb2, o));
+            wb3 = fmax(wb3, __shfl_xor_sync(0xffffffffu, wb3, o));
+        }
+        for (int jb = 0; jb < n_inst; jb += 32) {
+            const int jl = jb + lane;
+            unsigned vis = __ballot_sync(0xffffffffu, jl < n_inst && cull_sees(Dp->cull[jl], Dp->nx, Dp->ny,
+                                                                              wb0, wb1, wb2, wb3));
+            while (vis) {
+                const int j = jb + __ffs(vis) - 1;
+                vis &= vis - 1;
+                const InstDev in = Dp->inst[j];
+                const LoopDev &L = Dp->loops[in.loop];
+                bool any = false;
 #pragma unroll
-                    for (int k = 0; k < QPT; k++) {
-                        const uint32_t sk = (f >> (2 * k)) & 3u;
-                        if (!sk) continue;
-                        if constexpr (CNT) wk[WK_NODE]++;
-                        const bool outside = (fx[k] < nb.x - T[k]) | (fx[k] > nb.y + T[k]) |
-                                             (fy[k] < nb.z - T[k]) | (fy[k] > nb.w + T[k]);
-                        // does the +x ray from p meet the node's extent at all?
-                        const bool meets = !((fy[k] > yx.y + T[k]) | (fy[k] < yx.x - T[k]) | (fx[k] > yx.z + T[k]));
-                        bool full = false;     // stays in full mode: descend, crossings at the leaves
-                        if (sk == 1u) {
-                            if (!outside) {
-                                full = true;
-                                nearb |= 1u << k;
-                            } else if (gaps) {
-                                const float dx = (z.x - fx[k]) + (z.z - fxl[k]);
-                                const float dy = (z.y - fy[k]) + (z.w - fyl[k]);
-                                const float d2 = fmaf(dx, dx, dy * dy);
-                                if (d2 >= yx.w) {
-                                    const float4 t0 = __ldg(N + 4), t1 = __ldg(N + 5);
-                                    const int kq = d2 >= t0.x ? 4 : d2 >= t0.y ? 8 : d2 >= t0.z ? 12 : d2 >= t0.w ? 16
-                                                 : d2 >= t1.x ? 20 : d2 >= t1.y ? 24 : d2 >= t1.z ? 28 : kCluTerms;
-                                    kneed = max(kneed, kq);
-                                    mpb |= 1u << k;
-                                } else {
-                                    full = true;
-                                }
-                            }
+                for (int k = 0; k < QPT; k++) {
+                    const double2 p = s_p[k][tid];
+                    inc[k] = valid[k] && !(fl[k] & (QF_BOUNDARY | QF_ESCALATE)) && inst_sees(*Dp, in, L, p.x, p.y);
+                    if (in.type == IT_LINE) {
+                        if (inc[k]) {
+                            const int sd = line_side(*Dp, in, L, p.x, p.y);
+                            if (sd == 0) fl[k] |= QF_BOUNDARY;
+                            acc[k] += sd;
                         }
-                        uint32_t child = full ? 1u : 0u;
-                        if (!full && meets) {
-                            if (fx[k] < sp6.x - T[k]) {
-                                // the node lies right of p: its polyline's crossings
-                                // telescope to [end above] - [start above]
-                                const float d0 = sp6.y - fy[k], d1 = sp6.z - fy[k];
-                                int span = (d1 > 0.f ? 1 : 0) - (d0 > 0.f ? 1 : 0);
-                                if ((fabsf(d0) <= T[k]) | (fabsf(d1) <= T[k])) {
-                                    const double2 p = s_p[k][tid];
-                                    span = node_span_exact(Dp, __float_as_int(sp6.w), __float_as_int(__ldg(&N[7].x)),
-                                                           xsub(p.y, in.Ty));
-                                    if constexpr (CNT) wk[WK_EXACT]++;
-                                }
-                                if constexpr (CNT) wk[WK_TELE]++;
-                                acc[k] += 2 * span;
-                            } else {
-                                child = 2u;    // crossings only, below
-                            }
-                        }
-                        cf |= child << (2 * k);
-                    }
-                    if (gaps) {
-                        const int K = __reduce_max_sync(0xffffffffu, kneed);
-                        if (K > 0) {
-                            bool use[QPT];
-#pragma unroll
-                            for (int k = 0; k < QPT; k++) use[k] = __any_sync(0xffffffffu, (mpb >> k) & 1u);
-                            float gs[QPT];
-                            node_gap_sums<QPT>(N, fx, fy, fxl, fyl, use, K, gs);
-#pragma unroll
-                            for (int k = 0; k < QPT; k++)
-                                if (mpb >> k & 1u) {
-                                    two_sum_add(th[k], thl[k], gs[k]);
-                                    if constexpr (CNT) {
-                                        wk[WK_EXPANSION]++;
-                                        wk[WK_TERMS] += (uint32_t)K;
-                                    }
-                                }
-                        }
-                    }
-                    if (!leaf) {
-                        if (__any_sync(0xffffffffu, cf != 0u)) {
-                            sp++;
-                            if (lane == sp) {
-                                st_cur = __float_as_int(meta.z);
-                                st_end = __float_as_int(meta.w);
-                                st_lvl = lvl + 1;
-                            }
-                            const int sh = (lvl + 1) * SB;
-                            lf = (lf & ~(SMASK << sh)) | ((uint64_t)cf << sh);
-                        }
+                        inc[k] = false;
                         continue;
                     }
-                    // leaf: records [first, end) for the slots that still need them
-                    bool need_near = nearb != 0u, need_full = false, need_cross = false;
-#pragma unroll
-                    for (int k = 0; k < QPT; k++) {
-                        const uint32_t ck = (cf >> (2 * k)) & 3u;
-                        need_full |= ck == 1u;
-                        need_cross |= ck == 2u;
+                    const double dx = xsub(p.x, in.Tx) - ox, dy = xsub(p.y, in.Ty) - oy;
+                    fx[k] = (float)dx;
+                    fy[k] = (float)dy;
+                    fxl[k] = (float)(dx - (double)fx[k]);
+                    fyl[k] = (float)(dy - (double)fy[k]);
+                    const float mag = fmaxf(fabsf(fx[k]), fabsf(fy[k]));
+                    if (inc[k] && !(mag <= Mq)) {
+                        fl[k] |= QF_ESCALATE;
+                        inc[k] = false;
                     }
-                    const bool wn = __any_sync(0xffffffffu, need_near);
-                    const bool we = __any_sync(0xffffffffu, need_full);
-                    const bool wc = __any_sync(0xffffffffu, need_cross);
-                    if (!we && !wc) continue;
-                    const int r0 = __float_as_int(meta.z), r1 = __float_as_int(meta.w);
-                    float tcl[QPT];
+                    T[k] = kTwoM22 * (M + mag);
+                    any |= inc[k];
+                }
+                if (!__any_sync(0xffffffffu, any)) continue;
+                // a planar domain's loops hang below one root; otherwise each
+                // loop the instance covers is walked from its own root
+                const bool one_root = in.type == IT_ALL && Dp->all_root >= 0;
+                const int l0 = (in.type == IT_ALL) ? 0 : in.loop;
+                const int l1 = one_root ? 1 : (in.type == IT_ALL) ? Dp->n_loops : in.loop + 1;
+                for (int l = l0; l < l1; l++) {
+                    const int root = one_root ? Dp->all_root : Dp->loops[l].root;
+                    if (root < 0) continue;
+                    uint64_t lf = 0;
 #pragma unroll
-                    for (int k = 0; k < QPT; k++) tcl[k] = 0.f;
-                    for (int r = r0; r < r1; r++) {
-                        const float4 R0 = __ldg(rec + 4 * r), R1 = __ldg(rec + 4 * r + 1), R2 = __ldg(rec + 4 * r + 2);
-                        if (wn) {
-                            const float4 R3 = __ldg(rec + 4 * r + 3);
-                            bool nr[QPT];
-                            bool any_near = false;
+                    for (int k = 0; k < QPT; k++)
+                        if (inc[k]) lf |= 1ull << (2 * k);
+                    int st_cur = root, st_end = root + 1, st_lvl = 0;    // stack entry `lane`
+                    int sp = 0;
+                    while (sp >= 0) {
+                        const int cur = __shfl_sync(0xffffffffu, st_cur, sp);
+                        const int end = __shfl_sync(0xffffffffu, st_end, sp);
+                        const int lvl = __shfl_sync(0xffffffffu, st_lvl, sp);
+                        if (lane == sp) st_cur = cur + 1;
+                        if (cur + 1 >= end) sp--;
+                        const uint32_t f = (uint32_t)((lf >> (lvl * SB)) & SMASK);
+                        if (!__any_sync(0xffffffffu, f != 0u)) continue;
+                        const float4 *__restrict__ N = nodes + (size_t)kCluF4 * cur;
+                        const float4 nb = __ldg(N), yx = __ldg(N + 1), meta = __ldg(N + 3), sp6 = __ldg(N + 6);
+                        const int nflags = __float_as_int(meta.y);
+                        const bool gaps = nflags & 1, leaf = (nflags & 2) != 0;
+                        uint32_t cf = 0u, nearb = 0u, mpb = 0u;
+                        int kneed = 0;
+                        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (gaps) z = __ldg(N + 2);
 #pragma unroll
-                            for (int k = 0; k < QPT; k++) {
-                                const uint32_t ck = (cf >> (2 * k)) & 3u;
-                                int cc;
-                                float dth;
-                                bool slow;
-                                sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, nr[k], slow);
-                                if (slow && ck) {
-                                    const double2 p = s_p[k][tid];
-                                    sweep_record_exact(r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
-                                                       xsub(p.y, in.Ty), cc, dth);
-                                    if constexpr (CNT) wk[WK_EXACT]++;
+                        for (int k = 0; k < QPT; k++) {
+                            const uint32_t sk = (f >> (2 * k)) & 3u;
+                            if (!sk) continue;
+                            if constexpr (CNT) wk[WK_NODE]++;
+                            const bool outside = (fx[k] < nb.x - T[k]) | (fx[k] > nb.y + T[k]) |
+                                                 (fy[k] < nb.z - T[k]) | (fy[k] > nb.w + T[k]);
+                            // does the +x ray from p meet the node's extent at all?
+                            const bool meets = !((fy[k] > yx.y + T[k]) | (fy[k] < yx.x - T[k]) | (fx[k] > yx.z + T[k]));
+                            bool full = false;     // stays in full mode: descend, crossings at the leaves
+                            if (sk == 1u) {
+                                if (!outside) {
+                                    full = true;
+                                    nearb |= 1u << k;
+                                } else if (gaps) {
+                                    const float dx = (z.x - fx[k]) + (z.z - fxl[k]);
+                                    const float dy = (z.y - fy[k]) + (z.w - fyl[k]);
+                                    const float d2 = fmaf(dx, dx, dy * dy);
+                                    if (d2 >= yx.w) {
+                                        const float4 t0 = __ldg(N + 4), t1 = __ldg(N + 5);
+                                        const int kq = d2 >= t0.x ? 4 : d2 >= t0.y ? 8 : d2 >= t0.z ? 12 : d2 >= t0.w ? 16
+                                                     : d2 >= t1.x ? 20 : d2 >= t1.y ? 24 : d2 >= t1.z ? 28 : kCluTerms;
+                                        kneed = max(kneed, kq);
+                                        mpb |= 1u << k;
+                                    } else {
+                                        full = true;
+                                    }
                                 }
-                                if constexpr (CNT) {
-                                    if (ck == 1u) wk[WK_REC_NEAR]++;
-                                    else if (ck == 2u) wk[WK_REC_CROSS]++;
-                                }
-                                nr[k] = nr[k] && ck == 1u;
-                                if (ck) {
-                                    acc[k] += 2 * cc;
-                                    if (ck == 1u) tcl[k] += dth;
-                                }
-                                any_near |= nr[k];
                             }
-                            if (__any_sync(0xffffffffu, any_near)) {
+                            uint32_t child = full ? 1u : 0u;
+                            if (!full && meets) {
+                                if (fx[k] < sp6.x - T[k]) {
+                                    // the node lies right of p: its polyline's crossings
+                                    // telescope to [end above] - [start above]
+                                    const float d0 = sp6.y - fy[k], d1 = sp6.z - fy[k];
+                                    int span = (d1 > 0.f ? 1 : 0) - (d0 > 0.f ? 1 : 0);
+                                    if ((fabsf(d0) <= T[k]) | (fabsf(d1) <= T[k])) {
+                                        const double2 p = s_p[k][tid];
+                                        span = node_span_exact(Dp, __float_as_int(sp6.w), __float_as_int(__ldg(&N[7].x)),
+                                                               xsub(p.y, in.Ty));
+                                        if constexpr (CNT) wk[WK_EXACT]++;
+                                    }
+                                    if constexpr (CNT) wk[WK_TELE]++;
+                                    acc[k] += 2 * span;
+                                } else {
+                                    child = 2u;    // crossings only, below
+                                }
+                            }
+                            cf |= child << (2 * k);
+                        }
+                        if (gaps) {
+                            const int K = __reduce_max_sync(0xffffffffu, kneed);
+                            if (K > 0) {
+                                bool use[QPT];
+#pragma unroll
+                                for (int k = 0; k < QPT; k++) use[k] = __any_sync(0xffffffffu, (mpb >> k) & 1u);
+                                float gs[QPT];
+                                node_gap_sums<QPT>(N, fx, fy, fxl, fyl, use, K, gs);
+#pragma unroll
+                                for (int k = 0; k < QPT; k++)
+                                    if (mpb >> k & 1u) {
+                                        two_sum_add(th[k], thl[k], gs[k]);
+                                        if constexpr (CNT) {
+                                            wk[WK_EXPANSION]++;
+                                            wk[WK_TERMS] += (uint32_t)K;
+                                        }
+                                    }
+                            }
+                        }
+                        if (!leaf) {
+                            if (__any_sync(0xffffffffu, cf != 0u)) {
+                                sp++;
+                                if (lane == sp) {
+                                    st_cur = __float_as_int(meta.z);
+                                    st_end = __float_as_int(meta.w);
+                                    st_lvl = lvl + 1;
+                                }
+                                const int sh = (lvl + 1) * SB;
+                                lf = (lf & ~(SMASK << sh)) | ((uint64_t)cf << sh);
+                            }
+                            continue;
+                        }
+                        // leaf: records [first, end) for the slots that still need them
+                        bool need_near = nearb != 0u, need_full = false, need_cross = false;
+#pragma unroll
+                        for (int k = 0; k < QPT; k++) {
+                            const uint32_t ck = (cf >> (2 * k)) & 3u;
+                            need_full |= ck == 1u;
+                            need_cross |= ck == 2u;
+                        }
+                        const bool wn = __any_sync(0xffffffffu, need_near);
+                        const bool we = __any_sync(0xffffffffu, need_full);
+                        const bool wc = __any_sync(0xffffffffu, need_cross);
+                        if (!we && !wc) continue;
+                        const int r0 = __float_as_int(meta.z), r1 = __float_as_int(meta.w);
+                        float tcl[QPT];
+#pragma unroll
+                        for (int k = 0; k < QPT; k++) tcl[k] = 0.f;
+                        for (int r = r0; r < r1; r++) {
+                            const float4 R0 = __ldg(rec + 4 * r), R1 = __ldg(rec + 4 * r + 1), R2 = __ldg(rec + 4 * r + 2);
+                            if (wn) {
+                                const float4 R3 = __ldg(rec + 4 * r + 3);
+                                bool nr[QPT];
+                                bool any_near = false;
 #pragma unroll
                                 for (int k = 0; k < QPT; k++) {
-                                    const unsigned m = __ballot_sync(0xffffffffu, nr[k]);
-                                    if (!m) continue;
-                                    const int leader = __ffs(m) - 1;
-                                    unsigned long long base = 0;
-                                    if (lane == leader) base = atomicAdd(&A.counters[CNT_NEAR], (unsigned long long)__popc(m));
-                                    base = __shfl_sync(0xffffffffu, base, leader);
-                                    if (nr[k]) {
-                                        const unsigned long long idx = base + __popc(m & lt_mask);
-                                        if (idx < (unsigned long long)A.cap_near) {
-                                            Item it;
-                                            it.q = qid[k];
-                                            it.dom = (uint32_t)U.x;
-                                            it.inst = (uint32_t)j;
-                                            it.rec = (uint32_t)r;
-                                            A.near_items[idx] = it;
-                                        } else {
-                                            fl[k] |= QF_ESCALATE;
+                                    const uint32_t ck = (cf >> (2 * k)) & 3u;
+                                    int cc;
+                                    float dth;
+                                    bool slow;
+                                    sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, nr[k], slow);
+                                    if (slow && ck) {
+                                        const double2 p = s_p[k][tid];
+                                        sweep_record_exact(r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
+                                                           xsub(p.y, in.Ty), cc, dth);
+                                        if constexpr (CNT) wk[WK_EXACT]++;
+                                    }
+                                    if constexpr (CNT) {
+                                        if (ck == 1u) wk[WK_REC_NEAR]++;
+                                        else if (ck == 2u) wk[WK_REC_CROSS]++;
+                                    }
+                                    nr[k] = nr[k] && ck == 1u;
+                                    if (ck) {
+                                        acc[k] += 2 * cc;
+                                        if (ck == 1u) tcl[k] += dth;
+                                    }
+                                    any_near |= nr[k];
+                                }
+                                if (__any_sync(0xffffffffu, any_near)) {
+#pragma unroll
+                                    for (int k = 0; k < QPT; k++) {
+                                        const unsigned m = __ballot_sync(0xffffffffu, nr[k]);
+                                        if (!m) continue;
+                                        const int leader = __ffs(m) - 1;
+                                        unsigned long long base = 0;
+                                        if (lane == leader) base = atomicAdd(&A.counters[CNT_NEAR], (unsigned long long)__popc(m));
+                                        base = __shfl_sync(0xffffffffu, base, leader);
+                                        if (nr[k]) {
+                                            const unsigned long long idx = base + __popc(m & lt_mask);
+                                            if (idx < (unsigned long long)A.cap_near) {
+                                                Item it;
+                                                it.q = qid[k];
+                                                it.dom = (uint32_t)U.x;
+                                                it.inst = (uint32_t)j;
+                                                it.rec = (uint32_t)r;
+                                                A.near_items[idx] = it;
+                                            } else {
+                                                fl[k] |= QF_ESCALATE;
+                                            }
                                         }
                                     }
                                 }
-                            }
-                        } else if (we) {
-                            const float4 R3 = __ldg(rec + 4 * r + 3);
+                            } else if (we) {
+                                const float4 R3 = __ldg(rec + 4 * r + 3);
 #pragma unroll
-                            for (int k = 0; k < QPT; k++) {
-                                const uint32_t ck = (cf >> (2 * k)) & 3u;
-                                int cc;
-                                float dth;
-                                bool slow;
-                                sweep_record_far(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, slow);
-                                if (slow && ck) {
-                                    const double2 p = s_p[k][tid];
-                                    sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
-                                                       xsub(p.y, in.Ty), cc, dth);
-                                    if constexpr (CNT) wk[WK_EXACT]++;
-                                }
-                                if constexpr (CNT) {
-                                    if (ck == 1u) wk[WK_REC_FAR]++;
-                                    else if (ck == 2u) wk[WK_REC_CROSS]++;
-                                }
-                                if (ck) {
-                                    acc[k] += 2 * cc;
-                                    if (ck == 1u) tcl[k] += dth;
-                                }
-                            }
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < QPT; k++) {
-                                const uint32_t ck = (cf >> (2 * k)) & 3u;
-                                int cc;
-                                bool slow;
-                                sweep_record_cross(R0, R1, R2, fx[k], fy[k], T[k], cc, slow);
-                                if (slow && ck) {
-                                    const double2 p = s_p[k][tid];
+                                for (int k = 0; k < QPT; k++) {
+                                    const uint32_t ck = (cf >> (2 * k)) & 3u;
+                                    int cc;
                                     float dth;
-                                    sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
-                                                       xsub(p.y, in.Ty), cc, dth);
-                                    if constexpr (CNT) wk[WK_EXACT]++;
+                                    bool slow;
+                                    sweep_record_far(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, slow);
+                                    if (slow && ck) {
+                                        const double2 p = s_p[k][tid];
+                                        sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
+                                                           xsub(p.y, in.Ty), cc, dth);
+                                        if constexpr (CNT) wk[WK_EXACT]++;
+                                    }
+                                    if constexpr (CNT) {
+                                        if (ck == 1u) wk[WK_REC_FAR]++;
+                                        else if (ck == 2u) wk[WK_REC_CROSS]++;
+                                    }
+                                    if (ck) {
+                                        acc[k] += 2 * cc;
+                                        if (ck == 1u) tcl[k] += dth;
+                                    }
                                 }
-                                if constexpr (CNT) {
-                                    if (ck) wk[WK_REC_CROSS]++;
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < QPT; k++) {
+                                    const uint32_t ck = (cf >> (2 * k)) & 3u;
+                                    int cc;
+                                    bool slow;
+                                    sweep_record_cross(R0, R1, R2, fx[k], fy[k], T[k], cc, slow);
+                                    if (slow && ck) {
+                                        const double2 p = s_p[k][tid];
+                                        float dth;
+                                        sweep_record_exact(r, __float_as_uint(R1.w), false, Dp, xsub(p.x, in.Tx),
+                                                           xsub(p.y, in.Ty), cc, dth);
+                                        if constexpr (CNT) wk[WK_EXACT]++;
+                                    }
+                                    if constexpr (CNT) {
+                                        if (ck) wk[WK_REC_CROSS]++;
+                                    }
+                                    if (ck) acc[k] += 2 * cc;
                                 }
-                                if (ck) acc[k] += 2 * cc;
                             }
                         }
-                    }
 #pragma unroll
-                    for (int k = 0; k < QPT; k++) two_sum_add(th[k], thl[k], tcl[k]);
+                        for (int k = 0; k < QPT; k++) two_sum_add(th[k], thl[k], tcl[k]);
+                    }
                 }
             }
         }
