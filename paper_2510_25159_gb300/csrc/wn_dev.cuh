@@ -64,13 +64,14 @@ struct PairDev {
 // Where in query space (reduced to the base tile) an instance can see a
 // query: a box, a strip along the family normal n and a strip along the
 // loop's lattice vector v (each +-inf where it does not constrain), widened
-// so that every query its exact test accepts lies inside.  Used to skip an
-// instance for a whole warp of queries at once.
+// so that every query its exact test accepts lies inside, and rounded
+// outward to FP32.  Used to skip an instance for a whole warp at once.
 struct InstCull {
-    double x0, x1, y0, y1;      // box
-    double n0, n1;              // n.p range (family window)
-    double v0, v1;              // v.p range (copy slab)
-    double vx, vy;              // v (0 when the instance has no slab)
+    float x0, x1, y0, y1;       // box
+    float n0, n1;               // n.p range (family window)
+    float v0, v1;               // v.p range (copy slab)
+    float vx, vy;               // v (0 when the instance has no slab)
+    float pad0, pad1;
 };
 
 // Everything a kernel needs about one domain (copied per batch entry).
@@ -241,18 +242,22 @@ __device__ __forceinline__ bool inst_sees(const DomDev &D, const InstDev &in, co
     return k >= klo && k <= khi;
 }
 
-// Can an instance see any query in the box [bx0, bx1] x [by0, by1]?  True
-// whenever the exact test (inst_sees) accepts some query of the box.
-__device__ __forceinline__ bool cull_sees(const InstCull &c, double nx, double ny, double bx0, double bx1,
-                                          double by0, double by1)
+// Can an instance see any query in the box [bx0, bx1] x [by0, by1] (FP32,
+// rounded outward; wmag = the largest |coordinate| of the box)?  True
+// whenever the exact test (inst_sees) accepts some query of the box: the
+// projections carry a slack above their FP32 rounding.
+__device__ __forceinline__ bool cull_sees(const InstCull &c, float nx, float ny, float bx0, float bx1,
+                                          float by0, float by1, float wmag)
 {
     if (bx1 < c.x0 || bx0 > c.x1 || by1 < c.y0 || by0 > c.y1) return false;
-    const double n_lo = nx * (nx >= 0 ? bx0 : bx1) + ny * (ny >= 0 ? by0 : by1);
-    const double n_hi = nx * (nx >= 0 ? bx1 : bx0) + ny * (ny >= 0 ? by1 : by0);
-    if (n_hi < c.n0 || n_lo > c.n1) return false;
-    const double v_lo = c.vx * (c.vx >= 0 ? bx0 : bx1) + c.vy * (c.vy >= 0 ? by0 : by1);
-    const double v_hi = c.vx * (c.vx >= 0 ? bx1 : bx0) + c.vy * (c.vy >= 0 ? by1 : by0);
-    return !(v_hi < c.v0 || v_lo > c.v1);
+    const float sn = 4e-7f * (fabsf(nx) + fabsf(ny)) * wmag;
+    const float n_lo = fmaf(nx, nx >= 0.f ? bx0 : bx1, ny * (ny >= 0.f ? by0 : by1));
+    const float n_hi = fmaf(nx, nx >= 0.f ? bx1 : bx0, ny * (ny >= 0.f ? by1 : by0));
+    if (n_hi + sn < c.n0 || n_lo - sn > c.n1) return false;
+    const float sv = 4e-7f * (fabsf(c.vx) + fabsf(c.vy)) * wmag;
+    const float v_lo = fmaf(c.vx, c.vx >= 0.f ? bx0 : bx1, c.vy * (c.vy >= 0.f ? by0 : by1));
+    const float v_hi = fmaf(c.vx, c.vx >= 0.f ? bx1 : bx0, c.vy * (c.vy >= 0.f ? by1 : by0));
+    return !(v_hi + sv < c.v0 || v_lo - sv > c.v1);
 }
 
 // Line term of Eq. 9 (+1 on the left of L, -1 on the right, 0 on L) for the

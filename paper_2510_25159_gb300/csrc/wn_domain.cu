@@ -759,9 +759,10 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     // per instance, the query region its exact test can accept (inst_sees),
     // widened far beyond the rounding of that test
     std::vector<InstCull> cull(inst.size());
+    struct Cull64 { double x0, x1, y0, y1, n0, n1, v0, v1, vx, vy; };
     for (size_t j = 0; j < inst.size(); j++) {
         const InstDev &in = inst[j];
-        InstCull c;
+        Cull64 c;
         c.x0 = c.y0 = c.n0 = c.v0 = -INFINITY;
         c.x1 = c.y1 = c.n1 = c.v1 = INFINITY;
         c.vx = c.vy = 0.0;
@@ -803,7 +804,14 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
                                       (std::fabs(L.v[0]) + std::fabs(L.v[1])) * (Pu + Pv + 1.0));
             }
         }
-        cull[j] = c;
+        auto lo = [](double x) { return std::nextafter((float)x, -INFINITY); };
+        auto hi = [](double x) { return std::nextafter((float)x, INFINITY); };
+        InstCull f;
+        f.x0 = lo(c.x0); f.x1 = hi(c.x1); f.y0 = lo(c.y0); f.y1 = hi(c.y1);
+        f.n0 = lo(c.n0); f.n1 = hi(c.n1); f.v0 = lo(c.v0); f.v1 = hi(c.v1);
+        f.vx = (float)c.vx; f.vy = (float)c.vy;
+        f.pad0 = f.pad1 = 0.f;
+        cull[j] = f;
     }
     dv.cull = up.up(cull);
     dv.n_inst = (int)inst.size();

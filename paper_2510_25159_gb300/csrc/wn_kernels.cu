@@ -330,8 +330,10 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
     constexpr uint64_t SMASK = (1ull << SB) - 1ull;
     static_assert(SB * kTreeMaxLevels <= 64, "level flags must fit 64 bits");
     __shared__ double2 s_p[QPT][kSweepThreads];
+    __shared__ float s_wb[kSweepThreads / 32][8];     // per warp: query box, |max|, family normal
     const int tid = threadIdx.x;
     const int lane = tid & 31;
+    const int warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     uint32_t wk[WK_N];
 #pragma unroll
@@ -392,29 +394,47 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
             thl[k] = 0.f;
             fl[k] = 0u;
         }
-        // warp box of the reduced queries: instances whose window misses it
-        // are skipped by the whole warp (32 instances tested per round)
-        double wb0 = INFINITY, wb1 = -INFINITY, wb2 = INFINITY, wb3 = -INFINITY;
+        // warp box of the reduced queries (FP32, rounded outward): instances
+        // whose window misses it are skipped by the whole warp, 32 tested
+        // per round (a domain with one instance needs no test).  The box
+        // waits in shared memory, not in registers, during the tree walks.
+        if (n_inst > 1) {
+            float wb0 = INFINITY, wb1 = -INFINITY, wb2 = INFINITY, wb3 = -INFINITY;
 #pragma unroll
-        for (int k = 0; k < QPT; k++)
-            if (valid[k]) {
-                const double2 p = s_p[k][tid];
-                wb0 = fmin(wb0, p.x);
-                wb1 = fmax(wb1, p.x);
-                wb2 = fmin(wb2, p.y);
-                wb3 = fmax(wb3, p.y);
+            for (int k = 0; k < QPT; k++)
+                if (valid[k]) {
+                    const double2 p = s_p[k][tid];
+                    wb0 = fminf(wb0, __double2float_rd(p.x));
+                    wb1 = fmaxf(wb1, __double2float_ru(p.x));
+                    wb2 = fminf(wb2, __double2float_rd(p.y));
+                    wb3 = fmaxf(wb3, __double2float_ru(p.y));
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                wb0 = fminf(wb0, __shfl_xor_sync(0xffffffffu, wb0, o));
+                wb1 = fmaxf(wb1, __shfl_xor_sync(0xffffffffu, wb1, o));
+                wb2 = fminf(wb2, __shfl_xor_sync(0xffffffffu, wb2, o));
+                wb3 = fmaxf(wb3, __shfl_xor_sync(0xffffffffu, wb3, o));
             }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            wb0 = fmin(wb0, __shfl_xor_sync(0xffffffffu, wb0, o));
-            wb1 = fmax(wb1, __shfl_xor_sync(0xffffffffu, wb1, o));
-            wb2 = fmin(wb2, __shfl_xor_sync(0xffffffffu, wb2, o));
-            wb3 = fmax(wb3, __shfl_xor_sync(0xffffffffu, wb3, o));
+            if (lane == 0) {
+                s_wb[warp][0] = wb0;
+                s_wb[warp][1] = wb1;
+                s_wb[warp][2] = wb2;
+                s_wb[warp][3] = wb3;
+                s_wb[warp][4] = fmaxf(fmaxf(fabsf(wb0), fabsf(wb1)), fmaxf(fabsf(wb2), fabsf(wb3)));
+                s_wb[warp][5] = (float)Dp->nx;
+                s_wb[warp][6] = (float)Dp->ny;
+            }
+            __syncwarp();
         }
         for (int jb = 0; jb < n_inst; jb += 32) {
             const int jl = jb + lane;
-            unsigned vis = __ballot_sync(0xffffffffu, jl < n_inst && cull_sees(Dp->cull[jl], Dp->nx, Dp->ny,
-                                                                              wb0, wb1, wb2, wb3));
+            unsigned vis = 1u;
+            if (n_inst > 1) {
+                const float *wb = s_wb[warp];
+                vis = __ballot_sync(0xffffffffu, jl < n_inst && cull_sees(Dp->cull[jl], wb[5], wb[6], wb[0], wb[1],
+                                                                          wb[2], wb[3], wb[4]));
+            }
             while (vis) {
                 const int j = jb + __ffs(vis) - 1;
                 vis &= vis - 1;
