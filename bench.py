@@ -55,28 +55,55 @@ WORK_FLOPS = {"node_tests": 30.0, "telescoped_nodes": 8.0, "expansions": 21.0, "
 FP32_LANES_PER_SM = 128
 
 
-def workload(k, scale=1.0):
+SHARD_SEED_STRIDE = 1000
+
+
+def workload(k, scale=1.0, shard=0):
+    """Faces and queries of workload k.  Shard r (one per rank) draws its own
+    faces and queries (seed offset r * SHARD_SEED_STRIDE; the tessellation
+    workload takes faces 64r..64r+63): the ranks' problems are independent,
+    as the faces of a B-Rep are."""
+    off = SHARD_SEED_STRIDE * shard
+    tag = f" (shard {shard})" if shard else ""
     if k == 2 and scale != 1.0:
-        d, q = ws.config2(n_uniform=int(10_000_000 * scale), n_near=int(1_000_000 * scale))
+        d, q = ws.config2(n_uniform=int(10_000_000 * scale), n_near=int(1_000_000 * scale), seed_index=2 + off)
         return d, q, (f"workload 2 at {scale:g} of its queries (profiling case): 64 planar open/noisy domains, "
-                      f"{int(11_000_000 * scale)} queries")
+                      f"{int(11_000_000 * scale)} queries" + tag)
     if k == 1:
-        d, q = ws.config1()
-        return [d], [q], "one planar [0,1]^2 domain: 64-cubic CCW star (C0) + two 16-cubic CW holes; 100k uniform + 10k near (1e-6) queries"
+        d, q = ws.config1(seed_index=1 + off)
+        return [d], [q], ("one planar [0,1]^2 domain: 64-cubic CCW star (C0) + two 16-cubic CW holes; "
+                          "100k uniform + 10k near (1e-6) queries" + tag)
     if k == 2:
-        d, q = ws.config2()
+        d, q = ws.config2(seed_index=2 + off)
         return d, q, ("64 planar domains, 4-12 loops x 32-512 segments of degree 1-5, every join opened by a "
-                      "1e-4..1e-2 gap, control-point noise 1e-4; 10M uniform + 1M near-curve (1e-7..1e-3) queries")
+                      "1e-4..1e-2 gap, control-point noise 1e-4; 10M uniform + 1M near-curve (1e-7..1e-3) queries"
+                      + tag)
     if k == 3:
-        d, q = ws.config3()
-        return d, q, "256 bi-periodic faces (2pi x 2pi), 2-8 loops of 16-256 cubics, 30% non-contractible pairs, 10% open; 20M uniform queries"
+        d, q = ws.config3(seed_index=3 + off)
+        return d, q, ("256 bi-periodic faces (2pi x 2pi), 2-8 loops of 16-256 cubics, 30% non-contractible pairs, "
+                      "10% open; 20M uniform queries" + tag)
     if k == 4:
-        d, q = ws.config4()
-        return d, q, "10k faces, log-normal segments (median 40) and queries (median 4096, ~2e8 total), 20% periodic"
+        d, q = ws.config4(seed_index=4 + off)
+        return d, q, ("10k faces, log-normal segments (median 40) and queries (median 4096, ~2e8 total), "
+                      "20% periodic" + tag)
     if k == 5:
-        d = [ws.config5_face(f) for f in range(64)]
-        return d, None, "64 planar faces of ~100k cubics (fractal outer loop + 200 holes), 4096x4096 cell-centre grids"
+        d = [ws.config5_face(64 * shard + f) for f in range(64)]
+        return d, None, ("64 planar faces of ~100k cubics (fractal outer loop + 200 holes), 4096x4096 "
+                         "cell-centre grids" + tag)
     raise SystemExit(f"unknown workload {k}")
+
+
+def reduce_over_ranks(dist, ms, n_q, device):
+    """(slowest rank's milliseconds, all ranks' queries): the whole-job
+    figures of a weak-scaling run, each rank on its own shard."""
+    if dist is None:
+        return ms, n_q
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    q = torch.tensor([n_q], dtype=torch.int64, device=device)
+    dist.all_reduce(q, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(q.item())
 
 
 class Clocks:
@@ -219,7 +246,7 @@ def main():
     if args.qpt:
         wn.set_tuning(qpt=args.qpt)
 
-    doms, qs, desc = workload(args.workload, args.scale)
+    doms, qs, desc = workload(args.workload, args.scale, shard=rank)
     handles = [wn.Domain.from_dict(d) for d in doms]
     dev = torch.device("cuda", local)
     grid = qs is None
@@ -274,11 +301,8 @@ def main():
     wn.set_profiling(False)
     st = wn.stats()
     clocks = clk.summary()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n_q * world / (ms / 1e3)
+    ms, n_all = reduce_over_ranks(dist, ms, n_q, dev)
+    value = n_all / (ms / 1e3)
     launches_per_step = int(st["kernels"]) * (len(handles) if grid else 1)
 
     # roofline of the dominant kernel (the sweep): algorithmic FP32 flops / its event time
@@ -331,8 +355,8 @@ def main():
         step(wn.PLAIN_FP64)
         b.record(stream)
         torch.cuda.synchronize()
-        pms = a.elapsed_time(b)
-        extra["plain_fp64"] = {"value": n_q * world / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+        pms, _ = reduce_over_ranks(dist, a.elapsed_time(b), n_q, dev)
+        extra["plain_fp64"] = {"value": n_all / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
                                "launches_per_step": len(handles)}
         extra["speedup_vs_plain"] = pms / ms
         step()
@@ -351,8 +375,8 @@ def main():
         for _ in range(args.steps):
             wn.query_batched(handles, hpn, off, out_winding=hwn, out_inside=hsn)
         torch.cuda.synchronize()
-        et = (time.perf_counter() - t0) / args.steps
-        e2e = {"value": n_q * world / et, "unit": UNIT, "ms_per_step": et * 1e3,
+        et_ms, _ = reduce_over_ranks(dist, (time.perf_counter() - t0) / args.steps * 1e3, n_q, dev)
+        e2e = {"value": n_all / (et_ms / 1e3), "unit": UNIT, "ms_per_step": et_ms,
                "h2d_bytes_per_step": int(pts_h.nbytes), "d2h_bytes_per_step": int(n_q * 9)}
 
     # oracle on the host cores: bounded sample, also a parity check of the timed results
@@ -388,7 +412,8 @@ def main():
                 "config": {"workload": desc, "domains": len(doms), "queries": n_q,
                            "segments": int(sum(ws.n_segments(d) for d in doms)),
                            "l2": "inputs (16 B/query) larger than L2; 256 MB L2 flush between steps outside the events",
-                           "parallelism": f"replicas x{world}"},
+                           "queries_all_ranks": n_all,
+                           "parallelism": f"independent shards x{world} (no collective on the data path)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "clocks": clocks, "parity": parity, "tuning": tuning,
                 "escalation": {"near_pairs": st["near_pairs"], "fp64_pairs": st["fp64_pairs"],
