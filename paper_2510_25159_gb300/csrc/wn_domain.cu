@@ -384,8 +384,10 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
                     rc = std::fmax(rc, std::hypot(rn64[r].x - zx, rn64[r].y - zy));
                 }
                 rc = std::fmax(rc, 1e-300);
-                // M_k = sum_gaps (n - z)^k - (b - z)^k ;  c_k = (-1)^(k+1) M_k / (k rc^k)
-                double Mre[kCluTerms + 1] = {}, Mim[kCluTerms + 1] = {};
+                // M_k = sum_gaps (n - z)^k - (b - z)^k ;  c_k = (-1)^(k+1) M_k / (k rc^k),
+                // kept to kTail terms for the truncation bound
+                constexpr int kTail = 96;
+                double Mre[kTail + 1] = {}, Mim[kTail + 1] = {};
                 for (const auto &rg : ranges)
                 for (int r = rg.first; r < rg.second; r++) {
                     uint32_t fl;
@@ -397,7 +399,7 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
                         const double sg = side ? 1.0 : -1.0;
                         const double ux = (v.x - zx) / rc, uy = (v.y - zy) / rc;
                         double pr = 1.0, pi = 0.0;
-                        for (int k = 1; k <= kCluTerms; k++) {
+                        for (int k = 1; k <= kTail; k++) {
                             const double t = pr * ux - pi * uy;
                             pi = pr * uy + pi * ux;
                             pr = t;
@@ -412,13 +414,23 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
                     dst[0] = (float)(f * Mre[k]);
                     dst[1] = (float)(f * Mim[k]);
                 }
-                // C >= |c_k| for every k: each gap adds at most |g| / r_c.  The
-                // largest |w| with C |w|^(K+1) / (1 - |w|) <= tol, by bisection.
+                // Truncation after K terms at |w| = m: the next coefficients as
+                // computed, then C >= |c_k| for every k (each gap adds at most
+                // |g| / r_c) beyond kTail:
+                //   sum_{K<k<=kTail} |c_k| m^k + C m^(kTail+1) / (1 - m).
+                // The largest m with that <= tol, by bisection (it grows with m).
+                double cabs[kTail + 1];
+                for (int k = 1; k <= kTail; k++) cabs[k] = std::hypot(Mre[k], Mim[k]) / (double)k;
+                auto tail = [&](int K, double m) {
+                    double t = Cb * std::pow(m, kTail + 1) / (1.0 - m), mk = std::pow(m, K + 1);
+                    for (int k = K + 1; k <= kTail; k++, mk *= m) t += cabs[k] * mk;
+                    return t;
+                };
                 auto dist2 = [&](int K) {
                     double lo = 0.0, hi = 0.999;
-                    for (int it = 0; it < 80; it++) {
+                    for (int it = 0; it < 60; it++) {
                         const double m = 0.5 * (lo + hi);
-                        if (Cb * std::pow(m, K + 1) / (1.0 - m) <= kCluTol) lo = m;
+                        if (tail(K, m) <= kCluTol) lo = m;
                         else hi = m;
                     }
                     const double d = lo > 0 ? rc / lo : INFINITY;
