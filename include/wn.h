@@ -256,7 +256,7 @@ wn_status wn_sweep_work(int64_t *out8);
  * fixed device-memory budget.  This entry point keeps all of its scratch
  * (per-query accumulators, the near-pair and FP64 queues, the work list)
  * in one fixed-size device array that is part of the library image: every
- * process that loads the library holds it (about 6.6 MB) on each device it
+ * process that loads the library holds it (about 12.3 MB) on each device it
  * uses, until it exits.  The call itself makes no cudaMalloc, cudaFree or
  * other allocating call.
  *

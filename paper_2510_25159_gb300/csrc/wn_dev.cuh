@@ -101,6 +101,10 @@ struct DomDev {
     const float4 *nodes;        // [kCluF4 * n_nodes] record tree, see below
     int n_nodes;
     int all_root;               // planar: root over every loop (-1: per-loop roots)
+    const float4 *cp32;         // [total_cp] P - origin as FP32 (hi.x, hi.y, lo.x, lo.y)
+    const float *seg_B32;       // [n_segs] B rounded to FP32
+    float eps32;                // eps rounded to FP32
+    int pad4;
 };
 
 // Record tree: per loop, leaves over runs of at most kCluRecs consecutive
@@ -147,6 +151,7 @@ struct Item {
     uint32_t dom;               // batch entry
     uint32_t inst;
     uint32_t rec;
+    float fx, fy, fxl, fyl;     // p - (Tx, Ty) - origin as FP32 hi + lo (from the sweep)
 };
 
 // FP64 work item: the sub-interval [a, b] of a near pair whose FP32 error

@@ -587,6 +587,21 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     dv.rec_n64 = up.up(rn64);
     dv.n_nodes = (int)(nodes.size() / kCluF4);
     dv.all_root = all_root;
+    {
+        // FP32 hi/lo of every lifted control point relative to the origin,
+        // for the near walk's query-relative control points
+        std::vector<float4> cp32(ncp);
+        for (size_t i = 0; i < (size_t)ncp; i++) {
+            const double dx = P[2 * i] - ox, dy = P[2 * i + 1] - oy;
+            const float hx = (float)dx, hy = (float)dy;
+            cp32[i] = make_float4(hx, hy, (float)(dx - (double)hx), (float)(dy - (double)hy));
+        }
+        std::vector<float> b32(ns);
+        for (int i = 0; i < ns; i++) b32[i] = (float)segB[i];
+        dv.cp32 = up.up(cp32);
+        dv.seg_B32 = up.up(b32);
+        dv.eps32 = (float)eps;
+    }
     dv.nodes = up.up(nodes);
     if (up.err != cudaSuccess) return fail(up.err == cudaErrorMemoryAllocation ? 4 : 3,
                                            std::string("CUDA: ") + cudaGetErrorString(up.err));

@@ -31,6 +31,7 @@ namespace wn {
 
 constexpr float kTwoM22 = 2.384185791015625e-7f;   // 2^-22
 constexpr float kTwoM24 = 5.9604644775390625e-8f;  // 2^-24
+constexpr float kTwoM44 = 5.684341886080802e-14f;  // 2^-44
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr float kOmegaBandF = 1e-4f;               // classification band of the mixed path
 constexpr double kInv2Pi = 0.15915494309189533576888376337251;
@@ -643,6 +644,10 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                                 it.dom = (uint32_t)U.x;
                                                 it.inst = (uint32_t)j;
                                                 it.rec = (uint32_t)r;
+                                                it.fx = fx[k];
+                                                it.fy = fy[k];
+                                                it.fxl = fxl[k];
+                                                it.fyl = fyl[k];
                                                 A.near_items[idx] = it;
                                             } else {
                                                 fl[k] |= QF_ESCALATE;
@@ -908,6 +913,10 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
                                     it.dom = (uint32_t)U.x;
                                     it.inst = (uint32_t)j;
                                     it.rec = (uint32_t)(r0 + r);
+                                    it.fx = fx[k];
+                                    it.fy = fy[k];
+                                    it.fxl = fxl[k];
+                                    it.fyl = fyl[k];
                                     A.near_items[idx] = it;
                                 } else {
                                     fl[k] |= QF_ESCALATE;
@@ -990,34 +999,55 @@ __device__ __forceinline__ void emit_f64(const NearArgs &A, const Item &it, floa
     }
 }
 
+// (a_hi + a_lo) - (b_hi + b_lo) rounded once to FP32: Knuth's TwoSum of the
+// high parts carries their rounding error into the sum of the low parts.
+__device__ __forceinline__ float hilo_diff(float ah, float al, float bh, float bl)
+{
+    const float d = ah - bh;
+    const float bb = d - ah;
+    const float e = (ah - (d - bb)) + (-bh - bb);
+    return d + ((al - bl) + e);
+}
+
 // Set up the walk of one near pair.  Returns false when the item needs no
-// walk (already decided: *result 0 done, 1 boundary).
+// walk (already decided: *result 0 done, 1 boundary).  The query-relative
+// control points come from FP32 hi/lo pairs (control point and query, both
+// relative to the domain origin), within 2^-24 |q| + 2^-46 (|P - o| + |p - o|)
+// of P - p: the second term, below 2^-44 M, joins the evaluation bound E.
 __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S,
                                            int &result)
 {
     const DomDev *Dp = A.doms + it.dom;
-    double pxp, pyp;
-    item_query(Dp, A.src, it, pxp, pyp);
     const int s = __ldg(&Dp->rec_seg[it.rec]);
     const int deg = __ldg(&Dp->seg_deg[s]);
-    const double *P = Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]);
+    const float4 *P = Dp->cp32 + __ldg(&Dp->seg_cp[s]);
     float mq = 0.f;
 #pragma unroll
     for (int k = 0; k < kNcp; k++) {
         if (k <= deg) {
-            W.qx[k] = (float)(__ldg(P + 2 * k) - pxp);
-            W.qy[k] = (float)(__ldg(P + 2 * k + 1) - pyp);
+            const float4 c = __ldg(P + k);
+            W.qx[k] = hilo_diff(c.x, c.z, it.fx, it.fxl);
+            W.qy[k] = hilo_diff(c.y, c.w, it.fy, it.fyl);
             mq = fmaxf(mq, fabsf(W.qx[k]) + fabsf(W.qy[k]));
         } else {
             W.qx[k] = 0.f;
             W.qy[k] = 0.f;
         }
     }
+    const float eabs = kTwoM44 * 4.f * Dp->M;
+    // the endpoint signs must be those of the exact differences (the sweep
+    // decides the same vertices exactly): inside the representation error,
+    // the pair goes to FP64, which takes them from the FP64 control points
+    if ((fabsf(W.qy[0]) <= eabs) | (fabsf(W.qy[deg]) <= eabs)) {
+        emit_f64(A, it, 0.f, 1.f, 0u);
+        result = 0;
+        return false;
+    }
     W.n = deg;
     W.nmax = Dp->max_deg;
-    W.B = (float)__ldg(&Dp->seg_B[s]);
-    W.E = (float)(2 * deg + 4) * kTwoM24 * mq;
-    W.eps = (float)Dp->eps;
+    W.B = __ldg(&Dp->seg_B32[s]);
+    W.E = (float)(2 * deg + 4) * kTwoM24 * mq + eabs;
+    W.eps = Dp->eps32;
     W.cnt = 0;
     W.a = 0.f;
     W.ax = W.qx[0];
@@ -1077,10 +1107,11 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
         }
     }
     if (undecided) {
-        // the whole pair goes to FP64 (handing over only [a, b] and walking on
-        // costs more: the walk then continues next to the query)
-        emit_f64(A, it, 0.f, 1.f, (W.qy[0] > 0.f ? 1u : 0u) | (W.qy[W.n] > 0.f ? 2u : 0u));
-        W.cnt = 0;
+        // [0, a] is done (its crossings stay in W.cnt); [a, 1] goes to FP64
+        // with the walk's sign of gamma(a), so the two parts count the
+        // crossings at gamma(a) consistently.  (Handing over only [a, b] and
+        // walking on costs more: the walk then continues next to the query.)
+        emit_f64(A, it, W.a, 1.f, W.sa ? 1u : 0u);
         W.sp = 0;
         return 1;
     }
@@ -1144,10 +1175,15 @@ __global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
         double pxp, pyp;
         item_query(Dp, A.src, it, pxp, pyp);
         const int s = Dp->rec_seg[it.rec];
+        const int deg = Dp->seg_deg[s];
+        const double *P = Dp->cp + 2 * (size_t)Dp->seg_cp[s];
+        // a sub-interval's end signs are the FP32 walk's (consistent with
+        // its counts so far); the curve's own ends are decided exactly here
+        const bool sa = si.a == 0.f ? P[1] > pyp : (si.signs & 1u) != 0;
+        const bool sb = si.b == 1.f ? P[2 * deg + 1] > pyp : (si.signs & 2u) != 0;
         int cnt = 0;
-        const bool bnd = alg1_fp64_sub(Dp->cp + 2 * (size_t)Dp->seg_cp[s], Dp->seg_deg[s], Dp->max_deg, Dp->seg_B[s],
-                                       pxp, pyp, Dp->eps, (double)si.a, (double)si.b, (si.signs & 1u) != 0,
-                                       (si.signs & 2u) != 0, cnt);
+        const bool bnd = alg1_fp64_sub(P, deg, Dp->max_deg, Dp->seg_B[s], pxp, pyp, Dp->eps, (double)si.a,
+                                       (double)si.b, sa, sb, cnt);
         if (bnd) atomicOr(&A.flags[it.q], QF_BOUNDARY);
         else if (cnt) atomicAdd(&A.acc2[it.q], 2 * cnt);
     }
