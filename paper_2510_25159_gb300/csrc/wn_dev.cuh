@@ -28,6 +28,10 @@ enum : int { DK_PLANAR = 0, DK_UNI_U = 1, DK_UNI_V = 2, DK_BI = 3 };
 enum : int { IT_ALL = 0, IT_BOX = 1, IT_PE = 2, IT_LINE = 3 };
 enum : uint32_t { QF_BOUNDARY = 1u, QF_ESCALATE = 2u };
 enum : uint32_t { RF_CHORD = 1u, RF_GAP = 2u };
+// Record flags carry the record's segment in their upper 30 bits
+// (RF_NO_SEG for a closing chord).
+constexpr int RF_SEG_SHIFT = 2;
+constexpr uint32_t RF_NO_SEG = 0x3FFFFFFFu;
 
 // One lifted loop (FP64).
 struct LoopDev {
@@ -102,7 +106,7 @@ struct DomDev {
     int n_nodes;
     int all_root;               // planar: root over every loop (-1: per-loop roots)
     const float4 *cp32;         // [total_cp] P - origin as FP32 (hi.x, hi.y, lo.x, lo.y)
-    const float *seg_B32;       // [n_segs] B rounded to FP32
+    const int4 *seg_info;       // [n_segs] (first control point, degree, B as FP32 bits, 0)
     float eps32;                // eps rounded to FP32
     int pad4;
 };
@@ -150,7 +154,7 @@ struct Item {
     uint32_t q;                 // global query index
     uint32_t dom;               // batch entry
     uint32_t inst;
-    uint32_t rec;
+    uint32_t seg;               // the record's segment
     float fx, fy, fxl, fyl;     // p - (Tx, Ty) - origin as FP32 hi + lo (from the sweep)
 };
 

@@ -287,7 +287,8 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         const double cx = 0.5 * (a[0] + b[0]), cy = 0.5 * (a[1] + b[1]);
         const double R = (0.5 * B + eps) * (1.0 + std::ldexp(1.0, -20)) + 2.0 * Trec;
         const double gx = nxt[0] - b[0], gy = nxt[1] - b[1];
-        uint32_t fl = (chord ? RF_CHORD : 0u) | ((gx != 0.0 || gy != 0.0) ? RF_GAP : 0u);
+        uint32_t fl = (chord ? RF_CHORD : 0u) | ((gx != 0.0 || gy != 0.0) ? RF_GAP : 0u) |
+                      ((seg >= 0 ? (uint32_t)seg : RF_NO_SEG) << RF_SEG_SHIFT);
         r1.x = f32(cx - ox); r1.y = f32(cy - oy); r1.z = f32(R * R * (1.0 + std::ldexp(1.0, -20)));
         uint32_t flb = fl;
         std::memcpy(&r1.w, &flb, 4);
@@ -596,10 +597,15 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             const float hx = (float)dx, hy = (float)dy;
             cp32[i] = make_float4(hx, hy, (float)(dx - (double)hx), (float)(dy - (double)hy));
         }
-        std::vector<float> b32(ns);
-        for (int i = 0; i < ns; i++) b32[i] = (float)segB[i];
+        std::vector<int4> info(ns);
+        for (int i = 0; i < ns; i++) {
+            const float b32 = (float)segB[i];
+            int bi;
+            std::memcpy(&bi, &b32, 4);
+            info[i] = make_int4(seg_cp[i], seg_deg[i], bi, 0);
+        }
         dv.cp32 = up.up(cp32);
-        dv.seg_B32 = up.up(b32);
+        dv.seg_info = up.up(info);
         dv.eps32 = (float)eps;
     }
     dv.nodes = up.up(nodes);

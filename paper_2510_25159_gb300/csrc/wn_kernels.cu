@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                                 it.q = qid[k];
                                                 it.dom = (uint32_t)U.x;
                                                 it.inst = (uint32_t)j;
-                                                it.rec = (uint32_t)r;
+                                                it.seg = __float_as_uint(R1.w) >> RF_SEG_SHIFT;
                                                 it.fx = fx[k];
                                                 it.fy = fy[k];
                                                 it.fxl = fxl[k];
@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
                                     it.q = (uint32_t)(U.y + tid + k * kSweepThreads);
                                     it.dom = (uint32_t)U.x;
                                     it.inst = (uint32_t)j;
-                                    it.rec = (uint32_t)(r0 + r);
+                                    it.seg = __float_as_uint(R1.w) >> RF_SEG_SHIFT;
                                     it.fx = fx[k];
                                     it.fy = fy[k];
                                     it.fxl = fxl[k];
@@ -1018,9 +1018,9 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
                                            int &result)
 {
     const DomDev *Dp = A.doms + it.dom;
-    const int s = __ldg(&Dp->rec_seg[it.rec]);
-    const int deg = __ldg(&Dp->seg_deg[s]);
-    const float4 *P = Dp->cp32 + __ldg(&Dp->seg_cp[s]);
+    const int4 si = __ldg(&Dp->seg_info[it.seg]);
+    const int deg = si.y;
+    const float4 *P = Dp->cp32 + si.x;
     float mq = 0.f;
 #pragma unroll
     for (int k = 0; k < kNcp; k++) {
@@ -1045,7 +1045,7 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
     }
     W.n = deg;
     W.nmax = Dp->max_deg;
-    W.B = __ldg(&Dp->seg_B32[s]);
+    W.B = __int_as_float(si.z);
     W.E = (float)(2 * deg + 4) * kTwoM24 * mq + eabs;
     W.eps = Dp->eps32;
     W.cnt = 0;
@@ -1174,7 +1174,7 @@ __global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
         const DomDev *Dp = A.doms + it.dom;
         double pxp, pyp;
         item_query(Dp, A.src, it, pxp, pyp);
-        const int s = Dp->rec_seg[it.rec];
+        const int s = (int)it.seg;
         const int deg = Dp->seg_deg[s];
         const double *P = Dp->cp + 2 * (size_t)Dp->seg_cp[s];
         // a sub-interval's end signs are the FP32 walk's (consistent with
