@@ -61,6 +61,16 @@ def _bind(path):
                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, P]
     lib.or_extended_wn.restype = ctypes.c_int
+    lib.or_query_w.argtypes = [ctypes.c_int32, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_int64, P, P, P, P, ctypes.c_int32, P]
+    lib.or_query_w.restype = ctypes.c_int
+    lib.or_segment_wn_w.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, P, P]
+    lib.or_segment_wn_w.restype = ctypes.c_int
+    lib.or_eval_w.argtypes = [ctypes.c_int, P, P, ctypes.c_double, P]
+    lib.or_eval_w.restype = ctypes.c_int
+    lib.or_bound_w.argtypes = [ctypes.c_int, P, P]
+    lib.or_bound_w.restype = ctypes.c_double
     return lib
 
 
@@ -85,10 +95,16 @@ def _dom_arrays(dom):
     return lo, dg, cp
 
 
+def _weights(w):
+    return None if w is None else np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+
+
 def query(dom, pts, threads=None, margins=False, stats=False, eps=None, L=None):
-    """omega (NaN for BOUNDARY), state (u8) [, margin] [, stats dict]."""
+    """omega (NaN for BOUNDARY), state (u8) [, margin] [, stats dict].
+    A domain with "weights" (one per control point) is rational."""
     L = L or lib()
     lo, dg, cp = _dom_arrays(dom)
+    wt = _weights(dom.get("weights"))
     pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 2)
     n = pts.shape[0]
     w = np.empty(n)
@@ -97,8 +113,12 @@ def query(dom, pts, threads=None, margins=False, stats=False, eps=None, L=None):
     s5 = np.zeros(5, dtype=np.int64)
     th = threads or os.cpu_count() or 1
     e = dom["eps"] if eps is None else eps
-    rc = L.or_query(len(lo) - 1, _p(lo), _p(dg), _p(cp), dom["period_u"], dom["period_v"], e,
-                    n, _p(pts), _p(w), _p(st), _p(mg), th, _p(s5))
+    if wt is None:
+        rc = L.or_query(len(lo) - 1, _p(lo), _p(dg), _p(cp), dom["period_u"], dom["period_v"], e,
+                        n, _p(pts), _p(w), _p(st), _p(mg), th, _p(s5))
+    else:
+        rc = L.or_query_w(len(lo) - 1, _p(lo), _p(dg), _p(cp), _p(wt), dom["period_u"], dom["period_v"], e,
+                          n, _p(pts), _p(w), _p(st), _p(mg), th, _p(s5))
     if rc != 0:
         raise OracleError(rc)
     out = [w, st]
@@ -115,13 +135,19 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def segment_wn(cps, p, eps=1e-12, L=None):
-    """Algorithm 1 on one segment: (angle_radians, boundary, stats dict)."""
+def segment_wn(cps, p, eps=1e-12, L=None, weights=None):
+    """Algorithm 1 on one segment (rational with weights): (angle_radians,
+    boundary, stats dict)."""
     L = L or lib()
     cps = np.ascontiguousarray(cps, dtype=np.float64).reshape(-1)
     a = np.zeros(1)
     s5 = np.zeros(5, dtype=np.int64)
-    b = L.or_segment_wn(cps.size // 2 - 1, _p(cps), float(p[0]), float(p[1]), eps, _p(a), _p(s5))
+    wt = _weights(weights)
+    if wt is None:
+        b = L.or_segment_wn(cps.size // 2 - 1, _p(cps), float(p[0]), float(p[1]), eps, _p(a), _p(s5))
+    else:
+        b = L.or_segment_wn_w(cps.size // 2 - 1, _p(cps), _p(wt), float(p[0]), float(p[1]), eps, _p(a),
+                              _p(s5))
     return float(a[0]), bool(b), dict(zip(["evals", "nodes", "chords", "max_depth", "depth_cap"], s5.tolist()))
 
 
@@ -134,18 +160,25 @@ def hull_segment_wn(cps, p, eps=1e-12, L=None):
     return float(a[0]), bool(b), int(e[0])
 
 
-def eval_point(cps, t, L=None):
+def eval_point(cps, t, L=None, weights=None):
     L = L or lib()
     cps = np.ascontiguousarray(cps, dtype=np.float64).reshape(-1)
     o = np.zeros(2)
-    L.or_eval(cps.size // 2 - 1, _p(cps), float(t), _p(o))
+    wt = _weights(weights)
+    if wt is None:
+        L.or_eval(cps.size // 2 - 1, _p(cps), float(t), _p(o))
+    else:
+        L.or_eval_w(cps.size // 2 - 1, _p(cps), _p(wt), float(t), _p(o))
     return o
 
 
-def bound(cps, L=None):
+def bound(cps, L=None, weights=None):
     L = L or lib()
     cps = np.ascontiguousarray(cps, dtype=np.float64).reshape(-1)
-    return float(L.or_bound(cps.size // 2 - 1, _p(cps)))
+    wt = _weights(weights)
+    if wt is None:
+        return float(L.or_bound(cps.size // 2 - 1, _p(cps)))
+    return float(L.or_bound_w(cps.size // 2 - 1, _p(cps), _p(wt)))
 
 
 def domain_info(dom, L=None):

@@ -113,6 +113,7 @@ typedef struct {
     int deg;
     const double *P;   /* (deg+1) points, xy interleaved, lifted */
     double B;
+    const double *W;   /* (deg+1) weights of a rational segment, or NULL */
 } oseg_t;
 
 typedef struct {
@@ -133,6 +134,7 @@ typedef struct {
     oseg_t *seg;
     oloop_t *loop;
     double *cps;         /* lifted control points */
+    double *w;           /* weights per control point (rational input), or NULL */
     /* bi-periodic */
     int hp, hq;          /* homology of class A */
     long i0, j0;         /* family generator */
@@ -182,6 +184,53 @@ double or_bound(int deg, const double *P)
     return B;
 }
 
+/* gamma(t) of a rational segment (weights W > 0): the curve is the central
+ * projection of the polynomial curve with control points (w_i x_i, w_i y_i,
+ * w_i), so de Casteljau runs on those and the result is divided by the last
+ * coordinate (App. A.1 treats the rational case; W = NULL is polynomial). */
+int or_eval_w(int deg, const double *P, const double *W, double t, double *out)
+{
+    if (!W) return or_eval(deg, P, t, out);
+    double h[3 * (OR_MAX_DEG + 1)];
+    if (deg < 0 || deg > OR_MAX_DEG) return OR_ERR_ARG;
+    for (int i = 0; i <= deg; i++) {
+        h[3 * i] = W[i] * P[2 * i];
+        h[3 * i + 1] = W[i] * P[2 * i + 1];
+        h[3 * i + 2] = W[i];
+    }
+    for (int r = 1; r <= deg; r++)
+        for (int i = 0; i <= deg - r; i++)
+            for (int c = 0; c < 3; c++) h[3 * i + c] = (1.0 - t) * h[3 * i + c] + t * h[3 * i + 3 + c];
+    out[0] = h[0] / h[2];
+    out[1] = h[1] / h[2];
+    return OR_OK;
+}
+
+/* Derivative bound of a rational segment (App. A.1, after Floater):
+ *   |gamma'| <= n (W/w) max_{i,j} |P_i - P_j|  and
+ *   |gamma'| <= n (W/w)^2 max_i |P_i - P_{i-1}|,  W = max w_i, w = min w_i;
+ * both hold, so the smaller one is taken.  W = NULL: or_bound. */
+double or_bound_w(int deg, const double *P, const double *W)
+{
+    if (!W) return or_bound(deg, P);
+    double wmax = W[0], wmin = W[0];
+    for (int i = 1; i <= deg; i++) {
+        wmax = fmax(wmax, W[i]);
+        wmin = fmin(wmin, W[i]);
+    }
+    const double r = wmax / wmin;
+    double dall = 0.0, dnext = 0.0;
+    for (int i = 0; i <= deg; i++)
+        for (int j = i + 1; j <= deg; j++) {
+            double dx = P[2 * j] - P[2 * i], dy = P[2 * j + 1] - P[2 * i + 1];
+            double d = sqrt(dx * dx + dy * dy);
+            if (d > dall) dall = d;
+            if (j == i + 1 && d > dnext) dnext = d;
+        }
+    const double b1 = (double)deg * r * dall, b2 = (double)deg * r * r * dnext;
+    return b1 < b2 ? b1 : b2;
+}
+
 /* Eq. 3: winding number of the oriented chord a->b about p, in radians
  * (the signed angle from a-p to b-p). */
 static double chord_angle(double px, double py, const double *a, const double *b)
@@ -214,7 +263,7 @@ static int seg_wn(const oseg_t *s, double px, double py, double a, double b,
         return 1;
     }
     double m = 0.5 * (a + b), gm[2];
-    or_eval(s->deg, s->P, m, gm);
+    or_eval_w(s->deg, s->P, s->W, m, gm);
     acc->st.evals++;
     if (seg_wn(s, px, py, a, m, ga, gm, eps, depth + 1, acc)) return 1;
     return seg_wn(s, px, py, m, b, gm, gb, eps, depth + 1, acc);
@@ -225,12 +274,13 @@ static int seg_root(const oseg_t *s, double px, double py, double eps, acc_t *ac
     return seg_wn(s, px, py, 0.0, 1.0, s->P, s->P + 2 * s->deg, eps, 0, acc);
 }
 
-/* Alg. 1 on one segment; *angle receives the sum of chord angles (radians). */
-int or_segment_wn(int deg, const double *P, double px, double py, double eps,
-                  double *angle, int64_t *stats5)
+/* Alg. 1 on one segment (weights W, or NULL for a polynomial segment);
+ * *angle receives the sum of chord angles (radians). */
+int or_segment_wn_w(int deg, const double *P, const double *W, double px, double py, double eps,
+                    double *angle, int64_t *stats5)
 {
     if (deg < 1 || deg > OR_MAX_DEG) return -1;
-    oseg_t s = {deg, P, or_bound(deg, P)};
+    oseg_t s = {deg, P, or_bound_w(deg, P, W), W};
     acc_t acc;
     memset(&acc, 0, sizeof acc);
     acc.margin = INFINITY;
@@ -241,6 +291,12 @@ int or_segment_wn(int deg, const double *P, double px, double py, double eps,
         stats5[3] = acc.st.max_depth; stats5[4] = acc.st.depth_cap;
     }
     return bnd;
+}
+
+int or_segment_wn(int deg, const double *P, double px, double py, double eps,
+                  double *angle, int64_t *stats5)
+{
+    return or_segment_wn_w(deg, P, NULL, px, py, eps, angle, stats5);
 }
 
 /* ------------------------------------------------------------------ */
@@ -359,7 +415,7 @@ static void loop_mid(const odom_t *D, const oloop_t *L, double *out)
     int m = L->s1 - L->s0;
     int s = L->s0 + m / 2;
     double t = (m % 2) ? 0.5 : 0.0;
-    or_eval(D->seg[s].deg, D->seg[s].P, t, out);
+    or_eval_w(D->seg[s].deg, D->seg[s].P, D->seg[s].W, t, out);
 }
 
 /* Eq. 9: winding number about x of the periodically extended curve made
@@ -408,7 +464,7 @@ static double pe_value(const odom_t *D, const oloop_t *L, double x, double y, lo
 
 static void free_dom(odom_t *D)
 {
-    free(D->seg); free(D->loop); free(D->cps);
+    free(D->seg); free(D->loop); free(D->cps); free(D->w);
     free(D->pa); free(D->pb); free(D->pI); free(D->pJ); free(D->plo); free(D->phi);
     memset(D, 0, sizeof *D);
 }
@@ -416,7 +472,7 @@ static void free_dom(odom_t *D)
 static long lround_d(double x) { return (long)round(x); }
 
 static int build_dom(odom_t *D, int n_loops, const int32_t *loop_offsets, const int32_t *degrees,
-                     const double *cps, double Pu, double Pv, double eps)
+                     const double *cps, const double *weights, double Pu, double Pv, double eps)
 {
     memset(D, 0, sizeof *D);
     if (n_loops < 0 || !(Pu >= 0) || !(Pv >= 0) || isnan(eps)) return OR_ERR_ARG;
@@ -431,6 +487,9 @@ static int build_dom(odom_t *D, int n_loops, const int32_t *loop_offsets, const 
     }
     for (long i = 0; i < 2 * ncp; i++)
         if (!isfinite(cps[i])) return OR_ERR_ARG;
+    if (weights)
+        for (long i = 0; i < ncp; i++)
+            if (!(weights[i] > 0) || !isfinite(weights[i])) return OR_ERR_ARG;
     D->Pu = Pu; D->Pv = Pv;
     D->kind = (Pu > 0 && Pv > 0) ? K_BI : (Pu > 0) ? K_UNI_U : (Pv > 0) ? K_UNI_V : K_PLANAR;
     D->n_loops = n_loops; D->n_segs = ns;
@@ -439,6 +498,11 @@ static int build_dom(odom_t *D, int n_loops, const int32_t *loop_offsets, const 
     D->cps = malloc(sizeof(double) * 2 * (size_t)(ncp ? ncp : 1));
     if (!D->seg || !D->loop || !D->cps) { free_dom(D); return OR_ERR_OOM; }
     memcpy(D->cps, cps, sizeof(double) * 2 * (size_t)ncp);
+    if (weights) {
+        D->w = malloc(sizeof(double) * (size_t)(ncp ? ncp : 1));
+        if (!D->w) { free_dom(D); return OR_ERR_OOM; }
+        memcpy(D->w, weights, sizeof(double) * (size_t)ncp);
+    }
 
     /* R4: default tolerance */
     if (!(eps > 0)) {
@@ -457,6 +521,7 @@ static int build_dom(odom_t *D, int n_loops, const int32_t *loop_offsets, const 
     for (int s = 0; s < ns; s++) {
         D->seg[s].deg = degrees[s];
         D->seg[s].P = D->cps + 2 * off;
+        D->seg[s].W = D->w ? D->w + off : NULL;
         off += degrees[s] + 1;
     }
     /* R5: lift each loop into the covering space */
@@ -485,7 +550,7 @@ static int build_dom(odom_t *D, int n_loops, const int32_t *loop_offsets, const 
         L->box[1] = L->box[3] = -INFINITY;
         for (int s = L->s0; s < L->s1; s++) {
             oseg_t *sg = &D->seg[s];
-            sg->B = or_bound(sg->deg, sg->P);
+            sg->B = or_bound_w(sg->deg, sg->P, sg->W);
             for (int i = 0; i <= sg->deg; i++) {
                 L->box[0] = fmin(L->box[0], sg->P[2 * i]);
                 L->box[1] = fmax(L->box[1], sg->P[2 * i]);
@@ -745,13 +810,13 @@ static void *worker(void *arg)
  *   stats5     evals, nodes, chords, max depth, depth-cap hits (may be NULL)
  * Returns 0, or 1 (bad argument), 2 (topology), 4 (out of memory).
  */
-int or_query(int32_t n_loops, const int32_t *loop_offsets, const int32_t *degrees,
-             const double *cps, double Pu, double Pv, double eps, int64_t n, const double *pts,
-             double *out_w, uint8_t *out_state, double *out_margin, int32_t n_threads,
-             int64_t *stats5)
+int or_query_w(int32_t n_loops, const int32_t *loop_offsets, const int32_t *degrees,
+               const double *cps, const double *weights, double Pu, double Pv, double eps, int64_t n,
+               const double *pts, double *out_w, uint8_t *out_state, double *out_margin,
+               int32_t n_threads, int64_t *stats5)
 {
     odom_t D;
-    int rc = build_dom(&D, n_loops, loop_offsets, degrees, cps, Pu, Pv, eps);
+    int rc = build_dom(&D, n_loops, loop_offsets, degrees, cps, weights, Pu, Pv, eps);
     if (rc) return rc;
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
@@ -781,6 +846,16 @@ int or_query(int32_t n_loops, const int32_t *loop_offsets, const int32_t *degree
     return OR_OK;
 }
 
+/* or_query_w of a polynomial domain (weights all 1). */
+int or_query(int32_t n_loops, const int32_t *loop_offsets, const int32_t *degrees,
+             const double *cps, double Pu, double Pv, double eps, int64_t n, const double *pts,
+             double *out_w, uint8_t *out_state, double *out_margin, int32_t n_threads,
+             int64_t *stats5)
+{
+    return or_query_w(n_loops, loop_offsets, degrees, cps, NULL, Pu, Pv, eps, n, pts, out_w, out_state,
+                      out_margin, n_threads, stats5);
+}
+
 /*
  * Lifted control points (same layout as the input), per-loop homology
  * (2 ints per loop) and, for bi-periodic domains, the pairs (alpha loop,
@@ -791,7 +866,7 @@ int or_domain_info(int32_t n_loops, const int32_t *loop_offsets, const int32_t *
                    int32_t *homology, int64_t *pairs, int32_t *n_pairs, double *eps_out)
 {
     odom_t D;
-    int rc = build_dom(&D, n_loops, loop_offsets, degrees, cps, Pu, Pv, eps);
+    int rc = build_dom(&D, n_loops, loop_offsets, degrees, cps, NULL, Pu, Pv, eps);
     if (rc) return rc;
     long ncp = 0;
     for (int s = 0; s < D.n_segs; s++) ncp += D.seg[s].deg + 1;
@@ -823,7 +898,7 @@ int or_extended_wn(int32_t n_segs, const int32_t *degrees, const double *cps, do
 {
     int32_t lo[2] = {0, n_segs};
     odom_t D;
-    int rc = build_dom(&D, 1, lo, degrees, cps, 0.0, 0.0, eps);
+    int rc = build_dom(&D, 1, lo, degrees, cps, NULL, 0.0, 0.0, eps);
     if (rc) return -rc;
     D.Pu = Pu; D.Pv = Pv;
     oloop_t *L = &D.loop[0];

@@ -512,6 +512,133 @@ def pin_lift_homology(L, seed=26):
         assert len(pairs) == 1
 
 
+# ---------------------------------------------------------------- rational segments
+def rat_eval(cps, w, t):
+    """Rational Bezier point as the ratio of two Bernstein sums (test side)."""
+    cps = np.asarray(cps, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    n = cps.shape[0] - 1
+    t = np.asarray(t, dtype=np.float64)[..., None]
+    b = [comb(n, k) * t ** k * (1 - t) ** (n - k) for k in range(n + 1)]
+    num = sum(b[k] * w[k] * cps[k] for k in range(n + 1))
+    den = sum(b[k] * w[k] for k in range(n + 1))
+    return num / den
+
+
+def rat_speed(cps, w, t):
+    """|gamma'(t)| by the quotient rule on the numerator and denominator
+    polynomials and their hodographs (test side)."""
+    cps = np.asarray(cps, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    n = cps.shape[0] - 1
+    t = np.asarray(t, dtype=np.float64)[..., None]
+    H = np.concatenate([cps * w[:, None], w[:, None]], axis=1)
+    h = sum(comb(n, k) * t ** k * (1 - t) ** (n - k) * H[k] for k in range(n + 1))
+    d = sum(n * comb(n - 1, k) * t ** k * (1 - t) ** (n - 1 - k) * (H[k + 1] - H[k]) for k in range(n))
+    v = (d[..., :2] * h[..., 2:3] - h[..., :2] * d[..., 2:3]) / h[..., 2:3] ** 2
+    return np.hypot(v[..., 0], v[..., 1])
+
+
+def random_rational(rng, deg, spread=4.0):
+    cps = rng.uniform(-1.0, 1.0, (deg + 1, 2))
+    w = np.exp(rng.uniform(-math.log(spread), math.log(spread), deg + 1))
+    return cps, w
+
+
+def pin_rational_circle_arcs(L, seed=31):
+    """Rational quadratics represent circular arcs exactly: every evaluated
+    point lies on the circle; seen from a point inside the circle a CCW arc
+    sweeps its chord angle taken in [0, 2 pi); loops of unequal arcs wind
+    +1 / -1 inside and 0 outside."""
+    rng = np.random.default_rng(seed)
+    for _ in range(60):
+        c = rng.uniform(-1, 1, 2)
+        r = rng.uniform(0.2, 2.0)
+        a0 = rng.uniform(0, TWO_PI)
+        th = rng.uniform(0.1, 3.0)
+        cps, w = ws.rational_arc(c, r, a0, th)
+        for t in (0.1, 0.37, 0.5, 0.9):
+            assert abs(np.hypot(*(oracle.eval_point(cps, t, L=L, weights=w) - c)) - r) < 1e-12 * (1 + r)
+        for _ in range(10):
+            rr = r * math.sqrt(rng.uniform(0, 0.8))
+            ph = rng.uniform(0, TWO_PI)
+            p = c + rr * np.array([math.cos(ph), math.sin(ph)])
+            A, B = cps[0] - p, cps[2] - p
+            exp = math.atan2(A[0] * B[1] - A[1] * B[0], A @ B) % TWO_PI
+            ang, bnd, _ = oracle.segment_wn(cps, p, eps=1e-12, L=L, weights=w)
+            assert not bnd and abs(ang - exp) < 1e-10, (ang, exp)
+    for ccw, sign in ((True, 1), (False, -1)):
+        for angles in ([TWO_PI / 3] * 3, [0.5, 2.9, 2.1, TWO_PI - 5.5]):
+            dom = ws.make_domain([ws.rational_circle_loop((0.3, -0.2), 0.5, angles, ccw=ccw)], eps=1e-9)
+            rr = np.concatenate([rng.uniform(0, 0.45, 150), rng.uniform(0.56, 2.0, 150)])
+            ph = rng.uniform(0, TWO_PI, 300)
+            pts = np.stack([0.3 + rr * np.cos(ph), -0.2 + rr * np.sin(ph)], axis=1)
+            wv, st = oracle.query(dom, pts, threads=1, L=L)
+            assert np.all(st != 2)
+            assert np.max(np.abs(wv - np.where(rr < 0.5, sign, 0))) < 1e-12
+
+
+def pin_rational_bound(L, n=150, seed=32):
+    """The derivative bound of a rational segment bounds |gamma'| (sampled
+    densely through the quotient rule), so Lemma 1's ellipse holds; with
+    unit weights it is the polynomial bound."""
+    rng = np.random.default_rng(seed)
+    ts = np.linspace(0.0, 1.0, 4001)
+    for i in range(n):
+        cps, w = random_rational(rng, 1 + i % 5, spread=(2.0, 4.0, 10.0)[i % 3])
+        B = oracle.bound(cps, L=L, weights=w)
+        assert rat_speed(cps, w, ts).max() <= B * (1 + 1e-12)
+        pts = rat_eval(cps, w, ts)
+        d = np.hypot(*(pts - cps[0]).T) + np.hypot(*(pts - cps[-1]).T)
+        assert d.max() <= B * (1 + 1e-12)
+        assert abs(oracle.bound(cps, L=L, weights=np.ones(len(w))) - oracle.bound(cps, L=L)) <= 1e-14 * B
+    # a weight ratio large enough that |gamma'| exceeds the ratio times the
+    # polygon legs: the square of the ratio is needed
+    cps = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0]])
+    w = np.array([1.0, 8.0, 1.0])
+    assert rat_speed(cps, w, ts).max() <= oracle.bound(cps, L=L, weights=w) * (1 + 1e-12)
+
+
+def pin_rational_dense_polyline(L, n=40, seed=33):
+    """Random rational segments: Algorithm 1 equals the angle swept by a
+    dense polyline of exactly evaluated points."""
+    rng = np.random.default_rng(seed)
+    ts = np.linspace(0.0, 1.0, 200_001)
+    for i in range(n):
+        cps, w = random_rational(rng, 1 + i % 5)
+        pts = rat_eval(cps, w, ts)
+        for _ in range(3):
+            p = rng.uniform(-1.2, 1.2, 2)
+            if np.min(np.hypot(*(pts - p).T)) < 2e-3:
+                continue
+            v = pts - p
+            a = np.arctan2(v[:, 1], v[:, 0])
+            dd = (np.diff(a) + np.pi) % TWO_PI - np.pi
+            ang, bnd, _ = oracle.segment_wn(cps, p, eps=1e-12, L=L, weights=w)
+            assert not bnd and abs(ang - dd.sum()) < 1e-6, (ang, dd.sum())
+
+
+def pin_rational_invariants(L, n=60, seed=34):
+    """Scaling every weight leaves the curve; so does w_i -> w_i c^i (a
+    reparametrization, which changes the bound and the recursion); unit
+    weights are the polynomial segment."""
+    rng = np.random.default_rng(seed)
+    for i in range(n):
+        deg = 1 + i % 5
+        cps, w = random_rational(rng, deg)
+        p = rng.uniform(-1.2, 1.2, 2)
+        a0, b0, _ = oracle.segment_wn(cps, p, eps=1e-12, L=L, weights=w)
+        a1, b1, _ = oracle.segment_wn(cps, p, eps=1e-12, L=L, weights=3.7 * w)
+        c = rng.uniform(0.5, 2.0)
+        a2, b2, _ = oracle.segment_wn(cps, p, eps=1e-12, L=L, weights=w * c ** np.arange(deg + 1))
+        a3, b3, _ = oracle.segment_wn(cps, p, eps=1e-12, L=L, weights=np.ones(deg + 1))
+        a4, b4, _ = oracle.segment_wn(cps, p, eps=1e-12, L=L)
+        if b0 or b1 or b2:
+            continue
+        assert abs(a0 - a1) < 1e-11 and abs(a0 - a2) < 1e-9, (a0, a1, a2)
+        assert b3 == b4 and abs(a3 - a4) < 1e-12
+
+
 def pin_errors(L):
     """Inputs that violate the paper's assumptions are rejected."""
     P = TWO_PI
@@ -592,6 +719,8 @@ PLANAR_PINS = [pin_polygon_exact, pin_single_chord, pin_circles, pin_hull_oracle
                pin_bound_contains_curve, pin_eval, pin_depth_bound, pin_boundary_points,
                pin_classification, pin_config1_integers, pin_table3_shape,
                pin_boundary_fraction]
+RATIONAL_PINS = [pin_rational_circle_arcs, pin_rational_bound, pin_rational_dense_polyline,
+                 pin_rational_invariants]
 PERIODIC_PINS = [pin_cylinder_closed_form, pin_torus_bands, pin_lattice_translate,
                  pin_window_enlargement, pin_unfold_3x3, pin_lift_homology, pin_errors]
-ALL_PINS = PLANAR_PINS + PERIODIC_PINS
+ALL_PINS = PLANAR_PINS + RATIONAL_PINS + PERIODIC_PINS

@@ -35,7 +35,7 @@ MUTANTS = [
      "q[2 * i] = t * q[2 * i] + (1.0 - t) * q[2 * i + 2];", "de Casteljau weights swapped"),
     ("return seg_wn(s, px, py, m, b, gm, gb, eps, depth + 1, acc);",
      "return seg_wn(s, px, py, m, b, ga, gb, eps, depth + 1, acc);", "wrong endpoint on recursion"),
-    ("or_eval(s->deg, s->P, m, gm);", "or_eval(s->deg, s->P, 0.5, gm);", "midpoint of the root"),
+    ("or_eval_w(s->deg, s->P, s->W, m, gm);", "or_eval_w(s->deg, s->P, s->W, 0.5, gm);", "midpoint of the root"),
     ("acc->half += cr > 0 ? 1 : -1;", "acc->half += cr > 0 ? -1 : 1;", "line-term side"),
     ("double klo = ceil(sp - L->smax), khi",
      "double klo = ceil(sp - L->smax) + 1.0, khi", "slab window off by one"),
@@ -53,6 +53,12 @@ MUTANTS = [
     ("double clo = ceil((np - D->phi[k]) / PP), chi = floor((np - D->plo[k]) / PP);",
      "double clo = ceil((np - D->plo[k]) / PP), chi = floor((np - D->plo[k]) / PP);",
      "family window edge"),
+    ("out[0] = h[0] / h[2];", "out[0] = h[0];", "rational point not divided by its weight"),
+    ("h[3 * i + 2] = W[i];", "h[3 * i + 2] = 1.0;", "rational denominator without the weights"),
+    ("const double b1 = (double)deg * r * dall, b2 = (double)deg * r * r * dnext;",
+     "const double b1 = (double)deg * dall, b2 = (double)deg * dnext;", "rational bound without the weight ratio"),
+    ("D->seg[s].W = D->w ? D->w + off : NULL;", "D->seg[s].W = D->w ? D->w : NULL;",
+     "first segment's weights for every segment"),
 ]
 
 # fast pins first, so that most mutants fail within a second
@@ -61,7 +67,8 @@ BATTERY = [pins.pin_single_chord, pins.pin_circles, pins.pin_polygon_exact,
            pins.pin_eval, pins.pin_additivity_elevation_reversal, pins.pin_unit_jump,
            pins.pin_cylinder_closed_form, pins.pin_torus_bands, pins.pin_lift_homology,
            pins.pin_window_enlargement, pins.pin_lattice_translate, pins.pin_unfold_3x3,
-           pins.pin_config1_integers]
+           pins.pin_config1_integers, pins.pin_rational_circle_arcs, pins.pin_rational_bound,
+           pins.pin_rational_invariants, pins.pin_rational_dense_polyline]
 
 
 def _build_mutant(src_text, tmpdir, idx):

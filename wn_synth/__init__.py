@@ -56,15 +56,25 @@ def bezier_point(cps: np.ndarray, t):
 
 
 def make_domain(loops, period_u=0.0, period_v=0.0, eps=1e-9):
-    """Pack a list of loops (each a list of (n+1,2) control-point arrays)."""
-    degs, cps, offs = [], [], [0]
+    """Pack a list of loops (each a list of (n+1,2) control-point arrays).
+    A segment may also be a pair (control points, weights) of a rational
+    segment; a domain with any rational segment carries "weights", one per
+    control point (1 for the polynomial segments)."""
+    degs, cps, wts, offs = [], [], [], [0]
+    rational = False
     for loop in loops:
         for seg in loop:
-            seg = np.asarray(seg, dtype=np.float64)
+            if isinstance(seg, tuple):
+                seg, w = np.asarray(seg[0], dtype=np.float64), np.asarray(seg[1], dtype=np.float64)
+                rational = True
+            else:
+                seg = np.asarray(seg, dtype=np.float64)
+                w = np.ones(seg.shape[0])
             degs.append(seg.shape[0] - 1)
             cps.append(seg)
+            wts.append(w)
         offs.append(offs[-1] + len(loop))
-    return {
+    dom = {
         "loop_offsets": np.asarray(offs, dtype=np.int32),
         "degrees": np.asarray(degs, dtype=np.int32),
         "cps": np.ascontiguousarray(np.concatenate(cps, axis=0)) if cps else np.zeros((0, 2)),
@@ -72,6 +82,50 @@ def make_domain(loops, period_u=0.0, period_v=0.0, eps=1e-9):
         "period_v": float(period_v),
         "eps": float(eps),
     }
+    if rational:
+        dom["weights"] = np.ascontiguousarray(np.concatenate(wts))
+    return dom
+
+
+def domain_weights(dom):
+    """Per-segment weight arrays (None for a polynomial domain)."""
+    if "weights" not in dom:
+        return None
+    out, off = [], 0
+    for d in dom["degrees"]:
+        out.append(dom["weights"][off:off + d + 1])
+        off += d + 1
+    return out
+
+
+def rational_arc(center, radius, a0, theta):
+    """Exact circular arc of angle theta (|theta| < pi) from angle a0, as a
+    rational quadratic: middle point on the tangents' intersection, weight
+    cos(theta/2)."""
+    c = np.asarray(center, dtype=np.float64)
+    h = abs(theta) / 2.0
+    p0 = c + radius * np.array([math.cos(a0), math.sin(a0)])
+    p2 = c + radius * np.array([math.cos(a0 + theta), math.sin(a0 + theta)])
+    am = a0 + theta / 2.0
+    p1 = c + radius / math.cos(h) * np.array([math.cos(am), math.sin(am)])
+    return np.array([p0, p1, p2]), np.array([1.0, math.cos(h), 1.0])
+
+
+def rational_circle_loop(center, radius, angles, ccw=True):
+    """Closed loop of exact rational arcs whose angles (radians, each below
+    pi) sum to 2 pi; CW when ccw is False."""
+    a = 0.0
+    sgn = 1.0 if ccw else -1.0
+    segs = []
+    for th in angles:
+        cps, w = rational_arc(center, radius, sgn * a, sgn * th)
+        segs.append((cps, w))
+        a += th
+    # close exactly: the last end is the first start
+    last = segs[-1][0].copy()
+    last[-1] = segs[0][0][0]
+    segs[-1] = (last, segs[-1][1])
+    return segs
 
 
 def domain_segments(dom):
@@ -175,18 +229,30 @@ def _near_points(rng, dom, count, off_lo, off_hi=None):
         off = np.exp(rng.uniform(math.log(off_lo), math.log(off_hi), count))
     degs = dom["degrees"].astype(np.int64)
     start = np.concatenate([[0], np.cumsum(degs + 1)[:-1]])
+    wall = dom.get("weights")
     out = np.empty((count, 2))
     for n in np.unique(degs[which]):
         sel = np.nonzero(degs[which] == n)[0]
         base = start[which[sel]]
-        cps = dom["cps"][base[:, None] + np.arange(n + 1)[None, :]]      # (k, n+1, 2)
+        idx = base[:, None] + np.arange(n + 1)[None, :]
+        cps = dom["cps"][idx]      # (k, n+1, 2)
+        wt = np.ones((sel.size, n + 1)) if wall is None else wall[idx]
         tt = t[sel][:, None]
-        pt = np.zeros((sel.size, 2))
-        dv = np.zeros((sel.size, 2))
+        # placement only: homogeneous Bernstein sums (x w, y w, w) and their
+        # derivative give the point and the tangent direction
+        hp = np.zeros((sel.size, 3))
+        hd = np.zeros((sel.size, 3))
+        H = np.concatenate([cps * wt[:, :, None], wt[:, :, None]], axis=2)
         for k in range(n + 1):
-            pt += comb(n, k) * tt ** k * (1 - tt) ** (n - k) * cps[:, k]
+            hp += comb(n, k) * tt ** k * (1 - tt) ** (n - k) * H[:, k]
         for k in range(n):
-            dv += n * comb(n - 1, k) * tt ** k * (1 - tt) ** (n - 1 - k) * (cps[:, k + 1] - cps[:, k])
+            hd += n * comb(n - 1, k) * tt ** k * (1 - tt) ** (n - 1 - k) * (H[:, k + 1] - H[:, k])
+        if wall is None:        # polynomial: the Bernstein sums themselves
+            pt = hp[:, :2]
+            dv = hd[:, :2]
+        else:
+            pt = hp[:, :2] / hp[:, 2:3]
+            dv = (hd[:, :2] * hp[:, 2:3] - hp[:, :2] * hd[:, 2:3])
         L = np.hypot(dv[:, 0], dv[:, 1])
         ok = L > 0
         nh = np.zeros((sel.size, 2))
