@@ -15,7 +15,7 @@ achieved FP32 rate against the ALU peak, the FP64 oracle on the host cores
 and the SM clocks seen during the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload 1..5]
+                    [--workload 1..6]
 """
 from __future__ import annotations
 
@@ -86,6 +86,11 @@ def workload(k, scale=1.0, shard=0):
         d, q = ws.config4(seed_index=4 + off)
         return d, q, ("10k faces, log-normal segments (median 40) and queries (median 4096, ~2e8 total), "
                       "20% periodic" + tag)
+    if k == 6:
+        d, q = ws.config6(seed_index=6 + off, n_uniform=int(10_000_000 * scale), n_near=int(1_000_000 * scale))
+        return d, q, ("64 planar domains of rational segments (weights log-uniform in [0.8, 1.25]): workload 2's "
+                      "open/noisy star loops plus two exact rational-arc circles per face; 10M uniform + 1M "
+                      "near-curve queries" + (f" at {scale:g} of its queries" if scale != 1.0 else "") + tag)
     if k == 5:
         d = [ws.config5_face(64 * shard + f) for f in range(64)]
         return d, None, ("64 planar faces of ~100k cubics (fractal outer loop + 200 holes), 4096x4096 "

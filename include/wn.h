@@ -96,6 +96,27 @@ wn_status wn_create_domain(const int32_t *loop_offsets, int32_t n_loops,
                            double period_u, double period_v, double epsilon,
                            wn_domain **out);
 
+/*
+ * wn_create_domain for rational Bezier segments (Sec. 3.1 admits rational
+ * p-curves; App. A.1 gives their derivative bounds).
+ *
+ *   weights         host double[sum(degrees[s] + 1)], one per control point,
+ *                   each finite and > 0; NULL is wn_create_domain.  A segment
+ *                   whose weights are all equal is the polynomial curve.
+ *
+ * gamma(t) = sum w_i B_i(t) P_i / sum w_i B_i(t).  The bound of Lemma 1 /
+ * Eq. 5 for a rational segment is the smaller of n (W/w) max |P_i - P_j| and
+ * n (W/w)^2 max |P_i - P_{i-1}| (W, w: largest and smallest weight); the
+ * rest of the method is unchanged (the ellipse bound holds for any curve
+ * whose speed B bounds).  The other arguments, the errors and the ownership
+ * rules are those of wn_create_domain; a non-positive or non-finite weight is
+ * WN_ERR_ARG.
+ */
+wn_status wn_create_domain_rational(const int32_t *loop_offsets, int32_t n_loops,
+                                    const int32_t *degrees, const double *control_points,
+                                    const double *weights, double period_u, double period_v,
+                                    double epsilon, wn_domain **out);
+
 /* Free a domain (NULL is ignored).  Waits for the device to finish. */
 void wn_destroy_domain(wn_domain *domain);
 

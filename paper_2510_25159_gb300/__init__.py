@@ -55,6 +55,7 @@ def lib():
         L = ctypes.CDLL(path)
         P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         L.wn_create_domain.argtypes = [P, I32, P, P, D, D, D, ctypes.POINTER(ctypes.c_void_p)]
+        L.wn_create_domain_rational.argtypes = [P, I32, P, P, P, D, D, D, ctypes.POINTER(ctypes.c_void_p)]
         L.wn_destroy_domain.argtypes = [P]
         L.wn_destroy_domain.restype = None
         L.wn_query.argtypes = [P, P, I64, P, P, ctypes.c_int, P]
@@ -72,7 +73,7 @@ def lib():
         L.wn_kernel_times.argtypes = [P, P]
         L.wn_set_work_counting.argtypes = [I32]
         L.wn_sweep_work.argtypes = [P]
-        for f in ("wn_create_domain", "wn_query", "wn_query_batched", "wn_query_grid_bitmask",
+        for f in ("wn_create_domain", "wn_create_domain_rational", "wn_query", "wn_query_batched", "wn_query_grid_bitmask",
                   "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times", "wn_autotune",
                   "wn_get_tuning", "wn_set_work_counting", "wn_sweep_work"):
             getattr(L, f).restype = ctypes.c_int
@@ -103,22 +104,32 @@ def _stream(stream):
 
 
 class Domain:
-    """One face's trimming loops (``wn_create_domain``)."""
+    """One face's trimming loops (``wn_create_domain``; with ``weights``, one
+    per control point, ``wn_create_domain_rational``)."""
 
-    def __init__(self, loop_offsets, degrees, control_points, period_u=0.0, period_v=0.0, eps=0.0):
+    def __init__(self, loop_offsets, degrees, control_points, period_u=0.0, period_v=0.0, eps=0.0,
+                 weights=None):
         lo = np.ascontiguousarray(loop_offsets, dtype=np.int32)
         dg = np.ascontiguousarray(degrees, dtype=np.int32)
         cp = np.ascontiguousarray(control_points, dtype=np.float64).reshape(-1)
         h = ctypes.c_void_p()
         self._h = None
-        _check(lib().wn_create_domain(_ptr(lo), len(lo) - 1, _ptr(dg), _ptr(cp), float(period_u),
-                                      float(period_v), float(eps), ctypes.byref(h)))
+        if weights is None:
+            _check(lib().wn_create_domain(_ptr(lo), len(lo) - 1, _ptr(dg), _ptr(cp), float(period_u),
+                                          float(period_v), float(eps), ctypes.byref(h)))
+        else:
+            wt = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+            if wt.size * 2 != cp.size:
+                raise ValueError("one weight per control point")
+            _check(lib().wn_create_domain_rational(_ptr(lo), len(lo) - 1, _ptr(dg), _ptr(cp), _ptr(wt),
+                                                   float(period_u), float(period_v), float(eps),
+                                                   ctypes.byref(h)))
         self._h = h
 
     @classmethod
     def from_dict(cls, d, eps=None):
         return cls(d["loop_offsets"], d["degrees"], d["cps"], d["period_u"], d["period_v"],
-                   d["eps"] if eps is None else eps)
+                   d["eps"] if eps is None else eps, weights=d.get("weights"))
 
     @property
     def handle(self):

@@ -128,7 +128,7 @@ DevState *dev_state(wn_status &st)
 }
 
 // Scratch of the mixed path sized for n queries.
-cudaError_t ensure_work(Work &W, int64_t n)
+cudaError_t ensure_work(Work &W, int64_t n, int64_t near_expected)
 {
     cudaError_t e = cudaSuccess;
     int64_t nq = std::max<int64_t>(n, 1024);
@@ -140,7 +140,9 @@ cudaError_t ensure_work(Work &W, int64_t n)
         if ((e = grow(W.esc_q, c3, nq)) != cudaSuccess) return e;
         W.cap_q = nq;
     }
-    const int64_t need_near = std::max<int64_t>(1 << 22, 3 * nq);
+    // near pairs: 3 per query or twice the expected count, whichever is more
+    // (an overflowing pair sends its query to the FP64 recomputation)
+    const int64_t need_near = std::max<int64_t>(std::max<int64_t>(1 << 22, 3 * nq), 2 * near_expected);
     if ((e = grow(W.near_items, W.cap_near, need_near)) != cudaSuccess) return e;
     const int64_t need_f64 = std::max<int64_t>(1 << 18, nq / 8);
     if ((e = grow(W.f64_items, W.cap_f64, need_f64)) != cudaSuccess) return e;
@@ -161,16 +163,16 @@ const char *wn_last_error(void) { return g_err.c_str(); }
 
 const char *wn_version(void) { return "wn 0.1 (sm_103a)"; }
 
-wn_status wn_create_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
-                           const double *control_points, double period_u, double period_v,
-                           double epsilon, wn_domain **out)
+wn_status wn_create_domain_rational(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
+                                    const double *control_points, const double *weights, double period_u,
+                                    double period_v, double epsilon, wn_domain **out)
 {
     if (!out) return fail(WN_ERR_ARG, "out is NULL");
     *out = nullptr;
     std::string err;
     int rc;
     try {
-        rc = build_domain(loop_offsets, n_loops, degrees, control_points, period_u, period_v,
+        rc = build_domain(loop_offsets, n_loops, degrees, control_points, weights, period_u, period_v,
                           epsilon, out, err);
     } catch (const std::bad_alloc &) {
         return fail(WN_ERR_OOM, "host allocation failed");
@@ -178,6 +180,14 @@ wn_status wn_create_domain(const int32_t *loop_offsets, int32_t n_loops, const i
     if (rc != 0) return fail((wn_status)rc, err);
     g_err.clear();
     return WN_OK;
+}
+
+wn_status wn_create_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
+                           const double *control_points, double period_u, double period_v,
+                           double epsilon, wn_domain **out)
+{
+    return wn_create_domain_rational(loop_offsets, n_loops, degrees, control_points, nullptr, period_u,
+                                     period_v, epsilon, out);
 }
 
 void wn_destroy_domain(wn_domain *d)
@@ -371,7 +381,11 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             S->key_qpt = key;
             drop_graphs();
         }
-        if ((e = ensure_work(S->W, n)) != cudaSuccess) return cuda_fail(e, "scratch");
+        double near_expected = 0.0;
+        for (int d = 0; d < n_domains; d++)
+            near_expected += (double)(offsets[d + 1] - offsets[d]) * domains[d]->near_density;
+        near_expected = std::fmin(near_expected, 4e9);
+        if ((e = ensure_work(S->W, n, (int64_t)near_expected)) != cudaSuccess) return cuda_fail(e, "scratch");
         LaunchCfg cfg{S->n_sm, g_tun, S->profiling ? &S->events : nullptr};
         if (S->counting) cfg.work = S->d_work;
         cfg.grid_tiled = grid_tiled;

@@ -106,7 +106,10 @@ struct DomDev {
     int n_nodes;
     int all_root;               // planar: root over every loop (-1: per-loop roots)
     const float4 *cp32;         // [total_cp] P - origin as FP32 (hi.x, hi.y, lo.x, lo.y)
-    const int4 *seg_info;       // [n_segs] (first control point, degree, B as FP32 bits, 0)
+    const int4 *seg_info;       // [n_segs] (first control point, degree, B as FP32 bits, weight
+                                //   ratio W/w as FP32 bits for a rational segment, else 0)
+    const double *w;            // [total_cp] weights, or null when no segment is rational
+    const float *w32;           // [total_cp] the weights rounded to FP32, or null
     float eps32;                // eps rounded to FP32
     int pad4;
 };
@@ -323,6 +326,85 @@ __device__ __forceinline__ void bez_eval(const T *cx, const T *cy, int n, int nm
     }
 }
 
+// A rational segment: de Casteljau on the homogeneous control points
+// (w x, w y, w) -- the curve is their central projection -- then the
+// division by the weight coordinate.
+template <typename T, int NM>
+__device__ __forceinline__ void bez_eval_h_n(const T *hx, const T *hy, const T *hw, int n, T t, T &ox, T &oy)
+{
+    T qx[NM + 1], qy[NM + 1], qw[NM + 1];
+#pragma unroll
+    for (int i = 0; i <= NM; i++) {
+        qx[i] = hx[i];
+        qy[i] = hy[i];
+        qw[i] = i <= n ? hw[i] : T(1);     // hw may point into a longer array
+    }
+    const T s = T(1) - t;
+#pragma unroll
+    for (int r = 1; r <= NM; r++) {
+#pragma unroll
+        for (int i = 0; i <= NM - r; i++) {
+            if (i <= n - r) {
+                qx[i] = s * qx[i] + t * qx[i + 1];
+                qy[i] = s * qy[i] + t * qy[i + 1];
+                qw[i] = s * qw[i] + t * qw[i + 1];
+            }
+        }
+    }
+    const T r = T(1) / qw[0];          // one division per point
+    ox = qx[0] * r;
+    oy = qy[0] * r;
+}
+
+template <typename T>
+__device__ __forceinline__ void bez_eval_h(const T *hx, const T *hy, const T *hw, int n, int nmax, T t, T &ox,
+                                           T &oy)
+{
+    switch (nmax) {
+    case 1: bez_eval_h_n<T, 1>(hx, hy, hw, n, t, ox, oy); break;
+    case 2: bez_eval_h_n<T, 2>(hx, hy, hw, n, t, ox, oy); break;
+    case 3: bez_eval_h_n<T, 3>(hx, hy, hw, n, t, ox, oy); break;
+    case 4: bez_eval_h_n<T, 4>(hx, hy, hw, n, t, ox, oy); break;
+    case 5: bez_eval_h_n<T, 5>(hx, hy, hw, n, t, ox, oy); break;
+    case 6: bez_eval_h_n<T, 6>(hx, hy, hw, n, t, ox, oy); break;
+    default: bez_eval_h_n<T, kMaxDeg>(hx, hy, hw, n, t, ox, oy); break;
+    }
+}
+
+// Control points of one segment for the FP64 recursions: plain, or
+// homogeneous (w x, w y, w) when Wt (its weights) is not null.
+struct SegF64 {
+    double cx[kNcp], cy[kNcp], cw[kNcp];
+    int n, nmax;
+    bool rat;
+    __device__ __forceinline__ void load(const double *P, const double *Wt, int n_, int nmax_)
+    {
+        n = n_;
+        nmax = nmax_;
+        rat = Wt != nullptr;
+#pragma unroll
+        for (int i = 0; i < kNcp; i++) {
+            const double w = (rat && i <= n) ? Wt[i] : 1.0;
+            cx[i] = (i <= n) ? w * P[2 * i] : 0.0;
+            cy[i] = (i <= n) ? w * P[2 * i + 1] : 0.0;
+            cw[i] = w;
+        }
+    }
+    __device__ __forceinline__ void eval(double t, double &x, double &y) const
+    {
+        if (rat) bez_eval_h<double>(cx, cy, cw, n, nmax, t, x, y);
+        else bez_eval<double>(cx, cy, n, nmax, t, x, y);
+    }
+};
+
+// Weights of segment s, or null when it is polynomial.
+__device__ __forceinline__ const double *seg_weights(const DomDev &D, int s)
+{
+    if (!D.w) return nullptr;
+    const int4 si = D.seg_info[s];
+    return si.w ? D.w + si.x : nullptr;
+}
+
 // ---------------------------------------------------------------- Alg. 1, FP64
 // Far actions of Algorithm 1: the chord of an excluded sub-segment either adds
 // its signed angle (Eq. 3, the plain method) or its signed crossing of the
@@ -353,19 +435,15 @@ struct FarCross {
 // true when the query is on the boundary (an evaluated point closer than eps,
 // or the depth cap).
 template <class Far>
-__device__ bool alg1_fp64(const double *P, int n, int nmax, double B, double px, double py, double eps,
-                          Far &far)
+__device__ bool alg1_fp64(const double *P, const double *Wt, int n, int nmax, double B, double px, double py,
+                          double eps, Far &far)
 {
-    double cx[kNcp], cy[kNcp];
-#pragma unroll
-    for (int i = 0; i < kNcp; i++) {
-        cx[i] = (i <= n) ? P[2 * i] : 0.0;
-        cy[i] = (i <= n) ? P[2 * i + 1] : 0.0;
-    }
+    SegF64 sg;              // loaded at the first evaluation: most segments are far at the root
+    bool loaded = false;
     double st_t[kDepthCap64 + 2], st_x[kDepthCap64 + 2], st_y[kDepthCap64 + 2];
     int st_d[kDepthCap64 + 2];
     double a = 0.0;
-    double ax = cx[0] - px, ay = cy[0] - py;
+    double ax = P[0] - px, ay = P[1] - py;
     double ra = sqrt(ax * ax + ay * ay);
     int sp = 0;
     {
@@ -385,8 +463,12 @@ __device__ bool alg1_fp64(const double *P, int n, int nmax, double B, double px,
             continue;
         }
         if (d >= kDepthCap64) return true;
+        if (!loaded) {
+            sg.load(P, Wt, n, nmax);
+            loaded = true;
+        }
         double m = 0.5 * (a + b), mx, my;
-        bez_eval<double>(cx, cy, n, nmax, m, mx, my);
+        sg.eval(m, mx, my);
         st_d[sp - 1] = d + 1;
         st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;
         sp++;
@@ -398,25 +480,21 @@ __device__ bool alg1_fp64(const double *P, int n, int nmax, double B, double px,
 // the signed crossings of the +x ray from (px, py) by its chords; the end
 // points take the given signs (those of the FP32 chain around it).
 // Returns true when the query is on the boundary.
-__device__ inline bool alg1_fp64_sub(const double *P, int n, int nmax, double B, double px, double py,
-                                     double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
+__device__ inline bool alg1_fp64_sub(const double *P, const double *Wt, int n, int nmax, double B, double px,
+                                     double py, double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
 {
-    double cx[kNcp], cy[kNcp];
-#pragma unroll
-    for (int i = 0; i < kNcp; i++) {
-        cx[i] = (i <= n) ? P[2 * i] : 0.0;
-        cy[i] = (i <= n) ? P[2 * i + 1] : 0.0;
-    }
+    SegF64 sg;
+    sg.load(P, Wt, n, nmax);
     double st_t[kDepthCap64 + 2], st_x[kDepthCap64 + 2], st_y[kDepthCap64 + 2];
     int st_d[kDepthCap64 + 2];
     double gx, gy;
-    if (a0 == 0.0) { gx = cx[0]; gy = cy[0]; }
-    else bez_eval<double>(cx, cy, n, nmax, a0, gx, gy);
+    if (a0 == 0.0) { gx = P[0]; gy = P[1]; }
+    else sg.eval(a0, gx, gy);
     double a = a0, ax = gx - px, ay = gy - py;
     bool sa = sa0;
     double ra = sqrt(ax * ax + ay * ay);
-    if (b0 == 1.0) { gx = cx[n]; gy = cy[n]; }
-    else bez_eval<double>(cx, cy, n, nmax, b0, gx, gy);
+    if (b0 == 1.0) { gx = P[2 * n]; gy = P[2 * n + 1]; }
+    else sg.eval(b0, gx, gy);
     int d0 = 0;
     for (double w = b0 - a0; w < 1.0 && d0 < kDepthCap64; w *= 2.0) d0++;
     st_t[0] = b0; st_x[0] = gx - px; st_y[0] = gy - py; st_d[0] = d0;
@@ -441,7 +519,7 @@ __device__ inline bool alg1_fp64_sub(const double *P, int n, int nmax, double B,
         if (d >= kDepthCap64) return true;
         const double m = 0.5 * (a + b);
         double mx, my;
-        bez_eval<double>(cx, cy, n, nmax, m, mx, my);
+        sg.eval(m, mx, my);
         st_d[sp - 1] = d + 1;
         st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;
         sp++;

@@ -70,8 +70,8 @@ long long lround_ll(double x) { return (long long)std::llround(x); }
 }  // namespace
 
 int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
-                 const double *cps, double Pu, double Pv, double eps, wn_domain **out,
-                 std::string &err)
+                 const double *cps, const double *weights, double Pu, double Pv, double eps,
+                 wn_domain **out, std::string &err)
 {
     *out = nullptr;
     if (n_loops < 0 || !loop_offsets || (n_loops > 0 && (!degrees || !cps))) {
@@ -113,6 +113,23 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             err = "control points must be finite";
             return 1;
         }
+    // rational input: a segment whose weights are not all equal is rational
+    // (equal weights give the polynomial curve); weights must be positive
+    std::vector<double> Wt;
+    std::vector<char> seg_rat(ns, 0);
+    bool rational = false;
+    if (weights) {
+        Wt.assign(weights, weights + ncp);
+        for (long long i = 0; i < ncp; i++)
+            if (!(Wt[i] > 0) || !std::isfinite(Wt[i])) {
+                err = "weights must be finite and > 0";
+                return 1;
+            }
+        for (int s = 0; s < ns; s++)
+            for (int i = 1; i <= seg_deg[s]; i++)
+                if (Wt[seg_cp[s] + i] != Wt[seg_cp[s]]) seg_rat[s] = 1;
+        for (int s = 0; s < ns; s++) rational |= seg_rat[s] != 0;
+    }
     const int kind = (Pu > 0 && Pv > 0) ? DK_BI : (Pu > 0) ? DK_UNI_U : (Pv > 0) ? DK_UNI_V : DK_PLANAR;
     if (!(eps > 0)) {
         double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
@@ -154,10 +171,32 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             const double *q = &P[2 * seg_cp[s]];
             const int n = seg_deg[s];
             double B = 0.0;
-            for (int i = 1; i <= n; i++) {
-                double dx = q[2 * i] - q[2 * i - 2], dy = q[2 * i + 1] - q[2 * i - 1];
-                double b = (double)n * std::sqrt(dx * dx + dy * dy);
-                if (b > B) B = b;
+            if (!seg_rat[s]) {
+                // Lemma 1: the hodograph's control polygon, n |P_i - P_{i-1}|
+                for (int i = 1; i <= n; i++) {
+                    double dx = q[2 * i] - q[2 * i - 2], dy = q[2 * i + 1] - q[2 * i - 1];
+                    double b = (double)n * std::sqrt(dx * dx + dy * dy);
+                    if (b > B) B = b;
+                }
+            } else {
+                // App. A.1 (rational): n (W/w) max |P_i - P_j| and
+                // n (W/w)^2 max |P_i - P_{i-1}| both bound |gamma'|; the smaller
+                const double *w = &Wt[seg_cp[s]];
+                double wmax = w[0], wmin = w[0];
+                for (int i = 1; i <= n; i++) {
+                    wmax = std::fmax(wmax, w[i]);
+                    wmin = std::fmin(wmin, w[i]);
+                }
+                const double r = wmax / wmin;
+                double dall = 0.0, dnext = 0.0;
+                for (int i = 0; i <= n; i++)
+                    for (int j = i + 1; j <= n; j++) {
+                        const double dx = q[2 * j] - q[2 * i], dy = q[2 * j + 1] - q[2 * i + 1];
+                        const double d = std::sqrt(dx * dx + dy * dy);
+                        dall = std::fmax(dall, d);
+                        if (j == i + 1) dnext = std::fmax(dnext, d);
+                    }
+                B = std::fmin((double)n * r * dall, (double)n * r * r * dnext);
             }
             segB[s] = B;
             for (int i = 0; i <= n; i++) {
@@ -600,12 +639,31 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         std::vector<int4> info(ns);
         for (int i = 0; i < ns; i++) {
             const float b32 = (float)segB[i];
-            int bi;
+            int bi, ri = 0;
             std::memcpy(&bi, &b32, 4);
-            info[i] = make_int4(seg_cp[i], seg_deg[i], bi, 0);
+            if (seg_rat[i]) {
+                // weight ratio W/w of the segment, rounded up, for the FP32 error bound
+                const double *w = &Wt[seg_cp[i]];
+                double wmax = w[0], wmin = w[0];
+                for (int k = 1; k <= seg_deg[i]; k++) {
+                    wmax = std::fmax(wmax, w[k]);
+                    wmin = std::fmin(wmin, w[k]);
+                }
+                const float r32 = std::nextafter((float)(wmax / wmin), INFINITY);
+                std::memcpy(&ri, &r32, 4);
+            }
+            info[i] = make_int4(seg_cp[i], seg_deg[i], bi, ri);
         }
         dv.cp32 = up.up(cp32);
         dv.seg_info = up.up(info);
+        if (rational) {
+            // weights of the rational segments (1 elsewhere: those evaluate as
+            // polynomials, the seg_info ratio says which)
+            std::vector<float> w32(ncp);
+            for (long long i = 0; i < ncp; i++) w32[i] = (float)Wt[i];
+            dv.w = up.up(Wt);
+            dv.w32 = up.up(w32);
+        }
         dv.eps32 = (float)eps;
     }
     dv.nodes = up.up(nodes);
@@ -859,6 +917,20 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     D->n_instances = (int64_t)inst.size();
     D->sweep_records = 0;
     for (const InstDev &in : inst) D->sweep_records += in.r1 - in.r0;
+    {
+        // circle area of every record over the area queries come from (the
+        // base tile on periodic axes, else the control-point box), counted
+        // once per instance that sweeps it: the near queue is sized from it
+        double area = 0.0;
+        for (size_t r = 0; r < rec.size() / 4; r++) {
+            const double R = std::sqrt((double)rec[4 * r + 1].z);
+            area += M_PI * R * R;
+        }
+        const double wx = Pu > 0 ? Pu : std::fmax(bx1 - bx0, 1e-300);
+        const double wy = Pv > 0 ? Pv : std::fmax(by1 - by0, 1e-300);
+        const double per_inst = rec.empty() ? 0.0 : (double)D->sweep_records / (double)(rec.size() / 4);
+        D->near_density = std::fmin(area / (wx * wy) * std::fmax(per_inst, 1.0), 1e6);
+    }
     *out = D;
     return 0;
 }

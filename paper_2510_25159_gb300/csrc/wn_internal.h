@@ -16,6 +16,8 @@ struct wn_domain {
     int64_t n_records;
     int64_t n_instances;
     int64_t sweep_records;     // sum over instances of their record counts
+    double near_density;       // expected near pairs per uniform query: sum of the records'
+                               // circle areas over the query area
 };
 
 namespace wn {
@@ -106,7 +108,7 @@ cudaError_t launch_pe_eval(const DomDev *d_dom, const PeReq *d_req, int n, doubl
 
 // Domain build (wn_domain.cu)
 int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
-                 const double *cps, double Pu, double Pv, double eps, wn_domain **out,
-                 std::string &err);
+                 const double *cps, const double *weights, double Pu, double Pv, double eps,
+                 wn_domain **out, std::string &err);
 
 }  // namespace wn

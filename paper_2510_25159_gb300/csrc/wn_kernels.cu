@@ -948,10 +948,11 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
 // decision (eps test, ellipse test, chord sign, depth) the pair becomes an
 // FP64 work item and its FP32 walk stops.
 struct NearWalk {                      // scalars and control points (registers)
-    float qx[kNcp], qy[kNcp];
+    float qx[kNcp], qy[kNcp];           // q_k = P_k - p; times w_k for a rational segment
+    const float *qw;                    // rational segment: its FP32 weights (global, read per evaluation)
     float a, ax, ay, ra, B, E, eps;
     int n, nmax, sp, cnt;
-    bool sa, b_tested;
+    bool sa, b_tested, rat;
 };
 
 struct NearStack {                     // the walk's stack (dynamically indexed: local memory)
@@ -1009,6 +1010,19 @@ __device__ __forceinline__ float hilo_diff(float ah, float al, float bh, float b
     return d + ((al - bl) + e);
 }
 
+// gamma(t) - p of a rational segment in FP32, out of line so that the
+// polynomial walk keeps its registers: the homogeneous control points come
+// by value (x, y already times w), the weights from global memory.
+__device__ __noinline__ float2 near_eval_rat(float4 x0, float4 x1, float4 y0, float4 y1, const float *qw, int n,
+                                             int nmax, float t)
+{
+    const float hx[kNcp] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    const float hy[kNcp] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+    float mx, my;
+    bez_eval_h<float>(hx, hy, qw, n, nmax, t, mx, my);
+    return make_float2(mx, my);
+}
+
 // Set up the walk of one near pair.  Returns false when the item needs no
 // walk (already decided: *result 0 done, 1 boundary).  The query-relative
 // control points come from FP32 hi/lo pairs (control point and query, both
@@ -1046,7 +1060,12 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
     W.n = deg;
     W.nmax = Dp->max_deg;
     W.B = __int_as_float(si.z);
-    W.E = (float)(2 * deg + 4) * kTwoM24 * mq + eabs;
+    W.rat = si.w != 0;
+    // evaluation error bound: de Casteljau on q (2n + 4 ulps of mq); for a
+    // rational segment the homogeneous sums and the division scale it by
+    // the weight ratio W/w (with a factor 2 to spare)
+    W.E = W.rat ? kTwoM24 * mq * ((float)(8 * deg + 8) * __int_as_float(si.w) + 8.f) + eabs
+                : (float)(2 * deg + 4) * kTwoM24 * mq + eabs;
     W.eps = Dp->eps32;
     W.cnt = 0;
     W.a = 0.f;
@@ -1068,6 +1087,15 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
     S.x[0] = W.qx[deg];
     S.y[0] = W.qy[deg];
     S.d[0] = 0;
+    if (W.rat) {
+        W.qw = Dp->w32 + si.x;
+#pragma unroll
+        for (int k = 0; k < kNcp; k++) {
+            const float w = k <= deg ? __ldg(W.qw + k) : 1.f;
+            W.qx[k] *= w;
+            W.qy[k] *= w;
+        }
+    }
     W.sp = 1;
     W.b_tested = false;
     return true;
@@ -1127,7 +1155,16 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
     }
     const float m = 0.5f * (W.a + b);
     float mx, my;
-    bez_eval<float>(W.qx, W.qy, W.n, W.nmax, m, mx, my);
+    if (W.rat) {
+        const float2 r = near_eval_rat(make_float4(W.qx[0], W.qx[1], W.qx[2], W.qx[3]),
+                                       make_float4(W.qx[4], W.qx[5], W.qx[6], W.qx[7]),
+                                       make_float4(W.qy[0], W.qy[1], W.qy[2], W.qy[3]),
+                                       make_float4(W.qy[4], W.qy[5], W.qy[6], W.qy[7]), W.qw, W.n, W.nmax, m);
+        mx = r.x;
+        my = r.y;
+    } else {
+        bez_eval<float>(W.qx, W.qy, W.n, W.nmax, m, mx, my);
+    }
     S.d[sp - 1] = d + 1;
     S.t[sp] = m;
     S.x[sp] = mx;
@@ -1140,7 +1177,7 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
 
 // One thread per pair, grid-stride: consecutive queue entries come from
 // neighbouring queries of one tile, so a warp's walks stay similar.
-__global__ void __launch_bounds__(256) k_near(const NearArgs A)
+__global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
 {
     unsigned long long n = A.counters[CNT_NEAR];
     if (n > (unsigned long long)A.cap_near) n = (unsigned long long)A.cap_near;
@@ -1182,7 +1219,8 @@ __global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
         const bool sa = si.a == 0.f ? P[1] > pyp : (si.signs & 1u) != 0;
         const bool sb = si.b == 1.f ? P[2 * deg + 1] > pyp : (si.signs & 2u) != 0;
         int cnt = 0;
-        const bool bnd = alg1_fp64_sub(P, deg, Dp->max_deg, Dp->seg_B[s], pxp, pyp, Dp->eps, (double)si.a,
+        const bool bnd = alg1_fp64_sub(P, seg_weights(*Dp, s), deg, Dp->max_deg, Dp->seg_B[s], pxp, pyp, Dp->eps,
+                                       (double)si.a,
                                        (double)si.b, sa, sb, cnt);
         if (bnd) atomicOr(&A.flags[it.q], QF_BOUNDARY);
         else if (cnt) atomicAdd(&A.acc2[it.q], 2 * cnt);
@@ -1213,7 +1251,8 @@ __device__ void plain_query(const DomDev *Dp, double x0, double y0, double &om, 
         // the planar instance covers every loop of the domain
         const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
         for (int s = sb; s < se && !bnd; s++)
-            bnd = alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]), __ldg(&Dp->seg_deg[s]), Dp->max_deg,
+            bnd = alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]), seg_weights(*Dp, s), __ldg(&Dp->seg_deg[s]),
+                            Dp->max_deg,
                             __ldg(&Dp->seg_B[s]), qx, qy, eps, fa);
         if (in.type == IT_PE && !bnd) {
             const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
@@ -1366,7 +1405,8 @@ __global__ void __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
             const double qx = xsub(x, in.Tx), qy = xsub(y, in.Ty);
             const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
             for (int sg = sb + tid; sg < se && !bnd; sg += kEscThreads)
-                bnd |= alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[sg]), __ldg(&Dp->seg_deg[sg]), Dp->max_deg,
+                bnd |= alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[sg]), seg_weights(*Dp, sg),
+                                 __ldg(&Dp->seg_deg[sg]), Dp->max_deg,
                                  __ldg(&Dp->seg_B[sg]), qx, qy, Dp->eps, fa);
             if (in.type == IT_PE && tid == 0) {
                 const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
@@ -1414,13 +1454,10 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
     const double t = (m % 2) ? 0.5 : 0.0;
     const int deg = Dp->seg_deg[s];
     const double *P = Dp->cp + 2 * (size_t)Dp->seg_cp[s];
-    double cx[kNcp], cy[kNcp];
-    for (int k = 0; k < kNcp; k++) {
-        cx[k] = k <= deg ? P[2 * k] : 0.0;
-        cy[k] = k <= deg ? P[2 * k + 1] : 0.0;
-    }
+    SegF64 sgm;
+    sgm.load(P, seg_weights(*Dp, s), deg, Dp->max_deg);
     double mx, my;
-    bez_eval<double>(cx, cy, deg, Dp->max_deg, t, mx, my);
+    sgm.eval(t, mx, my);
     const double Pu = Dp->Pu, Pv = Dp->Pv;
     const double x = xadd(mx, xmul((double)R.IB, Pu)), y = xadd(my, xmul((double)R.JB, Pv));
     const LoopDev &L = Dp->loops[R.a];
@@ -1439,7 +1476,8 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
         const double qx = (Pu > 0) ? xsub(x, xmul((double)(R.IA + kk * L.hp), Pu)) : x;
         const double qy = (Pv > 0) ? xsub(y, xmul((double)(R.JA + kk * L.hq), Pv)) : y;
         for (int sg = L.s0; sg < L.s1; sg++) {
-            if (alg1_fp64(Dp->cp + 2 * (size_t)Dp->seg_cp[sg], Dp->seg_deg[sg], Dp->max_deg, Dp->seg_B[sg], qx, qy,
+            if (alg1_fp64(Dp->cp + 2 * (size_t)Dp->seg_cp[sg], seg_weights(*Dp, sg), Dp->seg_deg[sg], Dp->max_deg,
+                          Dp->seg_B[sg], qx, qy,
                           Dp->eps, fa)) {
                 out[i] = __longlong_as_double(0x7ff8000000000000ULL);
                 return;

@@ -56,6 +56,10 @@ def test_validation_codes_without_gpu(wnlib):
                               ctypes.byref(h)) == 1
     assert L.wn_create_domain(P(lo), 1, P(np.array([1], np.int32)), P(np.array([0.0, 0, np.nan, 1])),
                               0.0, 0.0, 0.0, ctypes.byref(h)) == 1
+    wneg = np.array([1.0, -2.0, 1.0])
+    assert L.wn_create_domain_rational(P(lo), 1, P(np.array([2], np.int32)), P(np.zeros(6)), P(wneg), 0.0, 0.0,
+                                       0.0, ctypes.byref(h)) == 1
+    assert b"weights" in L.wn_last_error()
     assert L.wn_set_tuning(3, 0, 0, -1, -1, -1) == 1
     assert L.wn_sweep_work(None) == 1
     assert L.wn_query(None, None, 0, None, None, 1, None) == 1

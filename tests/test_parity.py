@@ -68,6 +68,33 @@ def test_workload3_biperiodic(wn, name, prec, tol):
 
 
 @pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_rational_open_noisy(wn, name, prec, tol):
+    """Rational segments (every weight log-uniform in [1/2, 2]) on open,
+    noisy loops, plus exact circles of rational arcs."""
+    doms, qs = ws.config6(n_domains=64, n_uniform=64 * 8000, n_near=64 * 1500, domain_subset=range(5))
+    res = run(wn, doms, qs, prec)
+    for d, q, (w, s) in zip(doms, qs, res):
+        compare(d, q, w, s, tol)
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_rational_exact_circles_closed(wn, name, prec, tol):
+    """Closed loops of exact rational arcs: rounded omega and states exact,
+    also for points 1e-7..1e-3 from the circles and on a ragged query count."""
+    rng = np.random.default_rng(8)
+    outer = ws.rational_circle_loop((0.5, 0.5), 0.4, [1.0, 2.0, 1.5, 2 * np.pi - 4.5])
+    holes = [ws.rational_circle_loop((0.35, 0.5), 0.08, [2.5, 2.5, 2 * np.pi - 5.0], ccw=False),
+             ws.rational_circle_loop((0.65, 0.55), 0.1, [np.pi / 2] * 4, ccw=False)]
+    dom = ws.make_domain([outer] + holes, eps=1e-9)
+    r = np.concatenate([0.4 + rng.choice([-1, 1], 3000) * np.exp(rng.uniform(np.log(1e-7), np.log(1e-3), 3000)),
+                        rng.uniform(0, 0.5, 2001)])
+    ph = rng.uniform(0, 2 * np.pi, r.size)
+    q = np.stack([0.5 + r * np.cos(ph), 0.5 + r * np.sin(ph)], axis=1)
+    (w, s), = run(wn, [dom], [q], prec)
+    compare(dom, q, w, s, tol, closed=True)
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
 def test_uniperiodic_cylinders(wn, name, prec, tol):
     rng = ws.rng_for(40)
     doms, qs = [], []

@@ -327,6 +327,49 @@ def config2(n_domains=64, n_uniform=10_000_000, n_near=1_000_000, seed_index=2,
 
 
 # --------------------------------------------------------------------------
+# workload 6: rational segments (the rational case of App. A.1)
+# --------------------------------------------------------------------------
+def config6(n_domains=64, n_uniform=10_000_000, n_near=1_000_000, seed_index=6,
+            loops=(4, 12), segs=(32, 512), domain_subset=None):
+    """Workload 2's open/noisy star loops with every control point weighted
+    (log-uniform in [0.8, 1.25], the range of conic-section weights), plus two
+    holes per face that are exact circles
+    of rational quadratic arcs of unequal angles; queries as in workload 2.
+    Returns (list of domains, list of per-domain query arrays)."""
+    doms, qs = [], []
+    nu = [n_uniform // n_domains + (1 if i < n_uniform % n_domains else 0) for i in range(n_domains)]
+    nn = [n_near // n_domains + (1 if i < n_near % n_domains else 0) for i in range(n_domains)]
+    idx = range(n_domains) if domain_subset is None else domain_subset
+    for d in idx:
+        rng = rng_for(seed_index, salt=d + 1)
+        nl = int(rng.integers(loops[0], loops[1] + 1))
+        lps = []
+        for _ in range(nl):
+            ns = int(rng.integers(segs[0], segs[1] + 1))
+            degs = rng.integers(1, 6, ns)
+            ctr = rng.uniform(0.2, 0.8, 2)
+            rad = rng.uniform(0.05, 0.3)
+            star = star_loop(rng, ctr, rad, ns, degs, noise=1e-4, ccw=True,
+                             bend=0.2, gap_lo=1e-4, gap_hi=1e-2, radial_noise=0.2)
+            lps.append([(s, np.exp(rng.uniform(-math.log(1.25), math.log(1.25), s.shape[0]))) for s in star])
+        for _ in range(2):
+            k = int(rng.integers(3, 7))
+            cuts = np.sort(rng.uniform(0.0, 1.0, k - 1))
+            ang = np.diff(np.concatenate([[0.0], cuts, [1.0]])) * TWO_PI
+            while np.any(ang >= 3.0) or np.any(ang <= 0.05):
+                cuts = np.sort(rng.uniform(0.0, 1.0, k - 1))
+                ang = np.diff(np.concatenate([[0.0], cuts, [1.0]])) * TWO_PI
+            lps.append(rational_circle_loop(rng.uniform(0.2, 0.8, 2), rng.uniform(0.02, 0.1), ang, ccw=False))
+        dom = make_domain(lps, eps=1e-9)
+        qrng = rng_for(seed_index, salt=100000 + d)
+        q = np.concatenate([qrng.uniform(0.0, 1.0, (nu[d], 2)),
+                            _near_points(qrng, dom, nn[d], 1e-7, 1e-3)], axis=0)
+        doms.append(dom)
+        qs.append(np.ascontiguousarray(q))
+    return doms, qs
+
+
+# --------------------------------------------------------------------------
 # periodic helpers
 # --------------------------------------------------------------------------
 def _wrap_segments(segs, pu, pv):
