@@ -179,6 +179,34 @@ wn_status wn_query_grid_bitmask(const wn_domain *domain, int32_t nu, int32_t nv,
                                 wn_stream stream);
 
 /*
+ * Triangles of a trimmed cell-centre grid (the tessellation application of
+ * Sec. 5.4.3): the nu x nv cell centres of a wn_query_grid_bitmask call are
+ * the vertices, vertex (i, j) has index j*nu + i; each quad with lower-left
+ * vertex (i, j) has corners a = (i, j), b = (i+1, j), c = (i, j+1),
+ * d = (i+1, j+1) and triangles (a, b, d) then (a, d, c), counter-clockwise
+ * in (u, v); a triangle is kept when its three vertices have their bit set.
+ * With wrap_u (wrap_v) != 0 the axis is periodic: indices wrap modulo nu
+ * (nv) and the seam quads are included.  Quads are emitted row by row, so
+ * the output order is fixed.
+ *
+ *   bits        device uint32[(nu*nv + 31)/32], the layout of
+ *               wn_query_grid_bitmask.
+ *   out_tris    device int32[3 * capacity]: vertex indices, 3 per triangle;
+ *               only the first `capacity` triangles are written.
+ *   out_count   device int64[1]: the number of kept triangles (may exceed
+ *               capacity: then call again with a larger buffer).
+ *
+ * Three kernels on `stream` and a small stream-ordered allocation
+ * (cudaMallocAsync) for per-block counts.  Errors: WN_ERR_ARG (null or host
+ * pointers, capacity < 0), WN_ERR_LIMIT (nu or nv outside 1..65536, more than
+ * 2^31-1 vertices), WN_ERR_OOM, WN_ERR_CUDA.  No counterpart in the paper's
+ * text beyond the tessellation it describes.
+ */
+wn_status wn_grid_triangles(const uint32_t *bits, int32_t nu, int32_t nv, int32_t wrap_u,
+                            int32_t wrap_v, int32_t *out_tris, int64_t capacity,
+                            int64_t *out_count, wn_stream stream);
+
+/*
  * Tuning knobs of the mixed path (0 keeps the current value for the first
  * three, a negative value keeps it for the last three):
  *   tile_queries_per_thread  1, 2 or 4 queries per sweep thread

@@ -56,6 +56,8 @@ def lib():
         P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         L.wn_create_domain.argtypes = [P, I32, P, P, D, D, D, ctypes.POINTER(ctypes.c_void_p)]
         L.wn_create_domain_rational.argtypes = [P, I32, P, P, P, D, D, D, ctypes.POINTER(ctypes.c_void_p)]
+        L.wn_grid_triangles.argtypes = [P, I32, I32, I32, I32, P, I64, P, P]
+        L.wn_grid_triangles.restype = ctypes.c_int
         L.wn_destroy_domain.argtypes = [P]
         L.wn_destroy_domain.restype = None
         L.wn_query.argtypes = [P, P, I64, P, P, ctypes.c_int, P]
@@ -204,6 +206,24 @@ def query_grid_bitmask(domain, nu, nv, precision=MIXED, stream=None):
     _check(lib().wn_query_grid_bitmask(domain.handle, int(nu), int(nv), _ptr(bits), _ptr(nb),
                                        int(precision), _stream(stream)))
     return bits, nb
+
+
+def grid_triangles(bits, nu, nv, wrap_u=False, wrap_v=False, capacity=None, stream=None):
+    """Kept triangles of a classified cell-centre grid (``bits`` from
+    query_grid_bitmask): (T, 3) int32 device tensor of vertex indices."""
+    import torch
+    if capacity is None:
+        qu = nu if wrap_u else nu - 1
+        qv = nv if wrap_v else nv - 1
+        capacity = 2 * max(qu, 0) * max(qv, 0)
+    tris = torch.empty((max(capacity, 1), 3), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _check(lib().wn_grid_triangles(_ptr(bits), int(nu), int(nv), 1 if wrap_u else 0, 1 if wrap_v else 0,
+                                   _ptr(tris), int(capacity), _ptr(cnt), _stream(stream)))
+    n = int(cnt.item())
+    if n > capacity:
+        raise RuntimeError(f"{n} triangles, capacity {capacity}")
+    return tris[:n]
 
 
 def autotune(domains, points, offsets, iterations=3, stream=None):
