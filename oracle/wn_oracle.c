@@ -55,6 +55,9 @@
  *       (i0 in [0,|p|) for p != 0; i0 = -q, j0 = 0 for p = 0); a family is
  *       summed when n.(x - w_c) lies in the hull of the n-extents of alpha
  *       and of the paired beta, n = (-q Pv, p Pu).
+ *   R10 rational segments (weights w_i > 0): gamma is the projection of the
+ *       polynomial curve of (w_i x_i, w_i y_i, w_i); of the two derivative
+ *       bounds of App. A.1 the smaller is taken (both hold).
  *   R9  pairing: for each alpha in input order, among the remaining beta and
  *       the shifts c0-2..c0+2 (c0 brings beta's start within one family
  *       spacing of alpha's), take the copies left of alpha (ToLeft, Alg. 8,
@@ -68,7 +71,9 @@
  * shape, the boundary fraction trend, closed-form cylinder strips and torus
  * bands (which fix lifting, homology, families, line terms and pairing),
  * lattice translation, window enlargement for closed extended curves, the
- * 3x3 unfold, and 15 planted mistakes that the pins reject.
+ * 3x3 unfold, rational segments (exact circular arcs, the bound against
+ * sampled speeds, dense polylines, weight scaling and reparametrization),
+ * and 19 planted mistakes that the pins reject.
  * Parity unpinned: the contribution of OPEN loops on periodic domains
  * (R6/R7 windows are the definition there and nothing outside this file
  * fixes them), and the BOUNDARY decision for points whose distance to an
