@@ -207,6 +207,44 @@ wn_status wn_grid_triangles(const uint32_t *bits, int32_t nu, int32_t nv, int32_
                             int64_t *out_count, wn_stream stream);
 
 /*
+ * Several trimmed faces on one geometric surface (multi-patch B-Rep
+ * processing, Sec. 5.4.2): a point sampled on a surface is inside when it
+ * lies inside, or on the boundary of, ANY face that references the surface.
+ *
+ *   faces          host array of face pointers, grouped by surface.
+ *   surface_faces  HOST int32[n_surfaces+1]: surface s owns
+ *                  faces[surface_faces[s] .. surface_faces[s+1]) (may be empty).
+ *   point_offsets  HOST int64[n_surfaces+1]: surface s owns points
+ *                  [point_offsets[s], point_offsets[s+1]).
+ *   points         device double[2 * n], x,y interleaved, 16-byte aligned,
+ *                  in each surface's parameter domain.
+ *   out_inside     device uint8[n]: 1 inside some face of the point's
+ *                  surface (WN_INSIDE or WN_BOUNDARY there), else 0.
+ *
+ * One batched query over (surface, face) pairs (each surface's points are
+ * gathered once per face), then an OR per point; scratch comes from the
+ * stream-ordered pool (cudaMallocAsync).  Errors as wn_query_batched, and
+ * WN_ERR_LIMIT when the pairs hold more than 2^31-1 point copies.
+ */
+wn_status wn_query_surfaces(const wn_domain *const *faces, const int32_t *surface_faces,
+                            int32_t n_surfaces, const int64_t *point_offsets, const double *points,
+                            uint8_t *out_inside, int precision, wn_stream stream);
+
+/*
+ * Topological filtering of B-Rep intersection curves (Sec. 5.4.2): pieces of
+ * the raw intersection curves, already split at the face's trimming
+ * boundaries, are classified by their midpoints 0.5 (a + b).
+ *
+ *   pieces     device double[4 * n]: (ax, ay, bx, by) per piece, 32-byte aligned.
+ *   out_state  device uint8[n]: the midpoint's WN_OUTSIDE / WN_INSIDE /
+ *              WN_BOUNDARY (keep the piece when it is not WN_OUTSIDE).
+ *
+ * Errors as wn_query.
+ */
+wn_status wn_query_midpoints(const wn_domain *domain, const double *pieces, int64_t n,
+                             uint8_t *out_state, int precision, wn_stream stream);
+
+/*
  * Tuning knobs of the mixed path (0 keeps the current value for the first
  * three, a negative value keeps it for the last three):
  *   tile_queries_per_thread  1, 2 or 4 queries per sweep thread

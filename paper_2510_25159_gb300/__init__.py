@@ -58,6 +58,10 @@ def lib():
         L.wn_create_domain_rational.argtypes = [P, I32, P, P, P, D, D, D, ctypes.POINTER(ctypes.c_void_p)]
         L.wn_grid_triangles.argtypes = [P, I32, I32, I32, I32, P, I64, P, P]
         L.wn_grid_triangles.restype = ctypes.c_int
+        L.wn_query_surfaces.argtypes = [P, P, I32, P, P, P, ctypes.c_int, P]
+        L.wn_query_surfaces.restype = ctypes.c_int
+        L.wn_query_midpoints.argtypes = [P, P, I64, P, ctypes.c_int, P]
+        L.wn_query_midpoints.restype = ctypes.c_int
         L.wn_destroy_domain.argtypes = [P]
         L.wn_destroy_domain.restype = None
         L.wn_query.argtypes = [P, P, I64, P, P, ctypes.c_int, P]
@@ -224,6 +228,30 @@ def grid_triangles(bits, nu, nv, wrap_u=False, wrap_v=False, capacity=None, stre
     if n > capacity:
         raise RuntimeError(f"{n} triangles, capacity {capacity}")
     return tris[:n]
+
+
+def query_surfaces(faces_by_surface, points, point_offsets, precision=MIXED, stream=None):
+    """Inside flags (u8 device tensor) of points sampled on several surfaces,
+    each tested against every face of its surface (OR)."""
+    import torch
+    faces = [f for group in faces_by_surface for f in group]
+    sf = np.concatenate([[0], np.cumsum([len(g) for g in faces_by_surface])]).astype(np.int32)
+    off = np.ascontiguousarray(point_offsets, dtype=np.int64)
+    arr = (ctypes.c_void_p * max(len(faces), 1))(*[f.handle.value for f in faces])
+    out = torch.empty(int(off[-1]), dtype=torch.uint8, device="cuda")
+    _check(lib().wn_query_surfaces(ctypes.cast(arr, ctypes.c_void_p), _ptr(sf), len(faces_by_surface), _ptr(off),
+                                   _ptr(points), _ptr(out), int(precision), _stream(stream)))
+    return out
+
+
+def query_midpoints(domain, pieces, precision=MIXED, stream=None):
+    """States (u8 device tensor) of the midpoints of pieces ((n, 4) float64
+    device tensor: ax, ay, bx, by)."""
+    import torch
+    out = torch.empty(int(pieces.shape[0]), dtype=torch.uint8, device="cuda")
+    _check(lib().wn_query_midpoints(domain.handle, _ptr(pieces), int(pieces.shape[0]), _ptr(out), int(precision),
+                                    _stream(stream)))
+    return out
 
 
 def autotune(domains, points, offsets, iterations=3, stream=None):

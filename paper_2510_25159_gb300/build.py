@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwn.so")
-UNITS = ["wn_api.cu", "wn_domain.cu", "wn_kernels.cu", "wn_noalloc.cu", "wn_tess.cu"]
+UNITS = ["wn_api.cu", "wn_domain.cu", "wn_kernels.cu", "wn_noalloc.cu", "wn_tess.cu", "wn_multi.cu"]
 HEADERS = ["wn_dev.cuh", "wn_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",

@@ -63,6 +63,8 @@ def test_validation_codes_without_gpu(wnlib):
     assert L.wn_set_tuning(3, 0, 0, -1, -1, -1) == 1
     assert L.wn_sweep_work(None) == 1
     assert L.wn_grid_triangles(None, 4, 4, 0, 0, None, 0, None, None) == 1
+    assert L.wn_query_midpoints(None, None, 3, None, 1, None) == 1
+    assert L.wn_query_surfaces(None, None, 1, None, None, None, 1, None) == 1
     assert L.wn_query(None, None, 0, None, None, 1, None) == 1
     assert L.wn_query_grid_bitmask(None, 4, 4, None, None, 1, None) == 1
 
