@@ -389,6 +389,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
         LaunchCfg cfg{S->n_sm, g_tun, S->profiling ? &S->events : nullptr};
         if (S->counting) cfg.work = S->d_work;
         cfg.grid_tiled = grid_tiled;
+        for (int d = 0; d < n_domains; d++) cfg.rational |= domains[d]->dev.w != nullptr;
         const DomDev *d_doms = n_domains == 1 ? domains[0]->d_self : S->W.doms;
         // graph replay: only for device buffers on a non-default stream, not while profiling or counting
         const bool graph = g_tun.use_graph && !S->profiling && !S->counting && stream != nullptr && !h_pts &&

@@ -89,6 +89,7 @@ struct LaunchCfg {
     std::vector<cudaEvent_t> *events;  // non-null: record kProfEvents events per call
     unsigned long long *work = nullptr; // non-null: counting build of the tree sweep adds WK_* here
     bool grid_tiled = false;            // grid positions in 8 x 8 tiles instead of bucketing
+    bool rational = false;              // some domain of the batch has rational segments
 };
 
 // Kernels (wn_kernels.cu)

@@ -1028,6 +1028,7 @@ __device__ __noinline__ float2 near_eval_rat(float4 x0, float4 x1, float4 y0, fl
 // control points come from FP32 hi/lo pairs (control point and query, both
 // relative to the domain origin), within 2^-24 |q| + 2^-46 (|P - o| + |p - o|)
 // of P - p: the second term, below 2^-44 M, joins the evaluation bound E.
+template <bool RAT>
 __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S,
                                            int &result)
 {
@@ -1060,7 +1061,7 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
     W.n = deg;
     W.nmax = Dp->max_deg;
     W.B = __int_as_float(si.z);
-    W.rat = si.w != 0;
+    W.rat = RAT && si.w != 0;             // RAT: the batch holds rational segments
     // evaluation error bound: de Casteljau on q (2n + 4 ulps of mq); for a
     // rational segment the homogeneous sums and the division scale it by
     // the weight ratio W/w (with a factor 2 to spare)
@@ -1103,6 +1104,7 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
 
 // One node of the walk.  Returns 0 while walking, 1 when finished, 2 when the
 // query is certainly on the boundary.
+template <bool RAT>
 __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S)
 {
     const int sp = W.sp;
@@ -1155,7 +1157,7 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
     }
     const float m = 0.5f * (W.a + b);
     float mx, my;
-    if (W.rat) {
+    if (RAT && W.rat) {
         const float2 r = near_eval_rat(make_float4(W.qx[0], W.qx[1], W.qx[2], W.qx[3]),
                                        make_float4(W.qx[4], W.qx[5], W.qx[6], W.qx[7]),
                                        make_float4(W.qy[0], W.qy[1], W.qy[2], W.qy[3]),
@@ -1177,6 +1179,7 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
 
 // One thread per pair, grid-stride: consecutive queue entries come from
 // neighbouring queries of one tile, so a warp's walks stay similar.
+template <bool RAT>
 __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
 {
     unsigned long long n = A.counters[CNT_NEAR];
@@ -1187,12 +1190,12 @@ __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const Item it = A.items[i];
         int res = 0;
-        if (!near_start(A, it, W, S, res)) {
+        if (!near_start<RAT>(A, it, W, S, res)) {
             if (res == 1) atomicOr(&A.flags[it.q], QF_BOUNDARY);
             continue;
         }
         int r;
-        while ((r = near_step(A, it, W, S)) == 0) {
+        while ((r = near_step<RAT>(A, it, W, S)) == 0) {
         }
         if (r == 2) atomicOr(&A.flags[it.q], QF_BOUNDARY);
         else if (W.cnt) atomicAdd(&A.acc2[it.q], 2 * W.cnt);
@@ -1583,7 +1586,8 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     na.cap_f64 = W.cap_f64;
     na.counters = W.counters;
     mark(2);
-    k_near<<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
+    if (cfg.rational) k_near<true><<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
+    else k_near<false><<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
     mark(3);
     k_f64items<<<cfg.n_sm * 16, 128, 0, s>>>(na);
     mark(4);

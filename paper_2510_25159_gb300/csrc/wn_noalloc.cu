@@ -126,6 +126,7 @@ extern "C" wn_status wn_query_noalloc(const wn_domain *domain, const double *poi
     out.w = out_winding;
     out.st = out_inside;
     LaunchCfg cfg{n_sm, tun, nullptr};
+    cfg.rational = domain->dev.w != nullptr;
     e = launch_mixed(W, domain->d_self, 1, W.units, n_units, W.offsets, n, src, out, cfg, s);
     return e == cudaSuccess ? WN_OK : WN_ERR_CUDA;
 }
