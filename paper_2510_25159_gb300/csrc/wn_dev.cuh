@@ -140,7 +140,7 @@ struct DomDev {
 //       truncated after K terms with error at most C |w|^(K+1) / (1 - |w|),
 //       C = max_k |c_k| <= sum |gap| / r_c; the distances in [1], [4], [5]
 //       keep that below kCluTol radians.
-constexpr int kCluRecs = 16;
+constexpr int kCluRecs = 8;
 constexpr int kTreeArity = 4;
 constexpr int kTreeMaxLevels = 16;
 constexpr int kCluTerms = 32;
