@@ -372,6 +372,8 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             if (ncell > INT32_MAX) return fail(WN_ERR_LIMIT, "too many query cells");
             if ((e = grow(S->W.dcell, S->W.cap_dbin, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
             if ((e = grow(S->W.cell_cnt, S->W.cap_cells, ncell)) != cudaSuccess) return cuda_fail(e, "cells");
+            if ((e = grow(S->W.bin_chunk, S->W.cap_chunk, (ncell + 4095) / 4096)) != cudaSuccess)
+                return cuda_fail(e, "cells");
             S->W.n_cells = (int)ncell;
             if ((e = cudaMemcpy(S->W.dcell, dcell.data(), n_domains * sizeof(int4), cudaMemcpyHostToDevice)) !=
                     cudaSuccess)

@@ -55,8 +55,9 @@ struct Work {
     int *perm = nullptr;       // per query
     int *cell_cnt = nullptr;   // per cell
     int4 *dcell = nullptr;     // per domain: first cell, G
+    int *bin_chunk = nullptr;  // per 4096 cells: chunk sum, then its first position
     int n_cells = 0;
-    int64_t cap_bin_q = 0, cap_cells = 0, cap_dbin = 0;
+    int64_t cap_bin_q = 0, cap_cells = 0, cap_dbin = 0, cap_chunk = 0;
     int64_t cap_q = 0, cap_near = 0, cap_f64 = 0, cap_units = 0, cap_doms = 0, cap_off = 0;
 };
 

@@ -723,68 +723,122 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
 // the same in any order.
 struct BinArgs {
     const DomDev *doms;
-    const int64_t *offsets;     // per domain: first query
-    int n_doms;
+    const int4 *units;          // (domain, first query, count): the queries of each domain in runs
+    int n_units;
     long long n;
     PointSrc src;
     const int4 *dcell;          // per domain: first cell, G
     int *cell_of;               // per query
     int *cnt;                   // per cell: count, then cursor
+    int *chunk;                 // per chunk of kBinChunk cells: its sum, then its first position
     int *perm;
     int n_cells;
 };
 
-__device__ __forceinline__ uint32_t find_dom(const int64_t *off, int n_doms, long long q);
+constexpr int kBinChunk = 4096;     // cells per block of the chunked scan
 
+// Cell of every query, counted per cell.  One warp per unit, so the domain
+// is known without a search.
 __global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
 {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < A.n;
-         q += (long long)gridDim.x * blockDim.x) {
-        const uint32_t d = find_dom(A.offsets, A.n_doms, q);
-        const DomDev *Dp = A.doms + d;
-        const int4 dc = A.dcell[d];
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < A.n_units; u += warps) {
+        const int4 U = __ldg(&A.units[u]);
+        const DomDev *Dp = A.doms + U.x;
+        const int4 dc = __ldg(&A.dcell[U.x]);
         // G x G cells over the domain's box (the base tile on periodic axes);
         // FP32 is enough to choose a cell
         const float x0 = Dp->Pu > 0 ? 0.f : (float)Dp->ox - Dp->M;
         const float y0 = Dp->Pv > 0 ? 0.f : (float)Dp->oy - Dp->M;
         const float wx = Dp->Pu > 0 ? (float)Dp->Pu : 2.f * Dp->M;
         const float wy = Dp->Pv > 0 ? (float)Dp->Pv : 2.f * Dp->M;
-        const float4 bx = make_float4(x0, y0, __fdividef((float)dc.y, wx), __fdividef((float)dc.y, wy));
-        double x, y;
-        get_point(A.src, (uint32_t)q, x, y);
-        x = reduce_period(x, Dp->Pu);
-        y = reduce_period(y, Dp->Pv);
-        int cx = (int)floorf(((float)x - bx.x) * bx.z), cy = (int)floorf(((float)y - bx.y) * bx.w);
-        cx = min(max(cx, 0), dc.y - 1);
-        cy = min(max(cy, 0), dc.y - 1);
-        const int cell = dc.x + cy * dc.y + ((cy & 1) ? dc.y - 1 - cx : cx);
-        A.cell_of[q] = cell;
-        atomicAdd(&A.cnt[cell], 1);
+        const float sx = __fdividef((float)dc.y, wx), sy = __fdividef((float)dc.y, wy);
+        for (int ql = lane; ql < U.z; ql += 32) {
+            const uint32_t q = (uint32_t)(U.y + ql);
+            double x, y;
+            get_point(A.src, q, x, y);
+            x = reduce_period(x, Dp->Pu);
+            y = reduce_period(y, Dp->Pv);
+            int cx = (int)floorf(((float)x - x0) * sx), cy = (int)floorf(((float)y - y0) * sy);
+            cx = min(max(cx, 0), dc.y - 1);
+            cy = min(max(cy, 0), dc.y - 1);
+            const int cell = dc.x + cy * dc.y + ((cy & 1) ? dc.y - 1 - cx : cx);
+            A.cell_of[q] = cell;
+            atomicAdd(&A.cnt[cell], 1);
+        }
     }
 }
 
-// Exclusive scan of the cell counts in one CTA.
-__global__ void __launch_bounds__(1024) k_bin_scan(const BinArgs A)
+// Exclusive scan of the cell counts in three steps: chunk sums, one CTA
+// over the chunk sums, each chunk's local scan plus its offset.
+__device__ __forceinline__ int block_excl_scan_1024(int v, int *s_warp, int &total)
 {
-    __shared__ int s_sum[1024];
-    const int t = threadIdx.x;
-    const int per = (A.n_cells + 1023) / 1024;
-    const int b = t * per, e = min(b + per, A.n_cells);
-    int sum = 0;
-    for (int i = b; i < e; i++) sum += A.cnt[i];
-    s_sum[t] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int v = t >= off ? s_sum[t - off] : 0;
-        __syncthreads();
-        s_sum[t] += v;
-        __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    int run = s_sum[t] - sum;
-    for (int i = b; i < e; i++) {
-        const int c = A.cnt[i];
-        A.cnt[i] = run;
-        run += c;
+    if (lane == 31) s_warp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = s_warp[lane];
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        s_warp[lane] = xi - x;                  // exclusive warp offsets
+        if (lane == 31) s_warp[32] = xi;        // block total
+    }
+    __syncthreads();
+    const int r = s_warp[w] + incl - v;
+    total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_bin_chunk_sum(const BinArgs A)
+{
+    __shared__ int s_warp[33];
+    const int c0 = blockIdx.x * kBinChunk;
+    int v = 0;
+    for (int k = threadIdx.x; k < kBinChunk; k += 1024)
+        if (c0 + k < A.n_cells) v += A.cnt[c0 + k];
+    int total;
+    block_excl_scan_1024(v, s_warp, total);
+    if (threadIdx.x == 0) A.chunk[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_bin_chunk_scan(const BinArgs A, int n_chunks)
+{
+    __shared__ int s_warp[33];
+    int run = 0;
+    for (int base = 0; base < n_chunks; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < n_chunks ? A.chunk[i] : 0;
+        int total;
+        const int ex = block_excl_scan_1024(v, s_warp, total);
+        if (i < n_chunks) A.chunk[i] = run + ex;
+        run += total;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_bin_chunk_apply(const BinArgs A)
+{
+    __shared__ int s_warp[33];
+    const int c0 = blockIdx.x * kBinChunk;
+    int run = A.chunk[blockIdx.x];
+    for (int base = 0; base < kBinChunk; base += 1024) {
+        const int c = c0 + base + threadIdx.x;
+        const int v = c < A.n_cells ? A.cnt[c] : 0;
+        int total;
+        const int ex = block_excl_scan_1024(v, s_warp, total);
+        if (c < A.n_cells) A.cnt[c] = run + ex;
+        run += total;
     }
 }
 
@@ -1496,12 +1550,12 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
 bool mixed_buckets(const Work &W, const LaunchCfg &cfg)
 {
     return cfg.tun.tree && cfg.tun.bucket && !cfg.grid_tiled && W.perm && W.cell_of && W.cell_cnt && W.dcell &&
-           W.n_cells > 0;
+           W.bin_chunk && W.n_cells > 0;
 }
 
 int mixed_kernel_count(const Work &W, const LaunchCfg &cfg)
 {
-    return 5 + (mixed_buckets(W, cfg) ? 3 : 0);
+    return 5 + (mixed_buckets(W, cfg) ? 5 : 0);
 }
 
 cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const int4 *d_units,
@@ -1529,9 +1583,10 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     if (bucket) {
         BinArgs ba;
         ba.doms = d_doms;
-        ba.offsets = d_offsets;
-        ba.n_doms = n_doms;
+        ba.units = d_units;
+        ba.n_units = n_units;
         ba.n = n_queries;
+        ba.chunk = W.bin_chunk;
         ba.src = src;
         ba.dcell = W.dcell;
         ba.cell_of = W.cell_of;
@@ -1540,8 +1595,11 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
         ba.n_cells = W.n_cells;
         if ((e = cudaMemsetAsync(W.cell_cnt, 0, (size_t)W.n_cells * sizeof(int), s)) != cudaSuccess) return e;
         const int bin_blocks = (int)std::min<long long>((n_queries + 255) / 256, (long long)cfg.n_sm * 32);
+        const int n_chunks = (W.n_cells + kBinChunk - 1) / kBinChunk;
         k_bin_count<<<bin_blocks, 256, 0, s>>>(ba);
-        k_bin_scan<<<1, 1024, 0, s>>>(ba);
+        k_bin_chunk_sum<<<n_chunks, 1024, 0, s>>>(ba);
+        k_bin_chunk_scan<<<1, 1024, 0, s>>>(ba, n_chunks);
+        k_bin_chunk_apply<<<n_chunks, 1024, 0, s>>>(ba);
         k_bin_scatter<<<bin_blocks, 256, 0, s>>>(ba);
     }
     SweepArgs sa;
