@@ -754,7 +754,10 @@ __global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
         const float wx = Dp->Pu > 0 ? (float)Dp->Pu : 2.f * Dp->M;
         const float wy = Dp->Pv > 0 ? (float)Dp->Pv : 2.f * Dp->M;
         const float sx = __fdividef((float)dc.y, wx), sy = __fdividef((float)dc.y, wy);
-        for (int ql = lane; ql < U.z; ql += 32) {
+        for (int q0 = 0; q0 < U.z; q0 += 32) {
+            const int ql = q0 + lane;
+            const unsigned act = __ballot_sync(0xffffffffu, ql < U.z);
+            if (ql >= U.z) break;
             const uint32_t q = (uint32_t)(U.y + ql);
             double x, y;
             get_point(A.src, q, x, y);
@@ -765,7 +768,9 @@ __global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
             cy = min(max(cy, 0), dc.y - 1);
             const int cell = dc.x + cy * dc.y + ((cy & 1) ? dc.y - 1 - cx : cx);
             A.cell_of[q] = cell;
-            atomicAdd(&A.cnt[cell], 1);
+            // one atomic per distinct cell of the warp
+            const unsigned peers = __match_any_sync(act, cell);
+            if (lane == __ffs(peers) - 1) atomicAdd(&A.cnt[cell], __popc(peers));
         }
     }
 }
@@ -844,9 +849,22 @@ __global__ void __launch_bounds__(1024) k_bin_chunk_apply(const BinArgs A)
 
 __global__ void __launch_bounds__(256) k_bin_scatter(const BinArgs A)
 {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < A.n;
-         q += (long long)gridDim.x * blockDim.x)
-        A.perm[atomicAdd(&A.cnt[A.cell_of[q]], 1)] = (int)q;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); q0 < A.n; q0 += stride) {
+        const long long q = q0 + lane;
+        const unsigned act = __ballot_sync(0xffffffffu, q < A.n);
+        if (q >= A.n) break;
+        const int cell = A.cell_of[q];
+        // the warp's queries of one cell take consecutive slots from one atomic
+        const unsigned peers = __match_any_sync(act, cell);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&A.cnt[cell], __popc(peers));
+        base = __shfl_sync(act, base, leader);
+        A.perm[base + __popc(peers & lt_mask)] = (int)q;
+    }
 }
 
 template <int QPT>
