@@ -266,8 +266,9 @@ wn_status wn_set_tuning(int32_t tile_queries_per_thread, int32_t sweep_ctas_per_
  * Autotuner of the mixed path.  Times candidate launch shapes on the
  * caller's own batch and keeps the fastest for the following calls:
  * coordinate descent from the current setting over queries per sweep thread
- * {1, 2}, sweep CTAs per SM {2, 3, 4, 6}, near-pair CTAs per SM {4, 8, 16} and
- * the spatial bucket size {32, 64, 128} queries; each candidate runs one
+ * {1, 2}, sweep CTAs per SM {2, 3, 4, 6}, near-pair CTAs per SM {4, 8, 16},
+ * the spatial bucket size {32, 64, 128} queries and bucketing on / off;
+ * each candidate runs one
  * warm-up call and `iterations` timed calls (CUDA events on `stream`).
  *   domains, n_domains, point_offsets, points: as in wn_query_batched, with
  *                points in DEVICE memory (results go to library scratch).
@@ -279,10 +280,10 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains,
                       const int64_t *point_offsets, const double *points, int32_t iterations,
                       double *best_ms, wn_stream stream);
 
-/* Current tuning: out6 (host int32[6]) = queries per sweep thread, sweep
+/* Current tuning: out7 (host int32[7]) = queries per sweep thread, sweep
  * CTAs per SM, near-pair CTAs per SM, graph replay, tree sweep, bucket cell
- * size in queries. */
-wn_status wn_get_tuning(int32_t *out6);
+ * size in queries, spatial bucketing on/off. */
+wn_status wn_get_tuning(int32_t *out7);
 
 /* Counters of the last mixed call on this thread's device, read after the
  * stream is synchronised: queries, near pairs, pairs escalated to FP64,

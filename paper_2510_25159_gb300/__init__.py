@@ -266,9 +266,10 @@ def autotune(domains, points, offsets, iterations=3, stream=None):
 
 
 def get_tuning():
-    t = np.zeros(6, dtype=np.int32)
+    t = np.zeros(7, dtype=np.int32)
     _check(lib().wn_get_tuning(_ptr(t)))
-    return dict(zip(["qpt", "sweep_ctas_per_sm", "near_ctas_per_sm", "use_graph", "tree", "cell_q"], t.tolist()))
+    return dict(zip(["qpt", "sweep_ctas_per_sm", "near_ctas_per_sm", "use_graph", "tree", "cell_q", "bucket"],
+                    t.tolist()))
 
 
 def set_tuning(qpt=0, sweep_ctas_per_sm=0, near_ctas_per_sm=0, use_graph=-1, tree=-1, bucket=-1):

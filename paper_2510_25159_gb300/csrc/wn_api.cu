@@ -539,13 +539,15 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains, const 
     };
     double best_t = 0.0;
     wn_status r = trial(best, best_t);
-    const int qpts[] = {1, 2}, sweeps[] = {2, 3, 4, 6}, nears[] = {4, 8, 16}, cells[] = {32, 64, 128};
-    for (int knob = 0; knob < 4 && r == WN_OK; knob++) {
-        const int *vals = knob == 0 ? qpts : knob == 1 ? sweeps : knob == 2 ? nears : cells;
-        const int nv = knob == 0 ? 2 : knob == 1 ? 4 : 3;
+    const int qpts[] = {1, 2}, sweeps[] = {2, 3, 4, 6}, nears[] = {4, 8, 16}, cells[] = {32, 64, 128},
+              buckets[] = {1, 0};
+    for (int knob = 0; knob < 5 && r == WN_OK; knob++) {
+        const int *vals = knob == 0 ? qpts : knob == 1 ? sweeps : knob == 2 ? nears : knob == 3 ? cells : buckets;
+        const int nv = (knob == 0 || knob == 4) ? 2 : knob == 1 ? 4 : 3;
         for (int i = 0; i < nv && r == WN_OK; i++) {
             Tuning t = best;
-            int &field = knob == 0 ? t.qpt : knob == 1 ? t.sweep_ctas_per_sm : knob == 2 ? t.near_ctas_per_sm : t.cell_q;
+            int &field = knob == 0 ? t.qpt : knob == 1 ? t.sweep_ctas_per_sm : knob == 2 ? t.near_ctas_per_sm
+                       : knob == 3 ? t.cell_q : t.bucket;
             if (field == vals[i]) continue;
             field = vals[i];
             double ms = 0.0;
@@ -570,16 +572,17 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains, const 
     return r;
 }
 
-wn_status wn_get_tuning(int32_t *out6)
+wn_status wn_get_tuning(int32_t *out7)
 {
-    if (!out6) return fail(WN_ERR_ARG, "out is NULL");
+    if (!out7) return fail(WN_ERR_ARG, "out is NULL");
     std::lock_guard<std::mutex> lk(g_mu);
-    out6[0] = g_tun.qpt;
-    out6[1] = g_tun.sweep_ctas_per_sm;
-    out6[2] = g_tun.near_ctas_per_sm;
-    out6[3] = g_tun.use_graph;
-    out6[4] = g_tun.tree;
-    out6[5] = g_tun.cell_q;
+    out7[0] = g_tun.qpt;
+    out7[1] = g_tun.sweep_ctas_per_sm;
+    out7[2] = g_tun.near_ctas_per_sm;
+    out7[3] = g_tun.use_graph;
+    out7[4] = g_tun.tree;
+    out7[5] = g_tun.cell_q;
+    out7[6] = g_tun.bucket;
     return WN_OK;
 }
 
