@@ -45,12 +45,16 @@ FLOPS_PER_PAIR = 34.0
 #   telescoped node: two end signs and their bands 8
 #   expansion sum: w = r_c/(z_c - p) 12, Horner step 8 per term, Im part 3,
 #     compensated add 6
-#   record test with the near check: circle test 7 + chord crossing 10 +
-#     gap-chord crossing 10 + gap angle 17 (odd series, 6 FMA + divide)
-#   record test with crossings and gap angle: 37
+#   record test with the near check: circle test 6 + end signs and their
+#     bands 8 + the gap: next-vertex sign and band 3, hi/lo gap ends 8,
+#     choice of the shorter cross-product operand 6, cross and dot products
+#     6, gap angle by the odd series 18 (6 FMA + divide), accumulation 5
+#     = 60 (the chord crossings, taken only on a sign change, not counted)
+#   record test with crossings and gap angle: the same without the circle
+#     test, 54
 #   record test with crossings only: 20
 WORK_FLOPS = {"node_tests": 30.0, "telescoped_nodes": 8.0, "expansions": 21.0, "expansion_terms": 8.0,
-              "record_tests_near": 44.0, "record_tests_far": 37.0, "record_tests_cross": 20.0,
+              "record_tests_near": 60.0, "record_tests_far": 54.0, "record_tests_cross": 20.0,
               "exact_fp64": 0.0}
 FP32_LANES_PER_SM = 128
 
