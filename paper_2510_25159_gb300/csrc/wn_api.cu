@@ -618,9 +618,9 @@ wn_status wn_set_work_counting(int32_t on)
     return WN_OK;
 }
 
-wn_status wn_sweep_work(int64_t *out8)
+wn_status wn_sweep_work(int64_t *out9)
 {
-    if (!out8) return fail(WN_ERR_ARG, "out8 is NULL");
+    if (!out9) return fail(WN_ERR_ARG, "out9 is NULL");
     std::lock_guard<std::mutex> lk(g_mu);
     wn_status st;
     DevState *S = dev_state(st);
@@ -632,7 +632,7 @@ wn_status wn_sweep_work(int64_t *out8)
             return cuda_fail(e, "read work tallies");
         if ((e = cudaMemset(S->d_work, 0, sizeof c)) != cudaSuccess) return cuda_fail(e, "work tallies");
     }
-    for (int i = 0; i < WK_N; i++) out8[i] = (int64_t)c[i];
+    for (int i = 0; i < WK_N; i++) out9[i] = (int64_t)c[i];
     return WN_OK;
 }
 

@@ -130,15 +130,16 @@ __device__ __forceinline__ float gap_angle(float y, float x)
     return atan2_wide(y, x);
 }
 
-// One record against one query in FP32: the root step of Alg. 1 (circle
-// that contains the ellipse of Eq. 4 and the eps discs), the chord's
+// One record against one query in FP32: the root step of Alg. 1 (a circle
+// that contains the ellipse of Eq. 4 and the eps discs, then, inside it, the
+// ellipse itself; `ell` says the second test ran), the chord's
 // crossing of the +x ray from p, the gap chord's crossing and the gap angle.
 // `slow` is set when an error band cannot settle a sign; the caller then
 // redoes the record with sweep_record_exact.
 __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, const float4 R2,
                                              const float4 R3, float fx, float fy, float fxl,
                                              float fyl, float T, int &c, float &dth, bool &near,
-                                             bool &slow)
+                                             bool &slow, bool &ell)
 {
     const float uy = R0.y - fy, wy = R0.w - fy;
     const bool sa = uy > 0.f, sb = wy > 0.f;
@@ -146,14 +147,26 @@ __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, c
     const uint32_t fl = __float_as_uint(R1.w);
     const float wx = R0.z - fx;
     near = false;
+    ell = false;
     c = 0;
     dth = 0.f;
+    const float ux = R0.x - fx;
     if (!(fl & RF_CHORD)) {
         const float dcx = R1.x - fx, dcy = R1.y - fy;
         near = fmaf(dcx, dcx, dcy * dcy) <= R1.z;
+        if (near) {
+            // inside the circle: the ellipse of Eq. 5 with the circle's
+            // inflated focal sum 2R, |p - a| + |p - b| > 2R.  4T covers the
+            // FP32 coordinate errors and R's two 2^-20 inflations the
+            // relative rounding of the distances, their sum and the square,
+            // so "far" here implies far in Alg. 1's own test.
+            const float da = sqrtf(fmaf(ux, ux, uy * uy)), db = sqrtf(fmaf(wx, wx, wy * wy));
+            const float s = (da + db) - 4.f * T;
+            near = !((s > 0.f) & (s * s > 4.f * R1.z));
+            ell = true;
+        }
     }
     if (!near && sa != sb) {
-        const float ux = R0.x - fx;
         const float D = fmaf(ux, wy, -uy * wx);
         const float TD = T * (fabsf(ux) + fabsf(uy) + fabsf(wx) + fabsf(wy)) +
                          kTwoM22 * (fabsf(ux * wy) + fabsf(uy * wx));
@@ -608,8 +621,9 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                     const uint32_t ck = (cf >> (2 * k)) & 3u;
                                     int cc;
                                     float dth;
-                                    bool slow;
-                                    sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, nr[k], slow);
+                                    bool slow, ell;
+                                    sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, nr[k], slow,
+                                                 ell);
                                     if (slow && ck) {
                                         const double2 p = s_p[k][tid];
                                         sweep_record_exact(r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
@@ -617,6 +631,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs
                                         if constexpr (CNT) wk[WK_EXACT]++;
                                     }
                                     if constexpr (CNT) {
+                                        if (ck == 1u && ell) wk[WK_ELLIPSE]++;
                                         if (ck == 1u) wk[WK_REC_NEAR]++;
                                         else if (ck == 2u) wk[WK_REC_CROSS]++;
                                     }
@@ -954,8 +969,8 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
                     for (int k = 0; k < QPT; k++) {
                         int c;
                         float dth;
-                        bool slow;
-                        sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], c, dth, nr[k], slow);
+                        bool slow, ell;
+                        sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], c, dth, nr[k], slow, ell);
                         if (slow && inc[k]) {
                             const double2 p = s_p[k][tid];
                             sweep_record_exact(r0 + r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),

@@ -254,6 +254,7 @@ def test_work_counting_build(wn):
     assert work["telescoped_nodes"] + work["expansions"] <= 2 * work["node_tests"]
     assert 4 * work["expansions"] <= work["expansion_terms"] <= 32 * work["expansions"]
     assert work["record_tests_near"] > 0 and work["telescoped_nodes"] > 0
+    assert 0 < work["ellipse_tests"] <= work["record_tests_near"]
     assert wn.sweep_work()["node_tests"] == 0      # read clears
 
 
