@@ -62,7 +62,7 @@ struct Work {
 };
 
 enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_ERR = 4, CNT_OVF = 5,
-       CNT_NEAR_TAKEN = 6, CNT_N = 8 };
+       CNT_NEAR_CURSOR = 7, CNT_N = 8 };
 
 // Work tallies of the counting build of the tree sweep (per query slot):
 // node tests, nodes whose crossings telescoped, expansion evaluations and

@@ -338,7 +338,7 @@ __device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, cons
 // warp into A.work when the warp runs out of units; its decisions and
 // arithmetic are those of the plain build.
 template <int QPT, bool CNT>
-__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_tree(const SweepArgs A)
+__global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs A)
 {
     constexpr int SB = 2 * QPT;                     // status bits per level
     constexpr uint64_t SMASK = (1ull << SB) - 1ull;
@@ -1264,28 +1264,69 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
     return 0;
 }
 
-// One thread per pair, grid-stride: consecutive queue entries come from
-// neighbouring queries of one tile, so a warp's walks stay similar.
+// Persistent lanes: walks differ a lot in length (a few nodes for most
+// pairs, 30 or more for a query next to the curve), so a lane that finishes
+// its walk takes a new pair instead of waiting for the warp's longest walk.
+// Starting a pair costs three dependent global loads (pair, segment, control
+// points), so idle lanes are refilled together, once at least kNearRefill of
+// them wait, and one load latency serves them all; every iteration then
+// advances each busy lane by one node.  A warp draws kNearChunk pairs at a
+// time from the queue (one atomic per chunk); consecutive pairs come from
+// neighbouring queries of one tile, so the lanes' walks stay close in memory.
+constexpr int kNearChunk = 128;
+constexpr int kNearRefill = 16;
+
 template <bool RAT>
 __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
 {
     unsigned long long n = A.counters[CNT_NEAR];
     if (n > (unsigned long long)A.cap_near) n = (unsigned long long)A.cap_near;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
     NearWalk W;
     NearStack S;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const Item it = A.items[i];
-        int res = 0;
-        if (!near_start<RAT>(A, it, W, S, res)) {
-            if (res == 1) atomicOr(&A.flags[it.q], QF_BOUNDARY);
+    Item it;
+    bool busy = false, dry = false;                   // dry: the queue is used up (warp-uniform)
+    unsigned long long pool = 0, pool_end = 0;        // the warp's drawn range (warp-uniform)
+    for (;;) {
+        const unsigned idle = __ballot_sync(0xffffffffu, !busy);
+        if (__popc(idle) >= kNearRefill && !dry) {
+            if (pool >= pool_end) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(&A.counters[CNT_NEAR_CURSOR], (unsigned long long)kNearChunk);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (b >= n) {
+                    dry = true;
+                } else {
+                    pool = b;
+                    pool_end = min(b + (unsigned long long)kNearChunk, n);
+                }
+            }
+            if (!dry) {
+                if (!busy) {
+                    const unsigned long long i = pool + __popc(idle & lt_mask);
+                    if (i < pool_end) {
+                        it = A.items[i];
+                        int res = 0;
+                        busy = near_start<RAT>(A, it, W, S, res);
+                        if (!busy && res == 1) atomicOr(&A.flags[it.q], QF_BOUNDARY);
+                    }
+                }
+                pool = min(pool + (unsigned long long)__popc(idle), pool_end);
+            }
+        }
+        if (!__any_sync(0xffffffffu, busy)) {
+            if (dry) break;
             continue;
         }
-        int r;
-        while ((r = near_step<RAT>(A, it, W, S)) == 0) {
+        if (busy) {
+            const int r = near_step<RAT>(A, it, W, S);
+            if (r != 0) {
+                if (r == 2) atomicOr(&A.flags[it.q], QF_BOUNDARY);
+                else if (W.cnt) atomicAdd(&A.acc2[it.q], 2 * W.cnt);
+                busy = false;
+            }
         }
-        if (r == 2) atomicOr(&A.flags[it.q], QF_BOUNDARY);
-        else if (W.cnt) atomicAdd(&A.acc2[it.q], 2 * W.cnt);
     }
 }
 
