@@ -476,13 +476,124 @@ __device__ bool alg1_fp64(const double *P, const double *Wt, int n, int nmax, do
     return false;
 }
 
+// Algorithm 1 in FP64 on the sub-interval [a0, b0] of a polynomial segment
+// of degree n <= NM, adding the signed crossings of the +x ray from (px, py)
+// by its chords; the end points take the given signs (those of the FP32
+// chain around it).  Returns true when the query is on the boundary.
+//
+// FP64 is the slow unit here, so every node is cheap in FP64 operations:
+//   gamma(t) - p by Horner's rule in the power basis of the query-relative
+//     control points q_i = P_i - p: gamma(t) - p = sum_k C(n,k) D^k q_0 t^k,
+//     D^k the k-th forward difference (2n FMAs per point);
+//   the eps test on squared distances, |q|^2 < eps^2;
+//   the far test of Eq. 5, ra + rb > L with L = B (b - a), without square
+//     roots: with S = L^2 - ra^2 - rb^2 it holds iff S < 0 or
+//     4 ra^2 rb^2 > S^2 (both sides of ra + rb > L are non-negative).
+// Each decision is the exact one up to FP64 rounding of its operands.
+template <int NM>
+__device__ __noinline__ bool alg1_fp64_sub_pow(const double *P, int n, double B, double px, double py,
+                                                  double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
+{
+    double cx[NM + 1], cy[NM + 1];
+#pragma unroll
+    for (int i = 0; i <= NM; i++) {
+        cx[i] = i <= n ? P[2 * i] - px : 0.0;
+        cy[i] = i <= n ? P[2 * i + 1] - py : 0.0;
+    }
+#pragma unroll
+    for (int k = 1; k <= NM; k++) {
+#pragma unroll
+        for (int i = NM; i >= k; i--) {
+            if (i <= n) {
+                cx[i] -= cx[i - 1];
+                cy[i] -= cy[i - 1];
+            }
+        }
+    }
+    double bin = 1.0;
+#pragma unroll
+    for (int k = 1; k <= NM; k++) {
+        if (k <= n) {
+            bin = bin * (double)(n - k + 1) / (double)k;     // C(n, k), exact
+            cx[k] *= bin;
+            cy[k] *= bin;
+        }
+    }
+    auto eval = [&](double t, double &x, double &y) {
+        x = cx[NM];
+        y = cy[NM];
+#pragma unroll
+        for (int k = NM - 1; k >= 0; k--) {
+            x = fma(x, t, cx[k]);
+            y = fma(y, t, cy[k]);
+        }
+    };
+    const double eps2 = eps * eps;
+    double st_t[kDepthCap64 + 2], st_x[kDepthCap64 + 2], st_y[kDepthCap64 + 2];
+    int st_d[kDepthCap64 + 2];
+    double ax, ay, bx, by;
+    if (a0 == 0.0) { ax = P[0] - px; ay = P[1] - py; }
+    else eval(a0, ax, ay);
+    if (b0 == 1.0) { bx = P[2 * n] - px; by = P[2 * n + 1] - py; }
+    else eval(b0, bx, by);
+    double a = a0;
+    bool sa = sa0;
+    double qa = ax * ax + ay * ay;
+    int d0 = 0;
+    for (double w = b0 - a0; w < 1.0 && d0 < kDepthCap64; w *= 2.0) d0++;
+    st_t[0] = b0; st_x[0] = bx; st_y[0] = by; st_d[0] = d0;
+    int sp = 1;
+    cnt = 0;
+    while (sp > 0) {
+        const double b = st_t[sp - 1];
+        bx = st_x[sp - 1];
+        by = st_y[sp - 1];
+        const int d = st_d[sp - 1];
+        const double qb = bx * bx + by * by;
+        if (qa < eps2 || qb < eps2) return true;
+        const bool sb = (b == b0) ? sb0 : (by > 0.0);
+        const double L = B * (b - a);
+        const double S = L * L - (qa + qb);
+        if (S < 0.0 || 4.0 * qa * qb > S * S) {
+            if (sa != sb) {
+                const double D = ax * by - ay * bx;
+                if (!sa && sb && D > 0) cnt++;
+                else if (sa && !sb && D < 0) cnt--;
+            }
+            a = b; ax = bx; ay = by; qa = qb; sa = sb;
+            sp--;
+            continue;
+        }
+        if (d >= kDepthCap64) return true;
+        const double m = 0.5 * (a + b);
+        double mx, my;
+        eval(m, mx, my);
+        st_d[sp - 1] = d + 1;
+        st_t[sp] = m; st_x[sp] = mx; st_y[sp] = my; st_d[sp] = d + 1;
+        sp++;
+    }
+    return false;
+}
+
 // Algorithm 1 in FP64 on the sub-interval [a0, b0] of one segment, adding
 // the signed crossings of the +x ray from (px, py) by its chords; the end
 // points take the given signs (those of the FP32 chain around it).
-// Returns true when the query is on the boundary.
+// Returns true when the query is on the boundary.  Polynomial segments take
+// alg1_fp64_sub_pow; a rational one evaluates its homogeneous points.
 __device__ inline bool alg1_fp64_sub(const double *P, const double *Wt, int n, int nmax, double B, double px,
                                      double py, double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
 {
+    if (!Wt) {
+        switch (nmax) {
+        case 1: return alg1_fp64_sub_pow<1>(P, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+        case 2: return alg1_fp64_sub_pow<2>(P, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+        case 3: return alg1_fp64_sub_pow<3>(P, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+        case 4: return alg1_fp64_sub_pow<4>(P, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+        case 5: return alg1_fp64_sub_pow<5>(P, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+        case 6: return alg1_fp64_sub_pow<6>(P, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+        default: return alg1_fp64_sub_pow<kMaxDeg>(P, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+        }
+    }
     SegF64 sg;
     sg.load(P, Wt, n, nmax);
     double st_t[kDepthCap64 + 2], st_x[kDepthCap64 + 2], st_y[kDepthCap64 + 2];
