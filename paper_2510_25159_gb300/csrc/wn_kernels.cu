@@ -25,7 +25,11 @@
 // with atan2 (Eq. 3) -- the paper's method ported as is.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "wn_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace wn {
 
@@ -1501,18 +1505,26 @@ struct EscArgs {
     OutDst out;
 };
 
-// Plain FP64 recomputation of the escalated queries: one CTA per query, its
-// threads share the segments of every instance the query sees and reduce the
-// chord-angle sums (same arithmetic as k_plain, summed in another order).
+// Plain FP64 recomputation of the escalated queries (same arithmetic as
+// k_plain, summed in another order).  FP64 is the slow unit, so each query is
+// spread over one cluster of kEscCluster CTAs, i.e. as many SMs: every CTA's
+// threads share a slice of the segments of each instance the query sees and
+// reduce their chord-angle sums in shared memory; the cluster's first CTA
+// then adds the CTAs' partial sums from their shared memory and writes the
+// result.
 constexpr int kEscThreads = 128;
+constexpr int kEscCluster = 8;              // CTAs (one per SM) per escalated query
 
-__global__ void __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
+__global__ void __cluster_dims__(kEscCluster, 1, 1) __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
 {
     __shared__ double s_ang[kEscThreads];
     __shared__ int s_bnd[kEscThreads];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x;
     const unsigned long long n = A.counters[CNT_ESC];
-    for (unsigned long long i = blockIdx.x; i < n; i += gridDim.x) {
+    const unsigned long long n_cl = gridDim.x / kEscCluster;
+    for (unsigned long long i = blockIdx.x / kEscCluster; i < n; i += n_cl) {
         const uint2 e = A.esc[i];
         const DomDev *Dp = A.doms + e.y;
         double x0, y0;
@@ -1526,7 +1538,7 @@ __global__ void __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
             const LoopDev &L = Dp->loops[in.loop];
             if (!inst_sees(*Dp, in, L, x, y)) continue;
             if (in.type == IT_LINE) {
-                if (tid == 0) {
+                if (tid == 0 && rank == 0) {
                     const int sd = line_side(*Dp, in, L, x, y);
                     bnd |= sd == 0;
                     half += sd;
@@ -1535,11 +1547,11 @@ __global__ void __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
             }
             const double qx = xsub(x, in.Tx), qy = xsub(y, in.Ty);
             const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
-            for (int sg = sb + tid; sg < se && !bnd; sg += kEscThreads)
+            for (int sg = sb + rank * kEscThreads + tid; sg < se && !bnd; sg += kEscCluster * kEscThreads)
                 bnd |= alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[sg]), seg_weights(*Dp, sg),
                                  __ldg(&Dp->seg_deg[sg]), Dp->max_deg,
                                  __ldg(&Dp->seg_B[sg]), qx, qy, Dp->eps, fa);
-            if (in.type == IT_PE && tid == 0) {
+            if (in.type == IT_PE && tid == 0 && rank == 0) {
                 const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
                 fa.ang -= atan2(ax * by - ay * bx, ax * bx + ay * by);
             }
@@ -1554,19 +1566,26 @@ __global__ void __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
             }
             __syncthreads();
         }
-        if (tid == 0) {
+        cl.sync();
+        if (rank == 0 && tid == 0) {
+            double ang = 0.0;
+            int bd = 0;
+            for (int r = 0; r < kEscCluster; r++) {
+                ang += *cl.map_shared_rank(&s_ang[0], r);
+                bd |= *cl.map_shared_rank(&s_bnd[0], r);
+            }
             double om;
             int st;
-            if (s_bnd[0]) {
+            if (bd) {
                 om = __longlong_as_double(0x7ff8000000000000ULL);
                 st = 2;
             } else {
-                om = s_ang[0] / kTwoPi + 0.5 * (double)half;
+                om = ang / kTwoPi + 0.5 * (double)half;
                 st = om >= 0.5 ? 1 : 0;
             }
             write_out(A.out, e.x, om, st, true);
         }
-        __syncthreads();
+        cl.sync();      // the partial sums stay until the first CTA has read them
     }
 }
 
@@ -1742,7 +1761,7 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     ea.esc = W.esc_q;
     ea.counters = W.counters;
     ea.out = out;
-    k_f64query<<<cfg.n_sm * 2, kEscThreads, 0, s>>>(ea);
+    k_f64query<<<std::max(1, cfg.n_sm * 2 / kEscCluster) * kEscCluster, kEscThreads, 0, s>>>(ea);
     mark(6);
     return cudaGetLastError();
 }
