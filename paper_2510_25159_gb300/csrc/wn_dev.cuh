@@ -213,6 +213,7 @@ __host__ __device__ __forceinline__ double xdiv(double a, double b)
 __host__ __device__ __forceinline__ double reduce_period(double x, double P)
 {
     if (!(P > 0)) return x;
+    if (x >= 0.0 && x < P) return x;        // already in the base tile: fmod(x, P) == x
     double r = fmod(x, P);
     if (r < 0) r = xadd(r, P);
     if (r >= P) r = 0.0;
@@ -575,11 +576,109 @@ __device__ __noinline__ bool alg1_fp64_sub_pow(const double *P, int n, double B,
     return false;
 }
 
+// The same walk for a rational segment (weights w_i > 0): gamma(t) - p =
+// Q(t) / W(t) with the homogeneous query-relative control points
+// w_i (P_i - p) and weights w_i, each of Q_x, Q_y, W by Horner's rule in its
+// power basis.  Since W > 0, signs and cross products take Q alone, and the
+// eps and far tests are those of the polynomial walk multiplied through by
+// the squared weights (|Q|^2 = |gamma - p|^2 W^2), so no node divides.
+template <int NM>
+__device__ __noinline__ bool alg1_fp64_sub_rpow(const double *P, const double *Wt, int n, double B, double px,
+                                                double py, double eps, double a0, double b0, bool sa0, bool sb0,
+                                                int &cnt)
+{
+    double cx[NM + 1], cy[NM + 1], cw[NM + 1];
+#pragma unroll
+    for (int i = 0; i <= NM; i++) {
+        const double w = i <= n ? Wt[i] : 0.0;
+        cx[i] = i <= n ? w * (P[2 * i] - px) : 0.0;
+        cy[i] = i <= n ? w * (P[2 * i + 1] - py) : 0.0;
+        cw[i] = w;
+    }
+#pragma unroll
+    for (int k = 1; k <= NM; k++) {
+#pragma unroll
+        for (int i = NM; i >= k; i--) {
+            if (i <= n) {
+                cx[i] -= cx[i - 1];
+                cy[i] -= cy[i - 1];
+                cw[i] -= cw[i - 1];
+            }
+        }
+    }
+    double bin = 1.0;
+#pragma unroll
+    for (int k = 1; k <= NM; k++) {
+        if (k <= n) {
+            bin = bin * (double)(n - k + 1) / (double)k;
+            cx[k] *= bin;
+            cy[k] *= bin;
+            cw[k] *= bin;
+        }
+    }
+    auto eval = [&](double t, double &x, double &y, double &w) {
+        x = cx[NM];
+        y = cy[NM];
+        w = cw[NM];
+#pragma unroll
+        for (int k = NM - 1; k >= 0; k--) {
+            x = fma(x, t, cx[k]);
+            y = fma(y, t, cy[k]);
+            w = fma(w, t, cw[k]);
+        }
+    };
+    const double eps2 = eps * eps;
+    double st_t[kDepthCap64 + 2], st_x[kDepthCap64 + 2], st_y[kDepthCap64 + 2], st_w[kDepthCap64 + 2];
+    int st_d[kDepthCap64 + 2];
+    double ax, ay, aw, bx, by, bw;
+    if (a0 == 0.0) { aw = Wt[0]; ax = aw * (P[0] - px); ay = aw * (P[1] - py); }
+    else eval(a0, ax, ay, aw);
+    if (b0 == 1.0) { bw = Wt[n]; bx = bw * (P[2 * n] - px); by = bw * (P[2 * n + 1] - py); }
+    else eval(b0, bx, by, bw);
+    double a = a0;
+    bool sa = sa0;
+    double na = ax * ax + ay * ay, wa2 = aw * aw;
+    int d0 = 0;
+    for (double w = b0 - a0; w < 1.0 && d0 < kDepthCap64; w *= 2.0) d0++;
+    st_t[0] = b0; st_x[0] = bx; st_y[0] = by; st_w[0] = bw; st_d[0] = d0;
+    int sp = 1;
+    cnt = 0;
+    while (sp > 0) {
+        const double b = st_t[sp - 1];
+        bx = st_x[sp - 1];
+        by = st_y[sp - 1];
+        bw = st_w[sp - 1];
+        const int d = st_d[sp - 1];
+        const double nb = bx * bx + by * by, wb2 = bw * bw;
+        if (na < eps2 * wa2 || nb < eps2 * wb2) return true;
+        const bool sb = (b == b0) ? sb0 : (by > 0.0);
+        const double L = B * (b - a);
+        const double S = L * L * wa2 * wb2 - (na * wb2 + nb * wa2);
+        if (S < 0.0 || 4.0 * na * nb * wa2 * wb2 > S * S) {
+            if (sa != sb) {
+                const double D = ax * by - ay * bx;
+                if (!sa && sb && D > 0) cnt++;
+                else if (sa && !sb && D < 0) cnt--;
+            }
+            a = b; ax = bx; ay = by; na = nb; wa2 = wb2; sa = sb;
+            sp--;
+            continue;
+        }
+        if (d >= kDepthCap64) return true;
+        const double m = 0.5 * (a + b);
+        double mx, my, mw;
+        eval(m, mx, my, mw);
+        st_d[sp - 1] = d + 1;
+        st_t[sp] = m; st_x[sp] = mx; st_y[sp] = my; st_w[sp] = mw; st_d[sp] = d + 1;
+        sp++;
+    }
+    return false;
+}
+
 // Algorithm 1 in FP64 on the sub-interval [a0, b0] of one segment, adding
 // the signed crossings of the +x ray from (px, py) by its chords; the end
 // points take the given signs (those of the FP32 chain around it).
-// Returns true when the query is on the boundary.  Polynomial segments take
-// alg1_fp64_sub_pow; a rational one evaluates its homogeneous points.
+// Returns true when the query is on the boundary.
 __device__ inline bool alg1_fp64_sub(const double *P, const double *Wt, int n, int nmax, double B, double px,
                                      double py, double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
 {
@@ -594,48 +693,15 @@ __device__ inline bool alg1_fp64_sub(const double *P, const double *Wt, int n, i
         default: return alg1_fp64_sub_pow<kMaxDeg>(P, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
         }
     }
-    SegF64 sg;
-    sg.load(P, Wt, n, nmax);
-    double st_t[kDepthCap64 + 2], st_x[kDepthCap64 + 2], st_y[kDepthCap64 + 2];
-    int st_d[kDepthCap64 + 2];
-    double gx, gy;
-    if (a0 == 0.0) { gx = P[0]; gy = P[1]; }
-    else sg.eval(a0, gx, gy);
-    double a = a0, ax = gx - px, ay = gy - py;
-    bool sa = sa0;
-    double ra = sqrt(ax * ax + ay * ay);
-    if (b0 == 1.0) { gx = P[2 * n]; gy = P[2 * n + 1]; }
-    else sg.eval(b0, gx, gy);
-    int d0 = 0;
-    for (double w = b0 - a0; w < 1.0 && d0 < kDepthCap64; w *= 2.0) d0++;
-    st_t[0] = b0; st_x[0] = gx - px; st_y[0] = gy - py; st_d[0] = d0;
-    int sp = 1;
-    cnt = 0;
-    while (sp > 0) {
-        const double b = st_t[sp - 1], bx = st_x[sp - 1], by = st_y[sp - 1];
-        const int d = st_d[sp - 1];
-        const double rb = sqrt(bx * bx + by * by);
-        if (ra < eps || rb < eps) return true;
-        const bool sb = (b == b0) ? sb0 : (by > 0.0);
-        if (ra + rb > B * (b - a)) {
-            if (sa != sb) {
-                const double D = ax * by - ay * bx;
-                if (!sa && sb && D > 0) cnt++;
-                else if (sa && !sb && D < 0) cnt--;
-            }
-            a = b; ax = bx; ay = by; ra = rb; sa = sb;
-            sp--;
-            continue;
-        }
-        if (d >= kDepthCap64) return true;
-        const double m = 0.5 * (a + b);
-        double mx, my;
-        sg.eval(m, mx, my);
-        st_d[sp - 1] = d + 1;
-        st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;
-        sp++;
+    switch (nmax) {
+    case 1: return alg1_fp64_sub_rpow<1>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+    case 2: return alg1_fp64_sub_rpow<2>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+    case 3: return alg1_fp64_sub_rpow<3>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+    case 4: return alg1_fp64_sub_rpow<4>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+    case 5: return alg1_fp64_sub_rpow<5>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+    case 6: return alg1_fp64_sub_rpow<6>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+    default: return alg1_fp64_sub_rpow<kMaxDeg>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
     }
-    return false;
 }
 
 }  // namespace wn

@@ -38,8 +38,8 @@ constexpr float kTwoM24 = 5.9604644775390625e-8f;  // 2^-24
 constexpr float kTwoM44 = 5.684341886080802e-14f;  // 2^-44
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr float kOmegaBandF = 1e-4f;               // classification band of the mixed path
-constexpr double kInv2Pi = 0.15915494309189533576888376337251;
 constexpr float kInv2PiF = 0.15915494309189533577f;
+constexpr float kInv2PiLoF = 6.4206382432985265e-09f;   // 1/(2 pi) - kInv2PiF
 constexpr int kSweepThreads = 256;
 constexpr int kChunk = 64;                          // records per shared-memory stage
 
@@ -54,6 +54,41 @@ __device__ __forceinline__ void get_point(const PointSrc &s, uint32_t q, double 
         x = ((double)i + 0.5) / (double)s.nu * s.su;
         y = ((double)j + 0.5) / (double)s.nv * s.sv;
     }
+}
+
+// FP64 instructions, conversions included, run on GB300's narrow FP64 unit;
+// the two conversions below use integer instructions only.
+//
+// The double whose value is the float f (exact): the exponent re-biased and
+// the fraction widened; zeros, infinities and NaNs keep their kind, a
+// subnormal float becomes a normal double.
+__device__ __forceinline__ double f32_to_f64_exact(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+    const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    if (e == 0xffu) return __longlong_as_double(s | 0x7ff0000000000000ULL | ((unsigned long long)m << 29));
+    if (e == 0u) {
+        if (m == 0u) return __longlong_as_double(s);
+        const int p = 31 - __clz(m);                           // m = 2^p (1 + r), value m 2^-149
+        const uint32_t r = (m << (23 - p)) & 0x7fffffu;
+        return __longlong_as_double(s | ((unsigned long long)(p + 874) << 52) | ((unsigned long long)r << 29));
+    }
+    return __longlong_as_double(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29));
+}
+
+// The double x truncated to FP32 (toward zero), for choices that need no
+// exactness: magnitudes below FP32's normal range give 0, above it (and
+// infinities and NaNs) an infinity of x's sign.
+__device__ __forceinline__ float f64_to_f32_trunc(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
 __device__ __forceinline__ double exact_cross(double2 a, double2 b, double px, double py)
@@ -773,6 +808,10 @@ __global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
         const float wx = Dp->Pu > 0 ? (float)Dp->Pu : 2.f * Dp->M;
         const float wy = Dp->Pv > 0 ? (float)Dp->Pv : 2.f * Dp->M;
         const float sx = __fdividef((float)dc.y, wx), sy = __fdividef((float)dc.y, wy);
+        // periodic axes: the coordinate's tile offset removed in FP32 (a cell
+        // choice needs no exactness)
+        const bool pu = Dp->Pu > 0, pv = Dp->Pv > 0;
+        const float ipu = pu ? __fdividef(1.f, wx) : 0.f, ipv = pv ? __fdividef(1.f, wy) : 0.f;
         for (int q0 = 0; q0 < U.z; q0 += 32) {
             const int ql = q0 + lane;
             const unsigned act = __ballot_sync(0xffffffffu, ql < U.z);
@@ -780,9 +819,10 @@ __global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
             const uint32_t q = (uint32_t)(U.y + ql);
             double x, y;
             get_point(A.src, q, x, y);
-            x = reduce_period(x, Dp->Pu);
-            y = reduce_period(y, Dp->Pv);
-            int cx = (int)floorf(((float)x - x0) * sx), cy = (int)floorf(((float)y - y0) * sy);
+            float xf = f64_to_f32_trunc(x), yf = f64_to_f32_trunc(y);
+            if (pu) xf -= floorf(xf * ipu) * wx;
+            if (pv) yf -= floorf(yf * ipv) * wy;
+            int cx = (int)floorf((xf - x0) * sx), cy = (int)floorf((yf - y0) * sy);
             cx = min(max(cx, 0), dc.y - 1);
             cy = min(max(cy, 0), dc.y - 1);
             const int cell = dc.x + cy * dc.y + ((cy & 1) ? dc.y - 1 - cx : cx);
@@ -1274,9 +1314,11 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
 // Starting a pair costs three dependent global loads (pair, segment, control
 // points), so idle lanes are refilled together, once at least kNearRefill of
 // them wait, and one load latency serves them all; every iteration then
-// advances each busy lane by one node.  A warp draws kNearChunk pairs at a
-// time from the queue (one atomic per chunk); consecutive pairs come from
-// neighbouring queries of one tile, so the lanes' walks stay close in memory.
+// advances each busy lane by one node.  A warp draws up to kNearChunk pairs
+// at a time from the queue (one atomic per draw), fewer when the queue is
+// short, so that every warp of the grid gets pairs; consecutive pairs come
+// from neighbouring queries of one tile, so the lanes' walks stay close in
+// memory.
 constexpr int kNearChunk = 128;
 constexpr int kNearRefill = 16;
 
@@ -1287,6 +1329,10 @@ __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
     if (n > (unsigned long long)A.cap_near) n = (unsigned long long)A.cap_near;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    // pairs per draw: the queue spread over the grid's warps, 32 to kNearChunk
+    const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long chunk =
+        min((unsigned long long)kNearChunk, max(32ULL, (n / n_warps) & ~31ULL));
     NearWalk W;
     NearStack S;
     Item it;
@@ -1297,13 +1343,13 @@ __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
         if (__popc(idle) >= kNearRefill && !dry) {
             if (pool >= pool_end) {
                 unsigned long long b = 0;
-                if (lane == 0) b = atomicAdd(&A.counters[CNT_NEAR_CURSOR], (unsigned long long)kNearChunk);
+                if (lane == 0) b = atomicAdd(&A.counters[CNT_NEAR_CURSOR], chunk);
                 b = __shfl_sync(0xffffffffu, b, 0);
                 if (b >= n) {
                     dry = true;
                 } else {
                     pool = b;
-                    pool_end = min(b + (unsigned long long)kNearChunk, n);
+                    pool_end = min(b + chunk, n);
                 }
             }
             if (!dry) {
@@ -1477,7 +1523,19 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs A)
                 const float band = kOmegaBandF + 1e-6f * (fabsf(0.5f * (float)a2) + fabsf(th) * kInv2PiF);
                 if (fabsf(om32 - 0.5f) < band) esc = true;
                 st = om32 >= 0.5f ? 1 : 0;
-                if (A.out.w) om = 0.5 * (double)a2 - (double)th * kInv2Pi;
+                // omega = a2/2 - theta/(2 pi) as an FP32 pair hi + lo (exact
+                // product residual, TwoSum, 1/(2 pi) split in two floats), so
+                // its FP64 value costs one FP64 addition
+                if (A.out.w) {
+                    const float h = 0.5f * (float)a2;
+                    const float p = th * kInv2PiF;
+                    const float pe = fmaf(th, kInv2PiF, -p);
+                    const float s = h - p;
+                    const float bb = s - h;
+                    const float e = (h - (s - bb)) + (-p - bb);
+                    const float lo = (e - pe) - th * kInv2PiLoF;
+                    om = f32_to_f64_exact(s) + f32_to_f64_exact(lo);
+                }
             }
             if (esc) {
                 const unsigned long long idx = atomicAdd(&A.counters[CNT_ESC], 1ULL);
