@@ -86,9 +86,10 @@ def workload(k, scale=1.0, shard=0):
                       "1e-4..1e-2 gap, control-point noise 1e-4; 10M uniform + 1M near-curve (1e-7..1e-3) queries"
                       + tag)
     if k == 3:
-        d, q = ws.config3(seed_index=3 + off)
+        d, q = ws.config3(seed_index=3 + off, n_queries=int(20_000_000 * scale))
         return d, q, ("256 bi-periodic faces (2pi x 2pi), 2-8 loops of 16-256 cubics, 30% non-contractible pairs, "
-                      "10% open; 20M uniform queries" + tag)
+                      "10% open; 20M uniform queries" + (f" at {scale:g} of its queries" if scale != 1.0 else "")
+                      + tag)
     if k == 4:
         d, q = ws.config4(seed_index=4 + off)
         return d, q, ("10k faces, log-normal segments (median 40) and queries (median 4096, ~2e8 total), "

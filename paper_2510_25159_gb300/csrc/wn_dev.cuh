@@ -78,6 +78,18 @@ struct InstCull {
     float pad0, pad1;
 };
 
+// The FP32 side of one instance, so that the sweep decides most (query,
+// instance) pairs without FP64 instructions (GB300's FP64 unit is narrow):
+// its lattice shift as hi/lo pairs, the exact window shrunk well beyond the
+// rounding of its test and rounded inward (a query inside it is seen), and
+// for a line term the base point and direction of its line.
+struct InstF32 {
+    float txh, txl, tyh, tyl;   // (Tx, Ty) = (txh + txl, tyh + tyl) to ~2^-48
+    float x0, x1, y0, y1;       // inner box
+    float n0, n1, v0, v1;       // inner n.p and v.p ranges
+    float lx, ly, lvx, lvy;     // line term: (Fx + g0x, Fy + g0y) (F on periodic axes), v
+};
+
 // Everything a kernel needs about one domain (copied per batch entry).
 struct DomDev {
     int kind, n_loops, n_segs, n_inst, n_rec, n_pairs;
@@ -96,6 +108,7 @@ struct DomDev {
     const LoopDev *loops;       // [n_loops]
     const InstDev *inst;        // [n_inst]
     const InstCull *cull;       // [n_inst]
+    const InstF32 *instf;       // [n_inst]
     const PairDev *pairs;       // [n_pairs]
     const float4 *rec;          // [4 * n_rec]: (a, b), (centre, R^2, flags), (gap, next), (b low)
     const int *rec_seg;         // [n_rec] segment, -1 for a closing chord
@@ -271,6 +284,41 @@ __device__ __forceinline__ bool cull_sees(const InstCull &c, float nx, float ny,
     const float v_lo = fmaf(c.vx, c.vx >= 0.f ? bx0 : bx1, c.vy * (c.vy >= 0.f ? by0 : by1));
     const float v_hi = fmaf(c.vx, c.vx >= 0.f ? bx1 : bx0, c.vy * (c.vy >= 0.f ? by1 : by0));
     return !(v_hi + sv < c.v0 || v_lo - sv > c.v1);
+}
+
+// Is the box [bx0, bx1] x [by0, by1] (rounded outward) inside the inner
+// window of an instance, projections' rounding included?  Then the exact
+// test (inst_sees) accepts every query of the box.
+__device__ __forceinline__ bool inner_sees(const InstCull &c, const InstF32 &f, float nx, float ny, float bx0,
+                                           float bx1, float by0, float by1, float wmag)
+{
+    if (bx0 < f.x0 || bx1 > f.x1 || by0 < f.y0 || by1 > f.y1) return false;
+    if (f.n0 > -INFINITY || f.n1 < INFINITY) {
+        const float sn = 4e-7f * (fabsf(nx) + fabsf(ny)) * wmag;
+        const float n_lo = fmaf(nx, nx >= 0.f ? bx0 : bx1, ny * (ny >= 0.f ? by0 : by1));
+        const float n_hi = fmaf(nx, nx >= 0.f ? bx1 : bx0, ny * (ny >= 0.f ? by1 : by0));
+        if (n_lo - sn < f.n0 || n_hi + sn > f.n1) return false;
+    }
+    if (f.v0 > -INFINITY || f.v1 < INFINITY) {
+        const float sv = 4e-7f * (fabsf(c.vx) + fabsf(c.vy)) * wmag;
+        const float v_lo = fmaf(c.vx, c.vx >= 0.f ? bx0 : bx1, c.vy * (c.vy >= 0.f ? by0 : by1));
+        const float v_hi = fmaf(c.vx, c.vx >= 0.f ? bx1 : bx0, c.vy * (c.vy >= 0.f ? by1 : by0));
+        if (v_lo - sv < f.v0 || v_hi + sv > f.v1) return false;
+    }
+    return true;
+}
+
+// Line term sign in FP32 for the query (xr, yr) (the reduced point within
+// 2^-23 relative): +1 / -1 when the cross product clears its error band
+// (the coordinates' and the line data's rounding, four times over), 0 when
+// only the exact test (line_side) can decide.
+__device__ __forceinline__ int line_side_f32(const InstF32 &f, float xr, float yr)
+{
+    const float dx = xr - f.lx, dy = yr - f.ly;
+    const float cr = fmaf(f.lvx, dy, -f.lvy * dx);
+    const float band = 4.76837158203125e-7f *      // 2^-21
+                       (fabsf(f.lvx) * (fabsf(yr) + fabsf(f.ly)) + fabsf(f.lvy) * (fabsf(xr) + fabsf(f.lx)));
+    return cr > band ? 1 : (cr < -band ? -1 : 0);
 }
 
 // Line term of Eq. 9 (+1 on the left of L, -1 on the right, 0 on L) for the

@@ -848,51 +848,51 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     std::vector<PairDev> hp_dev;
     for (const Pair &pr : pairs) hp_dev.push_back({pr.plo, pr.phi});
     // per instance, the query region its exact test can accept (inst_sees),
-    // widened far beyond the rounding of that test
+    // widened far beyond the rounding of that test (InstCull: a query outside
+    // it is not seen), and the same region shrunk by as much (InstF32: a query
+    // inside it is seen)
     std::vector<InstCull> cull(inst.size());
-    struct Cull64 { double x0, x1, y0, y1, n0, n1, v0, v1, vx, vy; };
+    std::vector<InstF32> instf(inst.size());
+    struct Win64 { double x0, x1, y0, y1, n0, n1, v0, v1; };
     for (size_t j = 0; j < inst.size(); j++) {
         const InstDev &in = inst[j];
-        Cull64 c;
+        Win64 c, e;                 // c widened, e shrunk
         c.x0 = c.y0 = c.n0 = c.v0 = -INFINITY;
         c.x1 = c.y1 = c.n1 = c.v1 = INFINITY;
-        c.vx = c.vy = 0.0;
-        auto widen = [](double &lo, double &hi, double mag) {
+        e = c;
+        double vx = 0.0, vy = 0.0;
+        auto bounds = [](double lo, double hi, double mag, double &wlo, double &whi, double &slo, double &shi) {
             const double sl = 1e-9 * (mag + 1.0);
-            lo -= sl;
-            hi += sl;
+            wlo = lo - sl;
+            whi = hi + sl;
+            slo = lo + sl;
+            shi = hi - sl;
         };
         if (in.type == IT_BOX) {
             const HostLoop &L = loops[in.loop];
-            if (in.axes & 1) {
-                c.x0 = L.box[0] + in.Tx;
-                c.x1 = L.box[1] + in.Tx;
-                widen(c.x0, c.x1, std::fabs(L.box[0]) + std::fabs(L.box[1]) + std::fabs(in.Tx));
-            }
-            if (in.axes & 2) {
-                c.y0 = L.box[2] + in.Ty;
-                c.y1 = L.box[3] + in.Ty;
-                widen(c.y0, c.y1, std::fabs(L.box[2]) + std::fabs(L.box[3]) + std::fabs(in.Ty));
-            }
+            if (in.axes & 1)
+                bounds(L.box[0] + in.Tx, L.box[1] + in.Tx, std::fabs(L.box[0]) + std::fabs(L.box[1]) + std::fabs(in.Tx),
+                       c.x0, c.x1, e.x0, e.x1);
+            if (in.axes & 2)
+                bounds(L.box[2] + in.Ty, L.box[3] + in.Ty, std::fabs(L.box[2]) + std::fabs(L.box[3]) + std::fabs(in.Ty),
+                       c.y0, c.y1, e.y0, e.y1);
         } else if (in.type == IT_LINE || in.type == IT_PE) {
             if (in.pair >= 0) {
                 const Pair &pr = pairs[in.pair];
                 const double cp = (double)in.c * PP;
-                c.n0 = cp + pr.plo;
-                c.n1 = cp + pr.phi;
-                widen(c.n0, c.n1, std::fabs(cp) + std::fabs(pr.plo) + std::fabs(pr.phi) +
-                                      (std::fabs(nx) + std::fabs(ny)) * (Pu + Pv));
+                bounds(cp + pr.plo, cp + pr.phi,
+                       std::fabs(cp) + std::fabs(pr.plo) + std::fabs(pr.phi) + (std::fabs(nx) + std::fabs(ny)) * (Pu + Pv),
+                       c.n0, c.n1, e.n0, e.n1);
             }
             if (in.type == IT_PE) {
                 const HostLoop &L = loops[in.loop];
                 const double fx = (Pu > 0) ? in.Fx : 0.0, fy = (Pv > 0) ? in.Fy : 0.0;
                 const double off = fx * L.v[0] + fy * L.v[1];
-                c.vx = L.v[0];
-                c.vy = L.v[1];
-                c.v0 = ((double)in.k + L.smin) * L.vv + off;
-                c.v1 = ((double)in.k + L.smax) * L.vv + off;
-                widen(c.v0, c.v1, std::fabs(c.v0) + std::fabs(c.v1) + std::fabs(off) +
-                                      (std::fabs(L.v[0]) + std::fabs(L.v[1])) * (Pu + Pv + 1.0));
+                vx = L.v[0];
+                vy = L.v[1];
+                const double v0 = ((double)in.k + L.smin) * L.vv + off, v1 = ((double)in.k + L.smax) * L.vv + off;
+                bounds(v0, v1, std::fabs(v0) + std::fabs(v1) + std::fabs(off) + (std::fabs(L.v[0]) + std::fabs(L.v[1])) * (Pu + Pv + 1.0),
+                       c.v0, c.v1, e.v0, e.v1);
             }
         }
         auto lo = [](double x) { return std::nextafter((float)x, -INFINITY); };
@@ -900,11 +900,32 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         InstCull f;
         f.x0 = lo(c.x0); f.x1 = hi(c.x1); f.y0 = lo(c.y0); f.y1 = hi(c.y1);
         f.n0 = lo(c.n0); f.n1 = hi(c.n1); f.v0 = lo(c.v0); f.v1 = hi(c.v1);
-        f.vx = (float)c.vx; f.vy = (float)c.vy;
+        f.vx = (float)vx; f.vy = (float)vy;
         f.pad0 = f.pad1 = 0.f;
         cull[j] = f;
+        // inner window rounded inward, infinite sides kept (an empty window
+        // accepts nothing)
+        auto ilo = [](double x) { return std::isinf(x) ? (float)x : std::nextafter((float)x, INFINITY); };
+        auto ihi = [](double x) { return std::isinf(x) ? (float)x : std::nextafter((float)x, -INFINITY); };
+        InstF32 g;
+        g.x0 = ilo(e.x0); g.x1 = ihi(e.x1); g.y0 = ilo(e.y0); g.y1 = ihi(e.y1);
+        g.n0 = ilo(e.n0); g.n1 = ihi(e.n1); g.v0 = ilo(e.v0); g.v1 = ihi(e.v1);
+        g.txh = (float)in.Tx;
+        g.txl = (float)(in.Tx - (double)g.txh);
+        g.tyh = (float)in.Ty;
+        g.tyl = (float)(in.Ty - (double)g.tyh);
+        g.lx = g.ly = g.lvx = g.lvy = 0.f;
+        if (in.type == IT_LINE) {
+            const HostLoop &L = loops[in.loop];
+            g.lx = (float)(((Pu > 0) ? in.Fx : 0.0) + L.g0[0]);
+            g.ly = (float)(((Pv > 0) ? in.Fy : 0.0) + L.g0[1]);
+            g.lvx = (float)L.v[0];
+            g.lvy = (float)L.v[1];
+        }
+        instf[j] = g;
     }
     dv.cull = up.up(cull);
+    dv.instf = up.up(instf);
     dv.n_inst = (int)inst.size();
     dv.n_pairs = (int)pairs.size();
     dv.inst = up.up(inst);

@@ -91,6 +91,25 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x)
     return __uint_as_float(sign | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
+// An interval of FP32 values around a truncated coordinate r (within 2^-23
+// of the double it came from, or below 2^-126) that holds that double.
+__device__ __forceinline__ float pt_lo(float r) { return r - fabsf(r) * 2.384185791015625e-7f - 1e-30f; }
+__device__ __forceinline__ float pt_hi(float r) { return r + fabsf(r) * 2.384185791015625e-7f + 1e-30f; }
+
+// (h, l) = (ah + al) - (bh + bl) as an FP32 pair: Knuth's TwoSum of the high
+// parts, the low parts and the rounding error added, then TwoSum again, so
+// h + l is the difference to about 2^-47 of the operands' magnitudes.
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float &h, float &l)
+{
+    const float s = ah - bh;
+    const float bb = s - ah;
+    const float e = (ah - (s - bb)) + (-bh - bb);
+    const float t = e + (al - bl);
+    h = s + t;
+    const float b2 = h - s;
+    l = (s - (h - b2)) + (t - b2);
+}
+
 __device__ __forceinline__ double exact_cross(double2 a, double2 b, double px, double py)
 {
     double ax = a.x - px, ay = a.y - py, bx = b.x - px, by = b.y - py;
@@ -382,7 +401,9 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
     constexpr int SB = 2 * QPT;                     // status bits per level
     constexpr uint64_t SMASK = (1ull << SB) - 1ull;
     static_assert(SB * kTreeMaxLevels <= 64, "level flags must fit 64 bits");
-    __shared__ double2 s_p[QPT][kSweepThreads];
+    __shared__ double2 s_p[QPT][kSweepThreads];       // reduced queries (FP64), read on the slow paths
+    __shared__ float4 s_ph[QPT][kSweepThreads];       // p - o as FP32 hi/lo pairs (x hi, x lo, y hi, y lo)
+    __shared__ float2 s_pr[QPT][kSweepThreads];       // reduced query in FP32 (within 2^-23)
     __shared__ float s_wb[kSweepThreads / 32][8];     // per warp: query box, |max|, family normal
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -441,7 +462,16 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
                 }
                 if (valid[k]) get_point(A.src, qid[k], x, y);
             }
-            s_p[k][tid] = make_double2(reduce_period(x, Pu), reduce_period(y, Pv));
+            x = reduce_period(x, Pu);
+            y = reduce_period(y, Pv);
+            s_p[k][tid] = make_double2(x, y);
+            // the query's FP64 work, once per query: p - o split into FP32
+            // hi/lo pairs (each instance then subtracts its lattice shift in
+            // FP32), and the reduced point in FP32 for the window pre-tests
+            const double dx0 = x - ox, dy0 = y - oy;
+            const float hx = (float)dx0, hy = (float)dy0;
+            s_ph[k][tid] = make_float4(hx, (float)(dx0 - (double)hx), hy, (float)(dy0 - (double)hy));
+            s_pr[k][tid] = make_float2(f64_to_f32_trunc(x), f64_to_f32_trunc(y));
             acc[k] = 0;
             th[k] = 0.f;
             thl[k] = 0.f;
@@ -456,11 +486,11 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
 #pragma unroll
             for (int k = 0; k < QPT; k++)
                 if (valid[k]) {
-                    const double2 p = s_p[k][tid];
-                    wb0 = fminf(wb0, __double2float_rd(p.x));
-                    wb1 = fmaxf(wb1, __double2float_ru(p.x));
-                    wb2 = fminf(wb2, __double2float_rd(p.y));
-                    wb3 = fmaxf(wb3, __double2float_ru(p.y));
+                    const float2 r = s_pr[k][tid];
+                    wb0 = fminf(wb0, pt_lo(r.x));
+                    wb1 = fmaxf(wb1, pt_hi(r.x));
+                    wb2 = fminf(wb2, pt_lo(r.y));
+                    wb3 = fmaxf(wb3, pt_hi(r.y));
                 }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -475,11 +505,13 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
                 s_wb[warp][2] = wb2;
                 s_wb[warp][3] = wb3;
                 s_wb[warp][4] = fmaxf(fmaxf(fabsf(wb0), fabsf(wb1)), fmaxf(fabsf(wb2), fabsf(wb3)));
-                s_wb[warp][5] = (float)Dp->nx;
-                s_wb[warp][6] = (float)Dp->ny;
             }
-            __syncwarp();
         }
+        if (lane == 0) {
+            s_wb[warp][5] = (float)Dp->nx;
+            s_wb[warp][6] = (float)Dp->ny;
+        }
+        __syncwarp();
         for (int jb = 0; jb < n_inst; jb += 32) {
             const int jl = jb + lane;
             unsigned vis = 1u;
@@ -491,27 +523,47 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
             while (vis) {
                 const int j = jb + __ffs(vis) - 1;
                 vis &= vis - 1;
-                const InstDev in = Dp->inst[j];
-                const LoopDev &L = Dp->loops[in.loop];
+                const InstDev &in = Dp->inst[j];
+                const int itype = in.type;
+                const InstF32 F = Dp->instf[j];
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < QPT; k++) {
-                    const double2 p = s_p[k][tid];
-                    inc[k] = valid[k] && !(fl[k] & (QF_BOUNDARY | QF_ESCALATE)) && inst_sees(*Dp, in, L, p.x, p.y);
-                    if (in.type == IT_LINE) {
+                    inc[k] = valid[k] && !(fl[k] & (QF_BOUNDARY | QF_ESCALATE));
+                    const float2 r = s_pr[k][tid];
+                    if (inc[k] && itype != IT_ALL) {
+                        // FP32 pre-test of the window: outside the widened
+                        // window -> not seen, inside the shrunk one -> seen,
+                        // in between -> the exact FP64 test
+                        const float bx0 = pt_lo(r.x), bx1 = pt_hi(r.x), by0 = pt_lo(r.y), by1 = pt_hi(r.y);
+                        const float wm = fmaxf(fmaxf(fabsf(bx0), fabsf(bx1)), fmaxf(fabsf(by0), fabsf(by1)));
+                        const float *wb = s_wb[warp];
+                        if (!cull_sees(Dp->cull[j], wb[5], wb[6], bx0, bx1, by0, by1, wm)) {
+                            inc[k] = false;
+                        } else if (!inner_sees(Dp->cull[j], F, wb[5], wb[6], bx0, bx1, by0, by1, wm)) {
+                            const double2 p = s_p[k][tid];
+                            inc[k] = inst_sees(*Dp, in, Dp->loops[in.loop], p.x, p.y);
+                            if constexpr (CNT) wk[WK_EXACT]++;
+                        }
+                    }
+                    if (itype == IT_LINE) {
                         if (inc[k]) {
-                            const int sd = line_side(*Dp, in, L, p.x, p.y);
+                            int sd = line_side_f32(F, r.x, r.y);
+                            if (sd == 0) {
+                                const double2 p = s_p[k][tid];
+                                sd = line_side(*Dp, in, Dp->loops[in.loop], p.x, p.y);
+                                if constexpr (CNT) wk[WK_EXACT]++;
+                            }
                             if (sd == 0) fl[k] |= QF_BOUNDARY;
                             acc[k] += sd;
                         }
                         inc[k] = false;
                         continue;
                     }
-                    const double dx = xsub(p.x, in.Tx) - ox, dy = xsub(p.y, in.Ty) - oy;
-                    fx[k] = (float)dx;
-                    fy[k] = (float)dy;
-                    fxl[k] = (float)(dx - (double)fx[k]);
-                    fyl[k] = (float)(dy - (double)fy[k]);
+                    // p' - o = (p - o) - T in FP32 double-float arithmetic
+                    const float4 ph = s_ph[k][tid];
+                    df_sub(ph.x, ph.y, F.txh, F.txl, fx[k], fxl[k]);
+                    df_sub(ph.z, ph.w, F.tyh, F.tyl, fy[k], fyl[k]);
                     const float mag = fmaxf(fabsf(fx[k]), fabsf(fy[k]));
                     if (inc[k] && !(mag <= Mq)) {
                         fl[k] |= QF_ESCALATE;
