@@ -360,16 +360,29 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                                 cudaMemcpyHostToDevice)) != cudaSuccess)
                 return cuda_fail(e, "upload offsets");
             // spatial buckets: about cell_q queries per cell; G x G cells per
-            // domain (the bucketing kernel lays them over the domain's box)
+            // domain (the bucketing kernel lays them over the domain's box),
+            // G <= kBinMaxG so that one CTA holds a domain's cell counters;
+            // the bucketing kernels take each domain's queries in chunks of
+            // about twice its cell count
             std::vector<int4> dcell(n_domains);
+            std::vector<int4> bch;
             int64_t ncell = 0;
             for (int d = 0; d < n_domains; d++) {
                 const int64_t cnt = offsets[d + 1] - offsets[d];
-                const int G = (int)std::min<double>(4096.0, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
+                const int G = (int)std::min<double>((double)kBinMaxG, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
                 dcell[d] = make_int4((int)ncell, G, 0, 0);
                 ncell += (int64_t)G * G;
+                const int64_t csz = std::min<int64_t>(32768, std::max<int64_t>(4096, 2LL * G * G));
+                for (int64_t q0 = 0; q0 < cnt; q0 += csz)
+                    bch.push_back(make_int4(d, (int)(offsets[d] + q0), (int)std::min(csz, cnt - q0), 0));
             }
             if (ncell > INT32_MAX) return fail(WN_ERR_LIMIT, "too many query cells");
+            if ((e = grow(S->W.bchunks, S->W.cap_bchunks, (int64_t)bch.size())) != cudaSuccess)
+                return cuda_fail(e, "cells");
+            S->W.n_bchunks = (int)bch.size();
+            if (!bch.empty() && (e = cudaMemcpy(S->W.bchunks, bch.data(), bch.size() * sizeof(int4),
+                                                cudaMemcpyHostToDevice)) != cudaSuccess)
+                return cuda_fail(e, "upload cells");
             if ((e = grow(S->W.dcell, S->W.cap_dbin, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
             if ((e = grow(S->W.cell_cnt, S->W.cap_cells, ncell)) != cudaSuccess) return cuda_fail(e, "cells");
             if ((e = grow(S->W.bin_chunk, S->W.cap_chunk, (ncell + 4095) / 4096)) != cudaSuccess)
@@ -403,7 +416,8 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                                          (uintptr_t)S->key_qpt, (uintptr_t)g_tun.sweep_ctas_per_sm,
                                          (uintptr_t)g_tun.near_ctas_per_sm, (uintptr_t)g_tun.bucket,
                                          (uintptr_t)S->W.acc2, (uintptr_t)S->W.near_items, (uintptr_t)S->W.perm,
-                                         (uintptr_t)S->W.units, (uintptr_t)S->W.cell_cnt};
+                                         (uintptr_t)S->W.units, (uintptr_t)S->W.cell_cnt,
+                                         (uintptr_t)S->W.bchunks};
             for (int d = 0; d < n_domains; d++) gk.push_back((uintptr_t)domains[d]);
             if (!S->graph_exec || gk != S->graph_key) {
                 if (S->graph_exec) {

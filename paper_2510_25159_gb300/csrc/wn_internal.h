@@ -56,10 +56,19 @@ struct Work {
     int *cell_cnt = nullptr;   // per cell
     int4 *dcell = nullptr;     // per domain: first cell, G
     int *bin_chunk = nullptr;  // per 4096 cells: chunk sum, then its first position
+    int4 *bchunks = nullptr;   // (domain, first query, count, 0): runs of one domain's queries
     int n_cells = 0;
+    int n_bchunks = 0;
+    int64_t cap_bchunks = 0;
     int64_t cap_bin_q = 0, cap_cells = 0, cap_dbin = 0, cap_chunk = 0;
     int64_t cap_q = 0, cap_near = 0, cap_f64 = 0, cap_units = 0, cap_doms = 0, cap_off = 0;
 };
+
+// Spatial bucketing: at most kBinMaxG x kBinMaxG cells per domain, so that a
+// CTA can count one domain's cells in shared memory.
+constexpr int kBinMaxG = 110;
+constexpr int kBinSmemCells = 12288;
+static_assert(kBinMaxG * kBinMaxG <= kBinSmemCells, "cell counters must fit shared memory");
 
 enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_ERR = 4, CNT_OVF = 5,
        CNT_NEAR_CURSOR = 7, CNT_N = 8 };

@@ -829,8 +829,6 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
 // the same in any order.
 struct BinArgs {
     const DomDev *doms;
-    const int4 *units;          // (domain, first query, count): the queries of each domain in runs
-    int n_units;
     long long n;
     PointSrc src;
     const int4 *dcell;          // per domain: first cell, G
@@ -839,50 +837,57 @@ struct BinArgs {
     int *chunk;                 // per chunk of kBinChunk cells: its sum, then its first position
     int *perm;
     int n_cells;
+    const int4 *bchunks;        // (domain, first query, count): runs of one domain's queries
+    int n_bchunks;
 };
 
 constexpr int kBinChunk = 4096;     // cells per block of the chunked scan
+constexpr int kBinThreads = 512;
 
-// Cell of every query, counted per cell.  One warp per unit, so the domain
-// is known without a search.
-__global__ void __launch_bounds__(256) k_bin_count(const BinArgs A)
+// Cell of every query, counted per cell.  One CTA per run of one domain's
+// queries: the run is counted into the domain's cells in shared memory, then
+// one global atomic per non-empty cell adds the run's counts.
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(const BinArgs A)
 {
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < A.n_units; u += warps) {
-        const int4 U = __ldg(&A.units[u]);
-        const DomDev *Dp = A.doms + U.x;
-        const int4 dc = __ldg(&A.dcell[U.x]);
+    __shared__ int s_cnt[kBinSmemCells];
+    for (int c = blockIdx.x; c < A.n_bchunks; c += gridDim.x) {
+        const int4 R = __ldg(&A.bchunks[c]);
+        const DomDev *Dp = A.doms + R.x;
+        const int4 dc = __ldg(&A.dcell[R.x]);
+        const int G = dc.y, G2 = G * G;
         // G x G cells over the domain's box (the base tile on periodic axes);
         // FP32 is enough to choose a cell
         const float x0 = Dp->Pu > 0 ? 0.f : (float)Dp->ox - Dp->M;
         const float y0 = Dp->Pv > 0 ? 0.f : (float)Dp->oy - Dp->M;
         const float wx = Dp->Pu > 0 ? (float)Dp->Pu : 2.f * Dp->M;
         const float wy = Dp->Pv > 0 ? (float)Dp->Pv : 2.f * Dp->M;
-        const float sx = __fdividef((float)dc.y, wx), sy = __fdividef((float)dc.y, wy);
+        const float sx = __fdividef((float)G, wx), sy = __fdividef((float)G, wy);
         // periodic axes: the coordinate's tile offset removed in FP32 (a cell
         // choice needs no exactness)
         const bool pu = Dp->Pu > 0, pv = Dp->Pv > 0;
         const float ipu = pu ? __fdividef(1.f, wx) : 0.f, ipv = pv ? __fdividef(1.f, wy) : 0.f;
-        for (int q0 = 0; q0 < U.z; q0 += 32) {
-            const int ql = q0 + lane;
-            const unsigned act = __ballot_sync(0xffffffffu, ql < U.z);
-            if (ql >= U.z) break;
-            const uint32_t q = (uint32_t)(U.y + ql);
+        for (int i = threadIdx.x; i < G2; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < R.z; i += blockDim.x) {
+            const uint32_t q = (uint32_t)(R.y + i);
             double x, y;
             get_point(A.src, q, x, y);
             float xf = f64_to_f32_trunc(x), yf = f64_to_f32_trunc(y);
             if (pu) xf -= floorf(xf * ipu) * wx;
             if (pv) yf -= floorf(yf * ipv) * wy;
             int cx = (int)floorf((xf - x0) * sx), cy = (int)floorf((yf - y0) * sy);
-            cx = min(max(cx, 0), dc.y - 1);
-            cy = min(max(cy, 0), dc.y - 1);
-            const int cell = dc.x + cy * dc.y + ((cy & 1) ? dc.y - 1 - cx : cx);
-            A.cell_of[q] = cell;
-            // one atomic per distinct cell of the warp
-            const unsigned peers = __match_any_sync(act, cell);
-            if (lane == __ffs(peers) - 1) atomicAdd(&A.cnt[cell], __popc(peers));
+            cx = min(max(cx, 0), G - 1);
+            cy = min(max(cy, 0), G - 1);
+            const int lc = cy * G + ((cy & 1) ? G - 1 - cx : cx);      // serpentine order
+            A.cell_of[q] = dc.x + lc;
+            atomicAdd(&s_cnt[lc], 1);
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < G2; i += blockDim.x) {
+            const int v = s_cnt[i];
+            if (v) atomicAdd(&A.cnt[dc.x + i], v);
+        }
+        __syncthreads();
     }
 }
 
@@ -958,23 +963,30 @@ __global__ void __launch_bounds__(1024) k_bin_chunk_apply(const BinArgs A)
     }
 }
 
-__global__ void __launch_bounds__(256) k_bin_scatter(const BinArgs A)
+// Every query to its slot: per run of one domain's queries, the run's count
+// per cell in shared memory, one global atomic per non-empty cell reserves
+// the run's slots of that cell, and the queries take them in turn.
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const BinArgs A)
 {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); q0 < A.n; q0 += stride) {
-        const long long q = q0 + lane;
-        const unsigned act = __ballot_sync(0xffffffffu, q < A.n);
-        if (q >= A.n) break;
-        const int cell = A.cell_of[q];
-        // the warp's queries of one cell take consecutive slots from one atomic
-        const unsigned peers = __match_any_sync(act, cell);
-        const int leader = __ffs(peers) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&A.cnt[cell], __popc(peers));
-        base = __shfl_sync(act, base, leader);
-        A.perm[base + __popc(peers & lt_mask)] = (int)q;
+    __shared__ int s_cnt[kBinSmemCells];
+    for (int c = blockIdx.x; c < A.n_bchunks; c += gridDim.x) {
+        const int4 R = __ldg(&A.bchunks[c]);
+        const int4 dc = __ldg(&A.dcell[R.x]);
+        const int G2 = dc.y * dc.y;
+        for (int i = threadIdx.x; i < G2; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < R.z; i += blockDim.x) atomicAdd(&s_cnt[A.cell_of[R.y + i] - dc.x], 1);
+        __syncthreads();
+        for (int i = threadIdx.x; i < G2; i += blockDim.x) {
+            const int v = s_cnt[i];
+            if (v) s_cnt[i] = atomicAdd(&A.cnt[dc.x + i], v);      // the run's first slot in the cell
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < R.z; i += blockDim.x) {
+            const int q = R.y + i;
+            A.perm[atomicAdd(&s_cnt[A.cell_of[q] - dc.x], 1)] = q;
+        }
+        __syncthreads();
     }
 }
 
@@ -1753,7 +1765,7 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
 bool mixed_buckets(const Work &W, const LaunchCfg &cfg)
 {
     return cfg.tun.tree && cfg.tun.bucket && !cfg.grid_tiled && W.perm && W.cell_of && W.cell_cnt && W.dcell &&
-           W.bin_chunk && W.n_cells > 0;
+           W.bin_chunk && W.bchunks && W.n_cells > 0 && W.n_bchunks > 0;
 }
 
 int mixed_kernel_count(const Work &W, const LaunchCfg &cfg)
@@ -1786,8 +1798,6 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     if (bucket) {
         BinArgs ba;
         ba.doms = d_doms;
-        ba.units = d_units;
-        ba.n_units = n_units;
         ba.n = n_queries;
         ba.chunk = W.bin_chunk;
         ba.src = src;
@@ -1797,13 +1807,15 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
         ba.perm = W.perm;
         ba.n_cells = W.n_cells;
         if ((e = cudaMemsetAsync(W.cell_cnt, 0, (size_t)W.n_cells * sizeof(int), s)) != cudaSuccess) return e;
-        const int bin_blocks = (int)std::min<long long>((n_queries + 255) / 256, (long long)cfg.n_sm * 32);
+        ba.bchunks = W.bchunks;
+        ba.n_bchunks = W.n_bchunks;
+        const int bin_blocks = std::max(1, std::min(W.n_bchunks, cfg.n_sm * 4));
         const int n_chunks = (W.n_cells + kBinChunk - 1) / kBinChunk;
-        k_bin_count<<<bin_blocks, 256, 0, s>>>(ba);
+        k_bin_count<<<bin_blocks, kBinThreads, 0, s>>>(ba);
         k_bin_chunk_sum<<<n_chunks, 1024, 0, s>>>(ba);
         k_bin_chunk_scan<<<1, 1024, 0, s>>>(ba, n_chunks);
         k_bin_chunk_apply<<<n_chunks, 1024, 0, s>>>(ba);
-        k_bin_scatter<<<bin_blocks, 256, 0, s>>>(ba);
+        k_bin_scatter<<<bin_blocks, kBinThreads, 0, s>>>(ba);
     }
     SweepArgs sa;
     sa.doms = d_doms;
