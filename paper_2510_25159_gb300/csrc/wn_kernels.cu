@@ -158,6 +158,21 @@ __device__ __noinline__ void sweep_record_exact(int ridx, uint32_t fl, bool near
     }
 }
 
+// The exact FP64 window test and line-term sign of instance j, out of line:
+// the sweep's FP32 pre-tests settle almost every query, and inlined these
+// would only crowd the instruction cache.
+__device__ __noinline__ bool inst_sees_exact(const DomDev *__restrict__ Dp, int j, double x, double y)
+{
+    const InstDev &in = Dp->inst[j];
+    return inst_sees(*Dp, in, Dp->loops[in.loop], x, y);
+}
+
+__device__ __noinline__ int line_side_exact(const DomDev *__restrict__ Dp, int j, double x, double y)
+{
+    const InstDev &in = Dp->inst[j];
+    return line_side(*Dp, in, Dp->loops[in.loop], x, y);
+}
+
 // Signed crossings of the +x ray from p by a node's whole polyline when the
 // polyline lies right of p: [end above p] - [start above p], with the exact
 // FP64 comparison for a sign inside its band.  Out of line.
@@ -542,7 +557,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
                             inc[k] = false;
                         } else if (!inner_sees(Dp->cull[j], F, wb[5], wb[6], bx0, bx1, by0, by1, wm)) {
                             const double2 p = s_p[k][tid];
-                            inc[k] = inst_sees(*Dp, in, Dp->loops[in.loop], p.x, p.y);
+                            inc[k] = inst_sees_exact(Dp, j, p.x, p.y);
                             if constexpr (CNT) wk[WK_EXACT]++;
                         }
                     }
@@ -551,7 +566,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
                             int sd = line_side_f32(F, r.x, r.y);
                             if (sd == 0) {
                                 const double2 p = s_p[k][tid];
-                                sd = line_side(*Dp, in, Dp->loops[in.loop], p.x, p.y);
+                                sd = line_side_exact(Dp, j, p.x, p.y);
                                 if constexpr (CNT) wk[WK_EXACT]++;
                             }
                             if (sd == 0) fl[k] |= QF_BOUNDARY;
