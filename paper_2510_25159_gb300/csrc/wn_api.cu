@@ -1,6 +1,7 @@
 // wn_api.cu -- the C ABI of include/wn.h: domain lifetime, scratch memory,
 // the batched work list, host-buffer staging, tuning and counters.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -17,6 +18,37 @@ thread_local std::string g_err;
 std::mutex g_mu;
 Tuning g_tun;
 
+// Batch tables of one list of domains (see build_tables).
+struct Tables {
+    std::vector<const wn_domain *> key_doms;
+    std::vector<int64_t> key_offsets;
+    int key = 0;
+    int n_units = 0, n_cells = 0, n_bchunks = 0;
+    int4 *units = nullptr;
+    DomDev *doms = nullptr;
+    int64_t *offsets = nullptr;
+    int4 *dcell = nullptr;
+    int4 *bchunks = nullptr;
+    int64_t cap_units = 0, cap_doms = 0, cap_off = 0, cap_dbin = 0, cap_bchunks = 0;
+};
+
+// A large mixed batch from host buffers runs as G groups of domains, so that
+// each group's copies overlap the other groups' kernels.  With the copies
+// taking C (about 25 bytes per query at ~200 GB/s) a split hides C (1 - 1/G)
+// and costs about kGroupCostMs per extra group (the latency-bound tails of
+// each group's kernels), so G = sqrt(C / kGroupCostMs), at most kMaxGroups.
+constexpr int kMaxGroups = 8;
+constexpr int64_t kGroupMinQueries = 1 << 21;
+constexpr double kGroupCostMs = 0.3;
+constexpr double kCopyMsPerQuery = 25.0 / 200e9 * 1e3;
+
+int group_count(int64_t n, int32_t n_domains)
+{
+    if (n < kGroupMinQueries || n_domains < 2) return 1;
+    const int G = (int)std::lround(std::sqrt((double)n * kCopyMsPerQuery / kGroupCostMs));
+    return std::max(1, std::min({G, kMaxGroups, (int)n_domains}));
+}
+
 struct DevState {
     bool init = false;
     int n_sm = 0;
@@ -26,13 +58,13 @@ struct DevState {
     double *st_w = nullptr;
     uint8_t *st_st = nullptr;
     int64_t cap_st = 0;
-    // batch tables, reused while the batch layout does not change
-    std::vector<const wn_domain *> key_doms;
-    std::vector<int64_t> key_offsets;
-    int key_qpt = 0;
-    int n_units = 0;
-    std::vector<DomDev> h_doms;
-    std::vector<int4> h_units;
+    // batch tables, reused while the batch layout does not change: the
+    // whole list's, and those of the groups of a large host-buffer batch
+    Tables main;
+    Tables grp[kMaxGroups];
+    // copy streams and events of a grouped host-buffer batch
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev[2 * kMaxGroups + 2] = {};
     wn_stats last{};
     bool profiling = false;
     std::vector<cudaEvent_t> events;
@@ -203,11 +235,14 @@ void wn_destroy_domain(wn_domain *d)
     drop_graphs();
     // batch tables that name this domain must be rebuilt
     for (DevState &S : g_dev)
-        for (const wn_domain *k : S.key_doms)
-            if (k == d) {
-                S.key_doms.clear();
-                break;
-            }
+        for (int t = 0; t <= kMaxGroups; t++) {
+            Tables &T = t == 0 ? S.main : S.grp[t - 1];
+            for (const wn_domain *k : T.key_doms)
+                if (k == d) {
+                    T.key_doms.clear();
+                    break;
+                }
+        }
     delete d;
 }
 
@@ -226,6 +261,114 @@ wn_status wn_set_tuning(int32_t qpt, int32_t sweep_ctas_per_sm, int32_t near_cta
     if (tree >= 0) g_tun.tree = tree != 0;
     if (bucket >= 0) g_tun.bucket = bucket != 0;
     return WN_OK;
+}
+
+// The batch tables of one list of domains: the work list of (domain, query
+// tile) units in decreasing cost order, the domain records, the offsets and
+// the bucketing layout, uploaded once and reused while the list, its query
+// offsets and the launch shape are unchanged.
+static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *domains, int32_t n_domains,
+                              const int64_t *offsets, int key, bool grid_tiled, const PointSrc &src,
+                              int32_t grid_nv, int64_t tile)
+{
+    const bool same = T.key == key && T.key_doms.size() == (size_t)n_domains &&
+                      (n_domains == 1 || std::equal(T.key_doms.begin(), T.key_doms.end(), domains)) &&
+                      T.key_offsets.size() == (size_t)n_domains + 1 &&
+                      std::equal(T.key_offsets.begin(), T.key_offsets.end(), offsets);
+    cudaError_t e;
+    if (same) {
+        // the shared cell scratch may have been sized for a smaller list since
+        if ((e = grow(S->W.cell_cnt, S->W.cap_cells, (int64_t)T.n_cells)) != cudaSuccess ||
+            (e = grow(S->W.bin_chunk, S->W.cap_chunk, ((int64_t)T.n_cells + 4095) / 4096)) != cudaSuccess)
+            return cuda_fail(e, "cells");
+        return WN_OK;
+    }
+    T.key_doms.clear();
+    std::vector<DomDev> h_doms(n_domains);
+    std::vector<std::pair<double, int4>> u;
+    for (int d = 0; d < n_domains; d++) {
+        h_doms[d] = domains[d]->dev;
+        // positions to sweep: the queries, or the cells of every tile of the grid
+        const int64_t cnt = grid_tiled ? (int64_t)src.tiles_x * ((grid_nv + 7) / 8) * 64 : offsets[d + 1] - offsets[d];
+        // sweep cost of one query of this domain: records of every instance
+        const double work = (double)std::max<int64_t>(domains[d]->sweep_records, 1);
+        for (int64_t q0 = 0; q0 < cnt; q0 += tile) {
+            const int64_t c = std::min(tile, cnt - q0);
+            u.push_back({work * (double)c, make_int4(d, (int)(offsets[d] + q0), (int)c, 0)});
+        }
+    }
+    std::stable_sort(u.begin(), u.end(), [](const std::pair<double, int4> &a, const std::pair<double, int4> &b) {
+        return a.first > b.first;
+    });
+    std::vector<int4> h_units(u.size());
+    for (size_t i = 0; i < u.size(); i++) h_units[i] = u[i].second;
+    T.n_units = (int)u.size();
+    if ((e = grow(T.units, T.cap_units, (int64_t)u.size())) != cudaSuccess) return cuda_fail(e, "units");
+    if ((e = grow(T.doms, T.cap_doms, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "doms");
+    if ((e = grow(T.offsets, T.cap_off, (int64_t)n_domains + 1)) != cudaSuccess) return cuda_fail(e, "offsets");
+    if ((e = cudaMemcpy(T.units, h_units.data(), u.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "upload units");
+    if ((e = cudaMemcpy(T.doms, h_doms.data(), n_domains * sizeof(DomDev), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "upload domains");
+    if ((e = cudaMemcpy(T.offsets, offsets, (n_domains + 1) * sizeof(int64_t), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return cuda_fail(e, "upload offsets");
+    // spatial buckets: about cell_q queries per cell; G x G cells per
+    // domain (the bucketing kernel lays them over the domain's box),
+    // G <= kBinMaxG so that one CTA holds a domain's cell counters;
+    // the bucketing kernels take each domain's queries in chunks of
+    // about twice its cell count
+    std::vector<int4> dcell(n_domains);
+    std::vector<int4> bch;
+    int64_t ncell = 0;
+    for (int d = 0; d < n_domains; d++) {
+        const int64_t cnt = offsets[d + 1] - offsets[d];
+        const int G = (int)std::min<double>((double)kBinMaxG, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
+        dcell[d] = make_int4((int)ncell, G, 0, 0);
+        ncell += (int64_t)G * G;
+        const int64_t csz = std::min<int64_t>(32768, std::max<int64_t>(4096, 2LL * G * G));
+        for (int64_t q0 = 0; q0 < cnt; q0 += csz)
+            bch.push_back(make_int4(d, (int)(offsets[d] + q0), (int)std::min(csz, cnt - q0), 0));
+    }
+    if (ncell > INT32_MAX) return fail(WN_ERR_LIMIT, "too many query cells");
+    if ((e = grow(T.bchunks, T.cap_bchunks, (int64_t)bch.size())) != cudaSuccess) return cuda_fail(e, "cells");
+    T.n_bchunks = (int)bch.size();
+    if (!bch.empty() &&
+        (e = cudaMemcpy(T.bchunks, bch.data(), bch.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "upload cells");
+    if ((e = grow(T.dcell, T.cap_dbin, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
+    if ((e = grow(S->W.cell_cnt, S->W.cap_cells, ncell)) != cudaSuccess) return cuda_fail(e, "cells");
+    if ((e = grow(S->W.bin_chunk, S->W.cap_chunk, (ncell + 4095) / 4096)) != cudaSuccess)
+        return cuda_fail(e, "cells");
+    T.n_cells = (int)ncell;
+    if ((e = cudaMemcpy(T.dcell, dcell.data(), n_domains * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "upload cells");
+    T.key_doms.assign(domains, domains + n_domains);
+    T.key_offsets.assign(offsets, offsets + n_domains + 1);
+    T.key = key;
+    drop_graphs();
+    return WN_OK;
+}
+
+// The shared scratch with one list's tables in place.
+static Work work_with(const DevState *S, const Tables &T)
+{
+    Work W = S->W;
+    W.units = T.units;
+    W.doms = T.doms;
+    W.offsets = T.offsets;
+    W.dcell = T.dcell;
+    W.bchunks = T.bchunks;
+    W.n_cells = T.n_cells;
+    W.n_bchunks = T.n_bchunks;
+    return W;
+}
+
+static double near_expected_of(const wn_domain *const *domains, int32_t n_domains, const int64_t *offsets)
+{
+    double x = 0.0;
+    for (int d = 0; d < n_domains; d++) x += (double)(offsets[d + 1] - offsets[d]) * domains[d]->near_density;
+    return std::fmin(x, 4e9);
 }
 
 static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
@@ -276,10 +419,15 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
     }
     if (points && !h_pts && (reinterpret_cast<uintptr_t>(points) & 15))
         return fail(WN_ERR_ARG, "device points must be 16-byte aligned");
+    // a large mixed batch from host buffers runs as groups of domains whose
+    // copies overlap the other groups' kernels
+    const int n_groups = group_count(n, n_domains);
+    const bool grouped = h_pts && precision == WN_PREC_MIXED && !grid.nu && !bits && !S->profiling &&
+                         !S->counting && n_groups >= 2;
     const double *d_pts = points;
     if (h_pts) {
-        if ((e = cudaMemcpyAsync(S->st_pts, points, 2 * n * sizeof(double), cudaMemcpyHostToDevice,
-                                 stream)) != cudaSuccess)
+        if (!grouped && (e = cudaMemcpyAsync(S->st_pts, points, 2 * n * sizeof(double), cudaMemcpyHostToDevice,
+                                             stream)) != cudaSuccess)
             return cuda_fail(e, "copy points");
         d_pts = S->st_pts;
     }
@@ -314,98 +462,103 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
         // the tree sweep gives each warp its own unit, the flat sweep each CTA
         const int64_t tile = (g_tun.tree ? 32LL : 256LL) * qpt;
         const int key = ((qpt * 2 + (g_tun.tree ? 1 : 0)) * 4096 + g_tun.cell_q) * 2 + (grid_tiled ? 1 : 0);
-        // the tables of a one-domain call do not depend on the domain (its
-        // kernels read the domain's own device copy)
-        const bool same = S->key_qpt == key && S->key_doms.size() == (size_t)n_domains &&
-                          (n_domains == 1 || std::equal(S->key_doms.begin(), S->key_doms.end(), domains)) &&
-                          S->key_offsets.size() == (size_t)n_domains + 1 &&
-                          std::equal(S->key_offsets.begin(), S->key_offsets.end(), offsets);
-        if (!same) {
-            S->h_doms.resize(n_domains);
-            std::vector<std::pair<double, int4>> u;
-            for (int d = 0; d < n_domains; d++) {
-                S->h_doms[d] = domains[d]->dev;
-                // positions to sweep: the queries, or the cells of every tile of the grid
-                const int64_t cnt = grid_tiled ? (int64_t)src.tiles_x * ((grid.nv + 7) / 8) * 64
-                                               : offsets[d + 1] - offsets[d];
-                // sweep cost of one query of this domain: records of every instance
-                const double work = (double)std::max<int64_t>(domains[d]->sweep_records, 1);
-                for (int64_t q0 = 0; q0 < cnt; q0 += tile) {
-                    const int64_t c = std::min(tile, cnt - q0);
-                    u.push_back({work * (double)c, make_int4(d, (int)(offsets[d] + q0), (int)c, 0)});
-                }
+        if (grouped) {
+            // groups of consecutive domains with about n / G queries each
+            const int G = n_groups;
+            std::vector<int> gb(1, 0);
+            for (int g = 1; g < G; g++) {
+                int d = gb.back() + 1;
+                while (d < n_domains && offsets[d] < (int64_t)((double)n * g / G)) d++;
+                if (d < n_domains) gb.push_back(d);
             }
-            std::stable_sort(u.begin(), u.end(),
-                             [](const std::pair<double, int4> &a, const std::pair<double, int4> &b) {
-                                 return a.first > b.first;
-                             });
-            S->h_units.resize(u.size());
-            for (size_t i = 0; i < u.size(); i++) S->h_units[i] = u[i].second;
-            S->n_units = (int)u.size();
-            int64_t cu = S->W.cap_units, cd = S->W.cap_doms;
-            if ((e = grow(S->W.units, cu, (int64_t)u.size())) != cudaSuccess) return cuda_fail(e, "units");
-            if ((e = grow(S->W.doms, cd, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "doms");
-            if ((e = grow(S->W.offsets, S->W.cap_off, (int64_t)n_domains + 1)) != cudaSuccess)
-                return cuda_fail(e, "offsets");
-            S->W.cap_units = cu;
-            S->W.cap_doms = cd;
-            cudaStreamSynchronize(stream);
-            if ((e = cudaMemcpy(S->W.units, S->h_units.data(), u.size() * sizeof(int4),
-                                cudaMemcpyHostToDevice)) != cudaSuccess)
-                return cuda_fail(e, "upload units");
-            if ((e = cudaMemcpy(S->W.doms, S->h_doms.data(), n_domains * sizeof(DomDev),
-                                cudaMemcpyHostToDevice)) != cudaSuccess)
-                return cuda_fail(e, "upload domains");
-            if ((e = cudaMemcpy(S->W.offsets, offsets, (n_domains + 1) * sizeof(int64_t),
-                                cudaMemcpyHostToDevice)) != cudaSuccess)
-                return cuda_fail(e, "upload offsets");
-            // spatial buckets: about cell_q queries per cell; G x G cells per
-            // domain (the bucketing kernel lays them over the domain's box),
-            // G <= kBinMaxG so that one CTA holds a domain's cell counters;
-            // the bucketing kernels take each domain's queries in chunks of
-            // about twice its cell count
-            std::vector<int4> dcell(n_domains);
-            std::vector<int4> bch;
-            int64_t ncell = 0;
-            for (int d = 0; d < n_domains; d++) {
-                const int64_t cnt = offsets[d + 1] - offsets[d];
-                const int G = (int)std::min<double>((double)kBinMaxG, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
-                dcell[d] = make_int4((int)ncell, G, 0, 0);
-                ncell += (int64_t)G * G;
-                const int64_t csz = std::min<int64_t>(32768, std::max<int64_t>(4096, 2LL * G * G));
-                for (int64_t q0 = 0; q0 < cnt; q0 += csz)
-                    bch.push_back(make_int4(d, (int)(offsets[d] + q0), (int)std::min(csz, cnt - q0), 0));
+            gb.push_back(n_domains);
+            const int ng = (int)gb.size() - 1;
+            // every table, scratch and stream first: nothing below waits on the host
+            std::vector<std::vector<int64_t>> og(ng);
+            int64_t n_max = 0;
+            double near_max = 0.0;
+            for (int g = 0; g < ng; g++) {
+                const int d0 = gb[g], d1 = gb[g + 1];
+                og[g].resize(d1 - d0 + 1);
+                for (int i = 0; i <= d1 - d0; i++) og[g][i] = offsets[d0 + i] - offsets[d0];
+                PointSrc sg = src;
+                if ((st = build_tables(S, S->grp[g], domains + d0, d1 - d0, og[g].data(), key, false, sg, 0, tile)) !=
+                    WN_OK)
+                    return st;
+                n_max = std::max(n_max, og[g].back());
+                near_max = std::max(near_max, near_expected_of(domains + d0, d1 - d0, og[g].data()));
             }
-            if (ncell > INT32_MAX) return fail(WN_ERR_LIMIT, "too many query cells");
-            if ((e = grow(S->W.bchunks, S->W.cap_bchunks, (int64_t)bch.size())) != cudaSuccess)
-                return cuda_fail(e, "cells");
-            S->W.n_bchunks = (int)bch.size();
-            if (!bch.empty() && (e = cudaMemcpy(S->W.bchunks, bch.data(), bch.size() * sizeof(int4),
-                                                cudaMemcpyHostToDevice)) != cudaSuccess)
-                return cuda_fail(e, "upload cells");
-            if ((e = grow(S->W.dcell, S->W.cap_dbin, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "cells");
-            if ((e = grow(S->W.cell_cnt, S->W.cap_cells, ncell)) != cudaSuccess) return cuda_fail(e, "cells");
-            if ((e = grow(S->W.bin_chunk, S->W.cap_chunk, (ncell + 4095) / 4096)) != cudaSuccess)
-                return cuda_fail(e, "cells");
-            S->W.n_cells = (int)ncell;
-            if ((e = cudaMemcpy(S->W.dcell, dcell.data(), n_domains * sizeof(int4), cudaMemcpyHostToDevice)) !=
+            if ((e = ensure_work(S->W, n_max, (int64_t)near_max)) != cudaSuccess) return cuda_fail(e, "scratch");
+            if (!S->s_h2d) {
+                if ((e = cudaStreamCreateWithFlags(&S->s_h2d, cudaStreamNonBlocking)) != cudaSuccess ||
+                    (e = cudaStreamCreateWithFlags(&S->s_d2h, cudaStreamNonBlocking)) != cudaSuccess)
+                    return cuda_fail(e, "copy streams");
+                for (int i = 0; i < 2 * kMaxGroups + 2; i++)
+                    if ((e = cudaEventCreateWithFlags(&S->ev[i], cudaEventDisableTiming)) != cudaSuccess)
+                        return cuda_fail(e, "copy events");
+            }
+            cudaEvent_t ev_in = S->ev[2 * kMaxGroups], ev_out = S->ev[2 * kMaxGroups + 1];
+            // the copy streams start after the caller's earlier work
+            if ((e = cudaEventRecord(ev_in, stream)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(S->s_h2d, ev_in, 0)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(S->s_d2h, ev_in, 0)) != cudaSuccess)
+                return cuda_fail(e, "copy streams");
+            for (int g = 0; g < ng; g++) {
+                const int64_t q0 = offsets[gb[g]], nq = offsets[gb[g + 1]] - q0;
+                if ((e = cudaMemcpyAsync(S->st_pts + 2 * q0, points + 2 * q0, 2 * nq * sizeof(double),
+                                         cudaMemcpyHostToDevice, S->s_h2d)) != cudaSuccess ||
+                    (e = cudaEventRecord(S->ev[g], S->s_h2d)) != cudaSuccess)
+                    return cuda_fail(e, "copy points");
+            }
+            int64_t kernels = 0;
+            for (int g = 0; g < ng; g++) {
+                const int d0 = gb[g], nd = gb[g + 1] - d0;
+                const int64_t q0 = offsets[d0], nq = og[g].back();
+                const Tables &T = S->grp[g];
+                Work Wg = work_with(S, T);
+                PointSrc sg = src;
+                sg.pts = S->st_pts + 2 * q0;
+                OutDst og_out = out;
+                if (out.w) og_out.w = out.w + q0;
+                if (out.st) og_out.st = out.st + q0;
+                LaunchCfg cfg{S->n_sm, g_tun, nullptr};
+                for (int d = d0; d < d0 + nd; d++) cfg.rational |= domains[d]->dev.w != nullptr;
+                const DomDev *d_doms = nd == 1 ? domains[d0]->d_self : T.doms;
+                if ((e = cudaStreamWaitEvent(stream, S->ev[g], 0)) != cudaSuccess)
+                    return cuda_fail(e, "copy points");
+                if ((e = launch_mixed(Wg, d_doms, nd, T.units, T.n_units, T.offsets, nq, sg, og_out, cfg, stream)) !=
                     cudaSuccess)
-                return cuda_fail(e, "upload cells");
-            S->key_doms.assign(domains, domains + n_domains);
-            S->key_offsets.assign(offsets, offsets + n_domains + 1);
-            S->key_qpt = key;
-            drop_graphs();
+                    return cuda_fail(e, "mixed kernels");
+                kernels += mixed_kernel_count(Wg, cfg);
+                if ((e = cudaEventRecord(S->ev[kMaxGroups + g], stream)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(S->s_d2h, S->ev[kMaxGroups + g], 0)) != cudaSuccess)
+                    return cuda_fail(e, "copy results");
+                if (h_w && (e = cudaMemcpyAsync(out_w + q0, S->st_w + q0, nq * sizeof(double), cudaMemcpyDeviceToHost,
+                                                S->s_d2h)) != cudaSuccess)
+                    return cuda_fail(e, "copy winding");
+                if (h_st && (e = cudaMemcpyAsync(out_st + q0, S->st_st + q0, nq, cudaMemcpyDeviceToHost, S->s_d2h)) !=
+                                cudaSuccess)
+                    return cuda_fail(e, "copy states");
+            }
+            if ((e = cudaEventRecord(ev_out, S->s_d2h)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(stream, ev_out, 0)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+                return cuda_fail(e, "synchronize");
+            S->last.queries = n;
+            S->last.kernels = kernels;
+            return WN_OK;
         }
-        double near_expected = 0.0;
-        for (int d = 0; d < n_domains; d++)
-            near_expected += (double)(offsets[d + 1] - offsets[d]) * domains[d]->near_density;
-        near_expected = std::fmin(near_expected, 4e9);
-        if ((e = ensure_work(S->W, n, (int64_t)near_expected)) != cudaSuccess) return cuda_fail(e, "scratch");
+        Tables &T = S->main;
+        if ((st = build_tables(S, T, domains, n_domains, offsets, key, grid_tiled, src, grid.nv, tile)) != WN_OK)
+            return st;
+        if ((e = ensure_work(S->W, n, (int64_t)near_expected_of(domains, n_domains, offsets))) != cudaSuccess)
+            return cuda_fail(e, "scratch");
+        Work Wl = work_with(S, T);
         LaunchCfg cfg{S->n_sm, g_tun, S->profiling ? &S->events : nullptr};
         if (S->counting) cfg.work = S->d_work;
         cfg.grid_tiled = grid_tiled;
         for (int d = 0; d < n_domains; d++) cfg.rational |= domains[d]->dev.w != nullptr;
-        const DomDev *d_doms = n_domains == 1 ? domains[0]->d_self : S->W.doms;
+        const DomDev *d_doms = n_domains == 1 ? domains[0]->d_self : T.doms;
         // graph replay: only for device buffers on a non-default stream, not while profiling or counting
         const bool graph = g_tun.use_graph && !S->profiling && !S->counting && stream != nullptr && !h_pts &&
                            !h_w && !h_st;
@@ -413,11 +566,10 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             std::vector<uintptr_t> gk = {(uintptr_t)stream, (uintptr_t)src.pts, (uintptr_t)out.w,
                                          (uintptr_t)out.st, (uintptr_t)out.bits, (uintptr_t)out.nbound,
                                          (uintptr_t)n, (uintptr_t)src.nu, (uintptr_t)src.nv,
-                                         (uintptr_t)S->key_qpt, (uintptr_t)g_tun.sweep_ctas_per_sm,
+                                         (uintptr_t)T.key, (uintptr_t)g_tun.sweep_ctas_per_sm,
                                          (uintptr_t)g_tun.near_ctas_per_sm, (uintptr_t)g_tun.bucket,
                                          (uintptr_t)S->W.acc2, (uintptr_t)S->W.near_items, (uintptr_t)S->W.perm,
-                                         (uintptr_t)S->W.units, (uintptr_t)S->W.cell_cnt,
-                                         (uintptr_t)S->W.bchunks};
+                                         (uintptr_t)T.units, (uintptr_t)S->W.cell_cnt, (uintptr_t)T.bchunks};
             for (int d = 0; d < n_domains; d++) gk.push_back((uintptr_t)domains[d]);
             if (!S->graph_exec || gk != S->graph_key) {
                 if (S->graph_exec) {
@@ -427,8 +579,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                 cudaGraph_t g = nullptr;
                 if ((e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                     return cuda_fail(e, "begin capture");
-                e = launch_mixed(S->W, d_doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src, out,
-                                 cfg, stream);
+                e = launch_mixed(Wl, d_doms, n_domains, T.units, T.n_units, T.offsets, n, src, out, cfg, stream);
                 cudaError_t e2 = cudaStreamEndCapture(stream, &g);
                 if (e != cudaSuccess || e2 != cudaSuccess) {
                     if (g) cudaGraphDestroy(g);
@@ -444,12 +595,12 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             }
             if ((e = cudaGraphLaunch(S->graph_exec, stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
             S->graph_launches++;
-        } else if ((e = launch_mixed(S->W, d_doms, n_domains, S->W.units, S->n_units, S->W.offsets, n, src,
-                                     out, cfg, stream)) != cudaSuccess) {
+        } else if ((e = launch_mixed(Wl, d_doms, n_domains, T.units, T.n_units, T.offsets, n, src, out, cfg,
+                                     stream)) != cudaSuccess) {
             return cuda_fail(e, "mixed kernels");
         }
         S->last.queries = n;
-        S->last.kernels = mixed_kernel_count(S->W, cfg);
+        S->last.kernels = mixed_kernel_count(Wl, cfg);
     }
     if (h_w && (e = cudaMemcpyAsync(out_w, S->st_w, n * sizeof(double), cudaMemcpyDeviceToHost,
                                     stream)) != cudaSuccess)
