@@ -1642,19 +1642,72 @@ struct EscArgs {
     OutDst out;
 };
 
-// Plain FP64 recomputation of the escalated queries (same arithmetic as
-// k_plain, summed in another order).  FP64 is the slow unit, so each query is
+// FP64 recomputation of the escalated queries in the crossing form of the
+// mixed path, every step exact up to FP64 rounding: per record of every
+// instance the query sees, the signed crossings of the +x ray by the chords
+// Algorithm 1 leaves of its segment (root step first, the FP64 walk only when
+// the query is inside the root ellipse), then its gap's crossing and angle;
+// omega = crossings + line halves - sum(gap angles) / 2 pi.  (Summing Eq. 3's
+// chord angles instead, as k_plain does, costs an FP64 atan2 at every node
+// of the walks next to the query.)  FP64 is the slow unit, so each query is
 // spread over one cluster of kEscCluster CTAs, i.e. as many SMs: every CTA's
-// threads share a slice of the segments of each instance the query sees and
-// reduce their chord-angle sums in shared memory; the cluster's first CTA
-// then adds the CTAs' partial sums from their shared memory and writes the
-// result.
+// threads share a slice of the records and reduce their sums in shared
+// memory; the cluster's first CTA then adds the CTAs' partial sums from their
+// shared memory and writes the result.
 constexpr int kEscThreads = 128;
 constexpr int kEscCluster = 8;              // CTAs (one per SM) per escalated query
 
+// One record against the query (p relative to the instance) in FP64: the
+// crossings of its segment's Algorithm 1 chords (or of the closing chord),
+// its gap's crossing and angle.  Returns true when the query is on the
+// boundary.
+__device__ __noinline__ bool record_f64(const DomDev *__restrict__ Dp, int r, double pxp, double pyp, int &c,
+                                        double &dth)
+{
+    const uint32_t fl = __float_as_uint(Dp->rec[4 * r + 1].w);
+    const double2 a = Dp->rec_a64[r], b = Dp->rec_b64[r], nx = Dp->rec_n64[r];
+    const bool sa = a.y > pyp, sb = b.y > pyp, sn = nx.y > pyp;
+    c = 0;
+    dth = 0.0;
+    bool chord = true;              // the straight chord a -> b decides the crossings
+    if (!(fl & RF_CHORD)) {
+        const int s = (int)(fl >> RF_SEG_SHIFT);
+        const double ax = a.x - pxp, ay = a.y - pyp, bx = b.x - pxp, by = b.y - pyp;
+        const double qa = ax * ax + ay * ay, qb = bx * bx + by * by;
+        const double eps = Dp->eps;
+        if (qa < eps * eps || qb < eps * eps) return true;
+        const double L = Dp->seg_B[s];
+        const double S = L * L - (qa + qb);
+        if (!(S < 0.0 || 4.0 * qa * qb > S * S)) {
+            // inside the root ellipse: the FP64 walk
+            int cnt = 0;
+            if (alg1_fp64_sub(Dp->cp + 2 * (size_t)Dp->seg_cp[s], seg_weights(*Dp, s), Dp->seg_deg[s], Dp->max_deg,
+                              L, pxp, pyp, eps, 0.0, 1.0, sa, sb, cnt))
+                return true;
+            c = cnt;
+            chord = false;
+        }
+    }
+    if (chord && sa != sb) {
+        const bool pos = exact_cross(a, b, pxp, pyp) > 0;
+        c += (!sa && sb && pos) ? 1 : ((sa && !sb && !pos) ? -1 : 0);
+    }
+    if (fl & RF_GAP) {
+        const double ux = b.x - pxp, uy = b.y - pyp, vx = nx.x - pxp, vy = nx.y - pyp;
+        const double d = ux * vy - uy * vx;
+        if (sb != sn) {
+            const bool pos = d > 0;
+            c += (!sb && sn && pos) ? 1 : ((sb && !sn && !pos) ? -1 : 0);
+        }
+        dth = atan2(d, ux * vx + uy * vy);
+    }
+    return false;
+}
+
 __global__ void __cluster_dims__(kEscCluster, 1, 1) __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
 {
-    __shared__ double s_ang[kEscThreads];
+    __shared__ double s_th[kEscThreads];
+    __shared__ long long s_acc[kEscThreads];
     __shared__ int s_bnd[kEscThreads];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -1667,8 +1720,8 @@ __global__ void __cluster_dims__(kEscCluster, 1, 1) __launch_bounds__(kEscThread
         double x0, y0;
         get_point(A.src, e.x, x0, y0);
         const double x = reduce_period(x0, Dp->Pu), y = reduce_period(y0, Dp->Pv);
-        FarAngle fa;
-        long long half = 0;
+        double th = 0.0;
+        long long acc = 0;            // 2 * crossings + line sides
         bool bnd = false;
         for (int j = 0; j < Dp->n_inst; j++) {
             const InstDev in = Dp->inst[j];
@@ -1678,37 +1731,39 @@ __global__ void __cluster_dims__(kEscCluster, 1, 1) __launch_bounds__(kEscThread
                 if (tid == 0 && rank == 0) {
                     const int sd = line_side(*Dp, in, L, x, y);
                     bnd |= sd == 0;
-                    half += sd;
+                    acc += sd;
                 }
                 continue;
             }
             const double qx = xsub(x, in.Tx), qy = xsub(y, in.Ty);
-            const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
-            for (int sg = sb + rank * kEscThreads + tid; sg < se && !bnd; sg += kEscCluster * kEscThreads)
-                bnd |= alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[sg]), seg_weights(*Dp, sg),
-                                 __ldg(&Dp->seg_deg[sg]), Dp->max_deg,
-                                 __ldg(&Dp->seg_B[sg]), qx, qy, Dp->eps, fa);
-            if (in.type == IT_PE && tid == 0 && rank == 0) {
-                const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
-                fa.ang -= atan2(ax * by - ay * bx, ax * bx + ay * by);
+            for (int r = in.r0 + rank * kEscThreads + tid; r < in.r1 && !bnd; r += kEscCluster * kEscThreads) {
+                int c;
+                double dth;
+                bnd |= record_f64(Dp, r, qx, qy, c, dth);
+                acc += 2 * c;
+                th += dth;
             }
         }
-        s_ang[tid] = fa.ang;
+        s_th[tid] = th;
+        s_acc[tid] = acc;
         s_bnd[tid] = bnd ? 1 : 0;
         __syncthreads();
         for (int w = kEscThreads / 2; w > 0; w >>= 1) {
             if (tid < w) {
-                s_ang[tid] += s_ang[tid + w];
+                s_th[tid] += s_th[tid + w];
+                s_acc[tid] += s_acc[tid + w];
                 s_bnd[tid] |= s_bnd[tid + w];
             }
             __syncthreads();
         }
         cl.sync();
         if (rank == 0 && tid == 0) {
-            double ang = 0.0;
+            double tsum = 0.0;
+            long long asum = 0;
             int bd = 0;
             for (int r = 0; r < kEscCluster; r++) {
-                ang += *cl.map_shared_rank(&s_ang[0], r);
+                tsum += *cl.map_shared_rank(&s_th[0], r);
+                asum += *cl.map_shared_rank(&s_acc[0], r);
                 bd |= *cl.map_shared_rank(&s_bnd[0], r);
             }
             double om;
@@ -1717,7 +1772,7 @@ __global__ void __cluster_dims__(kEscCluster, 1, 1) __launch_bounds__(kEscThread
                 om = __longlong_as_double(0x7ff8000000000000ULL);
                 st = 2;
             } else {
-                om = ang / kTwoPi + 0.5 * (double)half;
+                om = 0.5 * (double)asum - tsum / kTwoPi;
                 st = om >= 0.5 ? 1 : 0;
             }
             write_out(A.out, e.x, om, st, true);

@@ -239,6 +239,25 @@ def test_host_buffers_grouped_match_device(wn):
     assert st["queries"] == sum(len(q) for q in qs)
 
 
+@pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_half_band_escalation(wn, name, prec, tol):
+    """An open semicircle: its centre sees omega = 1/2 exactly, so queries
+    within 1e-5 of it fall in the mixed path's classification band and are
+    recomputed in FP64; their states hang on the sign of omega - 1/2 at the
+    1e-7 level and must match the oracle's."""
+    arcs = ws.circle_loop((0.5, 0.5), 0.3, n_arcs=16)[:8]
+    dom = ws.make_domain([arcs], eps=1e-9)
+    rng = np.random.default_rng(12)
+    r = np.exp(rng.uniform(np.log(1e-9), np.log(1e-5), 1500))
+    ph = rng.uniform(0, 2 * np.pi, r.size)
+    q = np.stack([0.5 + r * np.cos(ph), 0.5 + r * np.sin(ph)], axis=1)
+    (w, s), = run(wn, [dom], [q], prec)
+    res = compare(dom, q, w, s, tol)
+    assert res["n"] == 1500
+    if prec == 1:
+        assert wn.stats()["fp64_queries"] >= 1000
+
+
 def test_stats_and_profiling(wn):
     doms, qs = ws.config2(n_domains=64, n_uniform=64 * 2000, n_near=64 * 500, domain_subset=range(2))
     wn.set_profiling(True)
