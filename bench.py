@@ -56,9 +56,11 @@ FLOPS_PER_PAIR = 34.0
 #   ellipse test inside a record's circle: two distances 8 (with the two
 #     square roots), focal sum, band and square 4, comparisons 3, chord
 #     difference 1 = 16
+#   control-point box test inside a record's ellipse: chord vector 2, the two
+#     projections 6, band 5, widened bounds 4, comparisons 4 = 21
 WORK_FLOPS = {"node_tests": 30.0, "telescoped_nodes": 8.0, "expansions": 21.0, "expansion_terms": 8.0,
               "record_tests_near": 60.0, "record_tests_far": 54.0, "record_tests_cross": 20.0,
-              "exact_fp64": 0.0, "ellipse_tests": 16.0}
+              "exact_fp64": 0.0, "ellipse_tests": 16.0, "box_tests": 21.0}
 FP32_LANES_PER_SM = 128
 
 

@@ -318,9 +318,9 @@ wn_status wn_kernel_times(double *ms6, int64_t *n_calls);
  * Work tallies of the tree sweep, for measurement (no counterpart in the
  * paper).  With on != 0 the following WN_PREC_MIXED calls on this thread's
  * device run a counting build of the sweep kernel -- the same decisions and
- * arithmetic, plus per-warp tallies -- and add to nine counters, which
+ * arithmetic, plus per-warp tallies -- and add to ten counters, which
  * wn_set_work_counting also clears.  wn_sweep_work synchronises, writes them
- * into out9 (host int64[9]) and clears them:
+ * into out10 (host int64[10]) and clears them:
  *   [0] (query, node) tests          [1] nodes whose crossings telescoped
  *   [2] gap-angle expansion sums     [3] their terms
  *   [4] (query, record) tests with the near check (Alg. 1's first step)
@@ -328,10 +328,11 @@ wn_status wn_kernel_times(double *ms6, int64_t *n_calls);
  *   [6] record tests for crossings only
  *   [7] exact FP64 recomputations of a sign
  *   [8] ellipse tests (Eq. 5) of records whose enclosing circle held the query
+ *   [9] control-point box tests of records whose ellipse held the query
  * Zeros when the flat sweep ran (wn_set_tuning tree = 0) or nothing ran.
  */
 wn_status wn_set_work_counting(int32_t on);
-wn_status wn_sweep_work(int64_t *out9);
+wn_status wn_sweep_work(int64_t *out10);
 
 /*
  * wn_query_noalloc -- the WN_PREC_MIXED query of wn_query for one domain,

@@ -300,7 +300,8 @@ def kernel_times():
 
 
 WORK = ("node_tests", "telescoped_nodes", "expansions", "expansion_terms", "record_tests_near",
-        "record_tests_far", "record_tests_cross", "exact_fp64", "ellipse_tests")
+        "record_tests_far", "record_tests_cross", "exact_fp64", "ellipse_tests",
+        "box_tests")
 
 
 def set_work_counting(on=True):

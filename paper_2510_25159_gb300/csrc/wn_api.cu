@@ -783,9 +783,9 @@ wn_status wn_set_work_counting(int32_t on)
     return WN_OK;
 }
 
-wn_status wn_sweep_work(int64_t *out9)
+wn_status wn_sweep_work(int64_t *out10)
 {
-    if (!out9) return fail(WN_ERR_ARG, "out9 is NULL");
+    if (!out10) return fail(WN_ERR_ARG, "out10 is NULL");
     std::lock_guard<std::mutex> lk(g_mu);
     wn_status st;
     DevState *S = dev_state(st);
@@ -797,7 +797,7 @@ wn_status wn_sweep_work(int64_t *out9)
             return cuda_fail(e, "read work tallies");
         if ((e = cudaMemset(S->d_work, 0, sizeof c)) != cudaSuccess) return cuda_fail(e, "work tallies");
     }
-    for (int i = 0; i < WK_N; i++) out9[i] = (int64_t)c[i];
+    for (int i = 0; i < WK_N; i++) out10[i] = (int64_t)c[i];
     return WN_OK;
 }
 

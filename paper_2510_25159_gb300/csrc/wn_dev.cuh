@@ -112,6 +112,7 @@ struct DomDev {
     const PairDev *pairs;       // [n_pairs]
     const float4 *rec;          // [4 * n_rec]: (a, b), (centre, R^2, flags), (gap, next), (b low)
     const int *rec_seg;         // [n_rec] segment, -1 for a closing chord
+    const float4 *rec_obb;      // [n_rec] (t0, t1, d0, d1): control points' box in the chord's frame
     const double2 *rec_a64;     // [n_rec] exact chord start
     const double2 *rec_b64;     // [n_rec] exact chord end
     const double2 *rec_n64;     // [n_rec] exact next vertex

@@ -320,6 +320,28 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     std::vector<double2> ra64, rb64, rn64;
     std::vector<int> loop_r0(n_loops), loop_r1(n_loops);
     auto f32 = [](double x) { return (float)x; };
+    // per record, the box of its segment's control points in the chord's
+    // frame: t = (P - a).(b - a), d = (P - a) x (b - a), widened by eps |b - a|
+    // (and far beyond FP64 rounding) and rounded outward to FP32.  The curve
+    // lies in the control points' hull, so a query outside the box is more
+    // than eps from the curve and sees it under its chord's angle.
+    std::vector<float4> robb;
+    auto seg_box = [&](const double *a, const double *b, int seg) {
+        if (seg < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const double ex = b[0] - a[0], ey = b[1] - a[1];
+        double t0 = INFINITY, t1 = -INFINITY, d0 = INFINITY, d1 = -INFINITY;
+        for (int i = 0; i <= seg_deg[seg]; i++) {
+            const double px = P[2 * (seg_cp[seg] + i)] - a[0], py = P[2 * (seg_cp[seg] + i) + 1] - a[1];
+            const double t = px * ex + py * ey, d = px * ey - py * ex;
+            t0 = std::fmin(t0, t); t1 = std::fmax(t1, t);
+            d0 = std::fmin(d0, d); d1 = std::fmax(d1, d);
+        }
+        const double el = std::sqrt(ex * ex + ey * ey);
+        const double sl = eps * el * (1.0 + 1e-6) +
+                          1e-12 * (std::fabs(t0) + std::fabs(t1) + std::fabs(d0) + std::fabs(d1) + el * el);
+        return make_float4(std::nextafter((float)(t0 - sl), -INFINITY), std::nextafter((float)(t1 + sl), INFINITY),
+                           std::nextafter((float)(d0 - sl), -INFINITY), std::nextafter((float)(d1 + sl), INFINITY));
+    };
     auto push_rec = [&](const double *a, const double *b, const double *nxt, int seg, double B, bool chord) {
         float4 r0, r1, r2;
         r0.x = f32(a[0] - ox); r0.y = f32(a[1] - oy); r0.z = f32(b[0] - ox); r0.w = f32(b[1] - oy);
@@ -340,6 +362,7 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
         r3.z = f32((nxt[0] - ox) - (double)r2.z);
         r3.w = f32((nxt[1] - oy) - (double)r2.w);
         rec.push_back(r0); rec.push_back(r1); rec.push_back(r2); rec.push_back(r3);
+        robb.push_back(seg_box(a, b, seg));
         rec_seg.push_back(seg);
         ra64.push_back(make_double2(a[0], a[1]));
         rb64.push_back(make_double2(b[0], b[1]));
@@ -621,6 +644,7 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     dv.loops = up.up(hl);
     dv.n_rec = (int)rec_seg.size();
     dv.rec = up.up(rec);
+    dv.rec_obb = up.up(robb);
     dv.rec_seg = up.up(rec_seg);
     dv.rec_a64 = up.up(ra64);
     dv.rec_b64 = up.up(rb64);

@@ -77,9 +77,10 @@ enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_ERR = 4, CNT_OV
 // node tests, nodes whose crossings telescoped, expansion evaluations and
 // their terms, record tests with the near check (Alg. 1's root step), record
 // tests for crossings and gap angle, record tests for crossings only, exact
-// FP64 recomputations, ellipse tests of records whose circle held the query.
+// FP64 recomputations, ellipse tests of records whose circle held the query,
+// control-point box tests of records whose ellipse held it.
 enum { WK_NODE = 0, WK_TELE = 1, WK_EXPANSION = 2, WK_TERMS = 3, WK_REC_NEAR = 4, WK_REC_FAR = 5,
-       WK_REC_CROSS = 6, WK_EXACT = 7, WK_ELLIPSE = 8, WK_N = 9 };
+       WK_REC_CROSS = 6, WK_EXACT = 7, WK_ELLIPSE = 8, WK_BOX = 9, WK_N = 10 };
 
 struct Tuning {
     int qpt = 2;               // queries per sweep thread

@@ -203,16 +203,31 @@ __device__ __forceinline__ float gap_angle(float y, float x)
     return atan2_wide(y, x);
 }
 
+// Inside the ellipse: the box of the segment's control points in the chord's
+// frame (t along b - a, d across it, widened by eps); outside it the query is
+// more than eps from the curve, which it sees under the chord's angle.  The
+// band covers the FP32 errors of a - p = (ux, uy) (T per coordinate), of
+// b - a and of the products.  Out of line: few pairs get here.
+__device__ __noinline__ bool in_control_box(const float4 *obb, float4 R0, float ux, float uy, float T)
+{
+    const float4 O = __ldg(obb);
+    const float ex = R0.z - R0.x, ey = R0.w - R0.y;
+    const float tq = -fmaf(ux, ex, uy * ey), dq = fmaf(uy, ex, -ux * ey);
+    const float bd = 4.f * T * (fabsf(ex) + fabsf(ey) + fabsf(ux) + fabsf(uy));
+    return !((tq < O.x - bd) | (tq > O.y + bd) | (dq < O.z - bd) | (dq > O.w + bd));
+}
+
 // One record against one query in FP32: the root step of Alg. 1 (a circle
 // that contains the ellipse of Eq. 4 and the eps discs, then, inside it, the
-// ellipse itself; `ell` says the second test ran), the chord's
+// ellipse itself, then, inside that, the control points' box; `ell` and
+// `box` say which of the later tests ran), the chord's
 // crossing of the +x ray from p, the gap chord's crossing and the gap angle.
 // `slow` is set when an error band cannot settle a sign; the caller then
 // redoes the record with sweep_record_exact.
 __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, const float4 R2,
                                              const float4 R3, float fx, float fy, float fxl,
-                                             float fyl, float T, int &c, float &dth, bool &near,
-                                             bool &slow, bool &ell)
+                                             float fyl, float T, const float4 *obb, int &c, float &dth,
+                                             bool &near, bool &slow, bool &ell, bool &box)
 {
     const float uy = R0.y - fy, wy = R0.w - fy;
     const bool sa = uy > 0.f, sb = wy > 0.f;
@@ -221,6 +236,7 @@ __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, c
     const float wx = R0.z - fx;
     near = false;
     ell = false;
+    box = false;
     c = 0;
     dth = 0.f;
     const float ux = R0.x - fx;
@@ -237,6 +253,10 @@ __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, c
             const float s = (da + db) - 4.f * T;
             near = !((s > 0.f) & (s * s > 4.f * R1.z));
             ell = true;
+            if (near) {
+                near = in_control_box(obb, R0, ux, uy, T);
+                box = true;
+            }
         }
     }
     if (!near && sa != sb) {
@@ -727,9 +747,9 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
                                     const uint32_t ck = (cf >> (2 * k)) & 3u;
                                     int cc;
                                     float dth;
-                                    bool slow, ell;
-                                    sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], cc, dth, nr[k], slow,
-                                                 ell);
+                                    bool slow, ell, box;
+                                    sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], Dp->rec_obb + r, cc,
+                                                 dth, nr[k], slow, ell, box);
                                     if (slow && ck) {
                                         const double2 p = s_p[k][tid];
                                         sweep_record_exact(r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),
@@ -738,6 +758,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
                                     }
                                     if constexpr (CNT) {
                                         if (ck == 1u && ell) wk[WK_ELLIPSE]++;
+                                        if (ck == 1u && box) wk[WK_BOX]++;
                                         if (ck == 1u) wk[WK_REC_NEAR]++;
                                         else if (ck == 2u) wk[WK_REC_CROSS]++;
                                     }
@@ -1092,8 +1113,9 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
                     for (int k = 0; k < QPT; k++) {
                         int c;
                         float dth;
-                        bool slow, ell;
-                        sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], c, dth, nr[k], slow, ell);
+                        bool slow, ell, box;
+                        sweep_record(R0, R1, R2, R3, fx[k], fy[k], fxl[k], fyl[k], T[k], Dp->rec_obb + r0 + r, c, dth,
+                                     nr[k], slow, ell, box);
                         if (slow && inc[k]) {
                             const double2 p = s_p[k][tid];
                             sweep_record_exact(r0 + r, __float_as_uint(R1.w), nr[k], Dp, xsub(p.x, in.Tx),

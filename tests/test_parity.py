@@ -292,6 +292,7 @@ def test_work_counting_build(wn):
     assert 4 * work["expansions"] <= work["expansion_terms"] <= 32 * work["expansions"]
     assert work["record_tests_near"] > 0 and work["telescoped_nodes"] > 0
     assert 0 < work["ellipse_tests"] <= work["record_tests_near"]
+    assert 0 < work["box_tests"] <= work["ellipse_tests"]
     assert wn.sweep_work()["node_tests"] == 0      # read clears
 
 
