@@ -203,18 +203,30 @@ __device__ __forceinline__ float gap_angle(float y, float x)
     return atan2_wide(y, x);
 }
 
-// Inside the ellipse: the box of the segment's control points in the chord's
-// frame (t along b - a, d across it, widened by eps); outside it the query is
-// more than eps from the curve, which it sees under the chord's angle.  The
-// band covers the FP32 errors of a - p = (ux, uy) (T per coordinate), of
-// b - a and of the products.  Out of line: few pairs get here.
-__device__ __noinline__ bool in_control_box(const float4 *obb, float4 R0, float ux, float uy, float T)
+// A query inside a record's circle: is it inside the ellipse of Eq. 5 and
+// inside the box of the segment's control points (the root step's "near")?
+//   ellipse: the circle's inflated focal sum 2R, |p - a| + |p - b| > 2R is
+//     far; 4T covers the FP32 coordinate errors and R's two 2^-20 inflations
+//     the relative rounding of the distances, their sum and the square, so
+//     "far" here implies far in Alg. 1's own test;
+//   box: in the chord's frame (t along b - a, d across it, widened by eps);
+//     outside it the query is more than eps from the curve, which lies in
+//     the control points' hull and so is seen under its chord's angle.  The
+//     band covers the FP32 errors of a - p = (ux, uy) (T per coordinate), of
+//     b - a and of the products.
+// Out of line: only a few (query, record) pairs get here.  Returns 0 (far by
+// the ellipse), 1 (far by the box) or 2 (near).
+__device__ __noinline__ int root_near(const float4 R0, float R2c, float ux, float uy, float wx, float wy, float T,
+                                      const float4 *obb)
 {
+    const float da = sqrtf(fmaf(ux, ux, uy * uy)), db = sqrtf(fmaf(wx, wx, wy * wy));
+    const float s = (da + db) - 4.f * T;
+    if ((s > 0.f) & (s * s > 4.f * R2c)) return 0;
     const float4 O = __ldg(obb);
     const float ex = R0.z - R0.x, ey = R0.w - R0.y;
     const float tq = -fmaf(ux, ex, uy * ey), dq = fmaf(uy, ex, -ux * ey);
     const float bd = 4.f * T * (fabsf(ex) + fabsf(ey) + fabsf(ux) + fabsf(uy));
-    return !((tq < O.x - bd) | (tq > O.y + bd) | (dq < O.z - bd) | (dq > O.w + bd));
+    return ((tq < O.x - bd) | (tq > O.y + bd) | (dq < O.z - bd) | (dq > O.w + bd)) ? 1 : 2;
 }
 
 // One record against one query in FP32: the root step of Alg. 1 (a circle
@@ -244,19 +256,10 @@ __device__ __forceinline__ void sweep_record(const float4 R0, const float4 R1, c
         const float dcx = R1.x - fx, dcy = R1.y - fy;
         near = fmaf(dcx, dcx, dcy * dcy) <= R1.z;
         if (near) {
-            // inside the circle: the ellipse of Eq. 5 with the circle's
-            // inflated focal sum 2R, |p - a| + |p - b| > 2R.  4T covers the
-            // FP32 coordinate errors and R's two 2^-20 inflations the
-            // relative rounding of the distances, their sum and the square,
-            // so "far" here implies far in Alg. 1's own test.
-            const float da = sqrtf(fmaf(ux, ux, uy * uy)), db = sqrtf(fmaf(wx, wx, wy * wy));
-            const float s = (da + db) - 4.f * T;
-            near = !((s > 0.f) & (s * s > 4.f * R1.z));
+            const int rn = root_near(R0, R1.z, ux, uy, wx, wy, T, obb);
+            near = rn == 2;
             ell = true;
-            if (near) {
-                near = in_control_box(obb, R0, ux, uy, T);
-                box = true;
-            }
+            box = rn != 0;
         }
     }
     if (!near && sa != sb) {
