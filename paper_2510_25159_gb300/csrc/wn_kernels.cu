@@ -451,11 +451,21 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
 #pragma unroll
     for (int i = 0; i < WK_N; i++) wk[i] = 0u;
 
-    // every warp works on its own units (32*QPT queries): no block barrier
+    // every warp works on its own units (32*QPT queries): no block barrier.
+    // A warp claims `batch` consecutive units per atomic on the shared
+    // counter, more when there are many units per warp (the units come in
+    // decreasing cost order, so neighbours cost about the same)
+    const int n_warps = (int)(gridDim.x * (kSweepThreads / 32));
+    const int batch = max(1, min(8, A.n_units / (64 * n_warps)));
+    int u_next = 0, u_end = 0;          // the warp's claimed units (warp-uniform)
     for (;;) {
-        unsigned long long uu = 0;
-        if (lane == 0) uu = atomicAdd(&A.counters[CNT_UNIT], 1ULL);
-        const int u = (int)__shfl_sync(0xffffffffu, uu, 0);
+        if (u_next >= u_end) {
+            unsigned long long uu = 0;
+            if (lane == 0) uu = atomicAdd(&A.counters[CNT_UNIT], (unsigned long long)batch);
+            u_next = (int)__shfl_sync(0xffffffffu, uu, 0);
+            u_end = u_next + batch;
+        }
+        const int u = u_next++;
         if (u >= A.n_units) {
             if constexpr (CNT) {
 #pragma unroll
