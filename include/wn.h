@@ -158,7 +158,11 @@ wn_status wn_query(const wn_domain *domain, const double *points, int64_t n,
  * work list ordered by decreasing cost, then the near-pair, FP64 and
  * finalize kernels; with WN_PREC_PLAIN_FP64 one plain kernel is launched per
  * domain.  The tile shape and launch sizes come from wn_set_tuning or the
- * defaults.  Errors as wn_query.
+ * defaults.  A large WN_PREC_MIXED batch with host points (millions of
+ * queries) runs as groups of consecutive domains, so that the copies of one
+ * group overlap the kernels of the others (two library-owned copy streams,
+ * ordered after the caller's earlier work on `stream`); the call still
+ * returns after the results are in host memory.  Errors as wn_query.
  */
 wn_status wn_query_batched(const wn_domain *const *domains, int32_t n_domains,
                            const int64_t *point_offsets, const double *points,

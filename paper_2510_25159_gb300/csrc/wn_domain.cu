@@ -24,7 +24,8 @@
 //     window on the device.
 //   records: per loop, one FP32 record per segment (chord endpoints, the
 //     inflated circle that contains the ellipse of Lemma 1 and the eps discs,
-//     the gap to the next vertex) plus, for an extended curve, the closing
+//     the gap to the next vertex, and beside it the box of the segment's
+//     control points in the chord's frame) plus, for an extended curve, the closing
 //     chord gamma(0)+v -> gamma(0) that turns W(gamma) - omega(chord) of
 //     Eq. 9 into a closed polygon.
 #include <algorithm>

@@ -1,25 +1,31 @@
 // wn_kernels.cu -- query kernels of the containment library (sm_103a).
 //
 // Mixed path (WN_PREC_MIXED), per call:
-//   k_sweep     persistent CTAs pop (domain, query-tile) units; each CTA
-//               stages the records of every instance it needs in shared
-//               memory and sweeps them against a register tile of queries.
-//               Per record it applies the root step of Algorithm 1 in FP32:
-//               a circle that contains the ellipse of Eq. 4 (inflated by the
-//               FP32 error bound) decides "far"; a far chord then contributes
-//               its signed crossing of the +x ray from the query (the chord's
-//               Eq. 3 angle is an integer multiple of 2 pi plus endpoint
-//               angles that cancel around each loop), and every gap between
-//               consecutive segments contributes its own crossing and its
-//               exact small angle.  Pairs inside the circle go to a queue.
-//   k_near      FP32 Algorithm 1 on each queued pair in query-relative
-//               coordinates; every test carries an error band, and a pair
-//               whose band cannot settle a decision goes to FP64.
-//   k_f64items  Algorithm 1 in FP64 on those pairs.
-//   k_finalize  omega = crossings + line terms / 2 - sum(gap angles) / 2 pi;
-//               a query whose omega lies within 1e-4 of 1/2, or that any
-//               kernel flagged, is recomputed by the plain FP64 method.
-//   k_f64query  plain FP64 recomputation of those queries.
+//   k_bin_*       spatial bucketing: each domain's queries sorted into small
+//                 cells, so that a warp's queries lie close together.
+//   k_sweep_tree  persistent warps pop (domain, query-tile) units and walk
+//                 the record tree of every instance their queries see (the
+//                 flat k_sweep instead stages the records in shared memory).
+//                 Per record reached, the root step of Algorithm 1 in FP32:
+//                 a circle that contains the ellipse of Eq. 4, then the
+//                 ellipse of Eq. 5, then the box of the segment's control
+//                 points (each inflated by its FP32 error bound) decide
+//                 "far"; a far chord then contributes its signed crossing of
+//                 the +x ray from the query (the chord's Eq. 3 angle is an
+//                 integer multiple of 2 pi plus endpoint angles that cancel
+//                 around each loop), and every gap between consecutive
+//                 segments contributes its own crossing and its exact small
+//                 angle.  A node whose records are all far contributes its
+//                 crossings in O(1) and its gap angles by an expansion.
+//                 Pairs that are not far go to a queue.
+//   k_near        FP32 Algorithm 1 on each queued pair in query-relative
+//                 coordinates; every test carries an error band, and a pair
+//                 whose band cannot settle a decision hands its tail to FP64.
+//   k_f64items    Algorithm 1 in FP64 on those tails.
+//   k_finalize    omega = crossings + line terms / 2 - sum(gap angles) / 2 pi;
+//                 a query whose omega lies within 1e-4 of 1/2, or that any
+//                 kernel flagged, is recomputed in FP64.
+//   k_f64query    the FP64 recomputation of those queries (crossing form).
 // Plain path (WN_PREC_PLAIN_FP64): k_plain, one thread per query running
 // Algorithm 1 in FP64 on every segment the query sees, chord angles summed
 // with atan2 (Eq. 3) -- the paper's method ported as is.
