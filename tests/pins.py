@@ -639,6 +639,48 @@ def pin_rational_invariants(L, n=60, seed=34):
         assert b3 == b4 and abs(a3 - a4) < 1e-12
 
 
+def pin_control_box_far(L, n=150, seed=35):
+    """The far test the CUDA sweep adds after the ellipse: in the chord's
+    frame (t = (x - a).(b - a), d = (x - a) x (b - a)) the curve stays inside
+    the box of its control points (the convex-hull property, for positive
+    weights too), and for a query outside that box, widened by eps |b - a|,
+    Algorithm 1 returns exactly the chord's angle (Eq. 3) and no boundary."""
+    rng = np.random.default_rng(seed)
+    eps = 1e-9
+    for i in range(n):
+        deg = 1 + i % 5
+        if i % 2:
+            cps, w = random_rational(rng, deg, spread=2.0)
+        else:
+            cps, w = random_segment(rng, deg), None
+        a, b = cps[0], cps[-1]
+        e = b - a
+        el = math.hypot(e[0], e[1])
+        if el < 1e-3:
+            continue
+
+        def frame(x):
+            x = np.atleast_2d(x) - a
+            return x @ e, x[:, 0] * e[1] - x[:, 1] * e[0]
+
+        tc, dc = frame(cps)
+        ts = np.linspace(0.0, 1.0, 801)
+        curve = np.array([rat_eval(cps, w, t) for t in ts]) if w is not None else power_eval(cps, ts)
+        tcv, dcv = frame(curve)
+        slack = 1e-12 * (1.0 + el * el)
+        assert tcv.min() >= tc.min() - slack and tcv.max() <= tc.max() + slack
+        assert dcv.min() >= dc.min() - slack and dcv.max() <= dc.max() + slack
+        wd = eps * el
+        q = rng.uniform(-1.6, 1.6, (40, 2))
+        tq, dq = frame(q)
+        out = (tq < tc.min() - wd) | (tq > tc.max() + wd) | (dq < dc.min() - wd) | (dq > dc.max() + wd)
+        for p in q[out]:
+            ang, bnd, _ = oracle.segment_wn(cps, p, eps=eps, L=L, weights=w)
+            u, v = a - p, b - p
+            chord = math.atan2(u[0] * v[1] - u[1] * v[0], u[0] * v[0] + u[1] * v[1])
+            assert not bnd and abs(ang - chord) <= 1e-12, (i, ang, chord)
+
+
 def pin_errors(L):
     """Inputs that violate the paper's assumptions are rejected."""
     P = TWO_PI
@@ -720,7 +762,7 @@ PLANAR_PINS = [pin_polygon_exact, pin_single_chord, pin_circles, pin_hull_oracle
                pin_classification, pin_config1_integers, pin_table3_shape,
                pin_boundary_fraction]
 RATIONAL_PINS = [pin_rational_circle_arcs, pin_rational_bound, pin_rational_dense_polyline,
-                 pin_rational_invariants]
+                 pin_rational_invariants, pin_control_box_far]
 PERIODIC_PINS = [pin_cylinder_closed_form, pin_torus_bands, pin_lattice_translate,
                  pin_window_enlargement, pin_unfold_3x3, pin_lift_homology, pin_errors]
 ALL_PINS = PLANAR_PINS + RATIONAL_PINS + PERIODIC_PINS
