@@ -36,7 +36,8 @@ def edge_queries(dom, rng, per_edge=6):
     """Points on the box edges of every contractible loop and on the slab
     edges of every extended loop, at the offsets above, in several lattice
     tiles (the library and the oracle reduce them to the base tile)."""
-    P = dom["period_u"]
+    Pu, Pv = dom["period_u"], dom["period_v"]
+    per = np.array([Pu, Pv])
     lifted, hom, _, _ = oracle.domain_info(dom)
     lo = dom["loop_offsets"]
     start = np.concatenate([[0], np.cumsum(dom["degrees"] + 1)])
@@ -49,7 +50,7 @@ def edge_queries(dom, rng, per_edge=6):
             for e in range(4):
                 t = rng.uniform(0, 1, per_edge)
                 d = rng.choice(OFFSETS, per_edge)
-                shift = P * rng.integers(-2, 3, (per_edge, 2))
+                shift = per * rng.integers(-2, 3, (per_edge, 2))
                 if e < 2:
                     x = (x0 if e == 0 else x1) + d
                     y = y0 + t * (y1 - y0)
@@ -58,16 +59,33 @@ def edge_queries(dom, rng, per_edge=6):
                     y = (y0 if e == 2 else y1) + d
                 out.append(np.stack([x, y], axis=1) + shift)
         else:
-            v = np.array([hom[l, 0] * P, hom[l, 1] * P], dtype=np.float64)
+            v = np.array([hom[l, 0] * Pu, hom[l, 1] * Pv], dtype=np.float64)
             vv = float(v @ v)
             s = np.concatenate([cps, cps[:1] + v]) @ v / vv
             nrm = np.array([-v[1], v[0]]) / np.sqrt(vv)
             for edge in (s.min(), s.max()):
                 k = rng.integers(-2, 3, per_edge)
                 d = rng.choice(OFFSETS, per_edge)
-                a = rng.uniform(-P, P, per_edge)
+                a = rng.uniform(-max(Pu, Pv), max(Pu, Pv), per_edge)
                 out.append(((edge + k + d / np.sqrt(vv))[:, None] * v[None, :]) + a[:, None] * nrm[None, :])
     return np.ascontiguousarray(np.concatenate(out, axis=0))
+
+
+@pytest.mark.parametrize("name,prec,tol", [("mixed", 1, TOL_MIXED), ("plain", 0, TOL_PLAIN)])
+def test_cylinder_window_edges(wn, name, prec, tol):
+    """The same on uni-periodic (cylinder) faces: box windows along the
+    periodic axis only, extended curves winding once around it."""
+    rng = ws.rng_for(41)
+    doms = []
+    for f in range(5):
+        lps = ws.uniperiodic_face(rng, 3 + f, (6, 40), P=1.0, degrees=(1, 5))
+        doms.append(ws.make_domain(lps, 1.0, 0.0, eps=1e-9))
+    qr = np.random.default_rng(32)
+    qs = [edge_queries(d, qr) for d in doms]
+    assert sum(len(q) for q in qs) > 300
+    res = run(wn, doms, qs, prec)
+    for d, q, (w, s) in zip(doms, qs, res):
+        compare(d, q, w, s, tol)
 
 
 @pytest.mark.parametrize("name,prec,tol", [("mixed", 1, TOL_MIXED), ("plain", 0, TOL_PLAIN)])
