@@ -38,7 +38,9 @@ struct OutDst {
     unsigned long long *nbound;  // grid boundary counter
 };
 
-// Per-device scratch of the mixed path.
+// Per-device scratch of the mixed path, with the batch tables of the call in
+// place (the tables themselves are owned and sized elsewhere: the API keeps
+// one set per list of domains, the allocation-free query a fixed one).
 struct Work {
     int32_t *acc2 = nullptr;   // 2 * crossings + line halves, per query
     float *theta = nullptr;    // sum of gap angles, per query
@@ -59,9 +61,8 @@ struct Work {
     int4 *bchunks = nullptr;   // (domain, first query, count, 0): runs of one domain's queries
     int n_cells = 0;
     int n_bchunks = 0;
-    int64_t cap_bchunks = 0;
-    int64_t cap_bin_q = 0, cap_cells = 0, cap_dbin = 0, cap_chunk = 0;
-    int64_t cap_q = 0, cap_near = 0, cap_f64 = 0, cap_units = 0, cap_doms = 0, cap_off = 0;
+    int64_t cap_bin_q = 0, cap_cells = 0, cap_chunk = 0;
+    int64_t cap_q = 0, cap_near = 0, cap_f64 = 0;
 };
 
 // Spatial bucketing: at most kBinMaxG x kBinMaxG cells per domain, so that a
