@@ -492,6 +492,62 @@ def pin_unfold_3x3(L, seed=25):
     assert np.max(np.abs(w1[ok] - w2[ok])) < 1e-11
 
 
+def _transpose_loops(loops):
+    """Mirror loops across the diagonal (swap u and v) and reverse them, so
+    that a face periodic in u becomes the same face periodic in v with the
+    same inside (a mirror alone would flip every orientation)."""
+    return [ws.reverse_loop([s[:, ::-1].copy() for s in lp]) for lp in loops]
+
+
+def pin_cylinder_unfold(L, seed=28):
+    """Uni-periodic domains (Sec. 4.3 cylinder case, Alg. 4), period in u
+    only and, mirrored, period in v only.  Contractible star loops placed
+    across the seam plus one strip bounded by two separation loops: for
+    queries in the base tile of the periodic axis, omega equals the planar
+    domain of the stars' copies shifted by -1, 0, +1 periods along that axis
+    (every copy whose box can reach the base tile) plus the strip's
+    indicator (the closed form of the line terms, Eq. 9).  A query off the
+    periodic axis's range, above and below the loops, sees 0 from the stars."""
+    rng = np.random.default_rng(seed)
+    P = 2.0
+    stars = []
+    for j in range(5):
+        # centres near both seams and in the middle; radii keep every box
+        # within one period of the base tile
+        cx = [0.05, P - 0.1, 0.9, 0.02, P - 0.03][j]
+        stars.append(ws.star_loop(rng, (cx, rng.uniform(-0.6, 1.6)), rng.uniform(0.15, 0.45),
+                                  int(rng.integers(8, 15)), int(rng.integers(1, 5)),
+                                  ccw=bool(j % 2 == 0), bend=0.15))
+    strip_lo, strip_hi = 0.25, 0.75
+    a = line_loop((0.3, strip_lo), (P, 0.0), 5)
+    b = ws.reverse_loop(line_loop((1.1, strip_hi), (P, 0.0), 7))
+    unf = [[s + np.array([i * P, 0.0]) for s in lp] for lp in stars for i in (-1, 0, 1)]
+    udom = ws.make_domain(unf, eps=1e-9)
+    q = np.stack([rng.uniform(0, P, 1500), rng.uniform(-1.3, 2.3, 1500)], axis=1)
+    q = q[(np.abs(q[:, 1] - strip_lo) > 1e-3) & (np.abs(q[:, 1] - strip_hi) > 1e-3)]
+    wu, su = oracle.query(udom, q, threads=1, L=L)
+    strip = ((q[:, 1] > strip_lo) & (q[:, 1] < strip_hi)).astype(float)
+    loops = stars + [a, b]
+    for axis in ("u", "v"):
+        if axis == "u":
+            dom = ws.make_domain([wrap(lp, P, 0) for lp in loops], P, 0.0, eps=1e-9)
+            qq = q
+        else:
+            dom = ws.make_domain([wrap(lp, 0, P) for lp in _transpose_loops(loops)], 0.0, P, eps=1e-9)
+            qq = q[:, ::-1].copy()
+        w, st = oracle.query(dom, qq, threads=1, L=L)
+        ok = (su != 2) & (st != 2)
+        assert np.count_nonzero(ok) > 0.9 * len(q), axis
+        assert np.array_equal(st[ok], (wu[ok] + strip[ok] >= 0.5).astype(st.dtype)), axis
+        assert np.max(np.abs(w[ok] - (wu[ok] + strip[ok]))) < 1e-11, (axis, np.max(np.abs(w[ok] - wu[ok] - strip[ok])))
+        # a shift by whole periods along the periodic axis changes nothing
+        sh = qq.copy()
+        sh[:, 0 if axis == "u" else 1] += P * rng.integers(-3, 4, len(qq))
+        w2, st2 = oracle.query(dom, sh, threads=1, L=L)
+        assert np.array_equal(st2[ok], st[ok]), axis
+        assert np.max(np.abs(w2[ok] - w[ok])) < 1e-9, axis
+
+
 def pin_lift_homology(L, seed=26):
     """Lifting reconnects per-segment wrapped loops: each lifted segment
     starts where the previous ended and the homology is the generated
@@ -764,5 +820,5 @@ PLANAR_PINS = [pin_polygon_exact, pin_single_chord, pin_circles, pin_hull_oracle
 RATIONAL_PINS = [pin_rational_circle_arcs, pin_rational_bound, pin_rational_dense_polyline,
                  pin_rational_invariants, pin_control_box_far]
 PERIODIC_PINS = [pin_cylinder_closed_form, pin_torus_bands, pin_lattice_translate,
-                 pin_window_enlargement, pin_unfold_3x3, pin_lift_homology, pin_errors]
+                 pin_window_enlargement, pin_unfold_3x3, pin_cylinder_unfold, pin_lift_homology, pin_errors]
 ALL_PINS = PLANAR_PINS + RATIONAL_PINS + PERIODIC_PINS

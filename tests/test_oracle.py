@@ -59,6 +59,15 @@ MUTANTS = [
      "const double b1 = (double)deg * dall, b2 = (double)deg * dnext;", "rational bound without the weight ratio"),
     ("D->seg[s].W = D->w ? D->w + off : NULL;", "D->seg[s].W = D->w ? D->w : NULL;",
      "first segment's weights for every segment"),
+    ("if (Pu > 0) copies_1d(x, L->box[0], L->box[1], Pu, &ia, &ib);",
+     "if (Pv > 0) copies_1d(x, L->box[0], L->box[1], Pu, &ia, &ib);",
+     "u-cylinder contractible copies gated on the v period (only the i = 0 copy)"),
+    ("if (Pv > 0) copies_1d(y, L->box[2], L->box[3], Pv, &ja, &jb);",
+     "if (Pv > 0 && Pu > 0) copies_1d(y, L->box[2], L->box[3], Pv, &ja, &jb);",
+     "v-cylinder contractible copies skipped (only the j = 0 copy)"),
+    ("if (!(xs >= L->box[0] && xs <= L->box[1])) continue;",
+     "if (!(xs >= L->box[2] && xs <= L->box[3])) continue;",
+     "contractible copy window on the wrong axis's range"),
 ]
 
 # fast pins first, so that most mutants fail within a second
@@ -67,6 +76,7 @@ BATTERY = [pins.pin_single_chord, pins.pin_circles, pins.pin_polygon_exact,
            pins.pin_eval, pins.pin_additivity_elevation_reversal, pins.pin_unit_jump,
            pins.pin_cylinder_closed_form, pins.pin_torus_bands, pins.pin_lift_homology,
            pins.pin_window_enlargement, pins.pin_lattice_translate, pins.pin_unfold_3x3,
+           pins.pin_cylinder_unfold,
            pins.pin_config1_integers, pins.pin_rational_circle_arcs, pins.pin_rational_bound,
            pins.pin_rational_invariants, pins.pin_rational_dense_polyline]
 

@@ -109,6 +109,25 @@ def test_uniperiodic_cylinders(wn, name, prec, tol):
 
 
 @pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_uniperiodic_v_cylinders(wn, name, prec, tol):
+    """Faces periodic in v only (the cylinder case of Sec. 4.3 along the
+    other axis): workload-4-style cylinder faces with u and v exchanged,
+    separation loops along v, contractible stars across the v seam, queries
+    outside the base tile on both axes."""
+    rng = ws.rng_for(41)
+    doms, qs = [], []
+    for f in range(4):
+        lps = ws.uniperiodic_face(rng, 3 + f, (6, 40), P=1.0, degrees=(1, 5))
+        lps = [ws._wrap_segments(lp, 0.0, 1.0) for lp in ws.swap_axes_loops(lps)]
+        doms.append(ws.make_domain(lps, 0.0, 1.0, eps=1e-9))
+        q = np.stack([rng.uniform(-0.1, 1.1, 2300 + 37 * f), rng.uniform(-2, 3, 2300 + 37 * f)], axis=1)
+        qs.append(q)
+    res = run(wn, doms, qs, prec)
+    for d, q, (w, s) in zip(doms, qs, res):
+        compare(d, q, w, s, tol)
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
 def test_workload4_batched_mixed_kinds(wn, name, prec, tol):
     S, Q, kind = ws.config4_sizes()
     pick = list(np.nonzero(kind < 0.1)[0][:6]) + list(np.nonzero((kind >= 0.1) & (kind < 0.2))[0][:6]) + \

@@ -414,6 +414,13 @@ def reverse_loop(segs):
     return [s[::-1].copy() for s in segs[::-1]]
 
 
+def swap_axes_loops(loops):
+    """The same loops with u and v exchanged and each loop reversed: a face
+    periodic in u becomes a face periodic in v with the same inside (the
+    mirror alone would flip every orientation)."""
+    return [reverse_loop([s[:, ::-1].copy() for s in lp]) for lp in loops]
+
+
 HOMOLOGIES = [(1, 0), (0, 1), (1, 1), (1, 2), (2, 1), (2, 3), (3, 2)]
 
 
