@@ -45,9 +45,7 @@ typedef enum {
                              pairing of App. C finds no partner */
     WN_ERR_CUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error) */
     WN_ERR_OOM = 4,       /* device or host allocation failed */
-    WN_ERR_LIMIT = 5,     /* a size exceeds a documented maximum */
-    WN_ERR_DEVICE = 6     /* a kernel reported an error through the device status word
-                             (a bounded wait ran out); results of that call are invalid */
+    WN_ERR_LIMIT = 5      /* a size exceeds a documented maximum */
 } wn_status;
 
 /* out_inside values (Sec. 4.1: classify by omega; on-boundary per Alg. 1). */
@@ -271,7 +269,9 @@ wn_status wn_set_tuning(int32_t tile_queries_per_thread, int32_t sweep_ctas_per_
  * caller's own batch and keeps the fastest for the following calls:
  * coordinate descent from the current setting over queries per sweep thread
  * {1, 2}, sweep CTAs per SM {2, 3, 4, 6}, near-pair CTAs per SM {4, 8, 16},
- * the spatial bucket size {32, 64, 128} queries and bucketing on / off;
+ * the spatial bucket size {32, 64, 128} queries, bucketing on / off, the
+ * FP32 near-walk depth cap {16, 22, 28}, the near-pair draw {64, 128, 256}
+ * and the refill threshold {8, 16, 24} (see wn_set_near_tuning);
  * each candidate runs one
  * warm-up call and `iterations` timed calls (CUDA events on `stream`).
  *   domains, n_domains, point_offsets, points: as in wn_query_batched, with
@@ -284,26 +284,74 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains,
                       const int64_t *point_offsets, const double *points, int32_t iterations,
                       double *best_ms, wn_stream stream);
 
-/* Current tuning: out7 (host int32[7]) = queries per sweep thread, sweep
- * CTAs per SM, near-pair CTAs per SM, graph replay, tree sweep, bucket cell
- * size in queries, spatial bucketing on/off. */
-wn_status wn_get_tuning(int32_t *out7);
+/* Current tuning: the first min(n_out, 10) of (queries per sweep thread,
+ * sweep CTAs per SM, near-pair CTAs per SM, graph replay, tree sweep, bucket
+ * cell size in queries, spatial bucketing on/off, FP32 near-walk depth cap,
+ * near-pair draw, refill threshold) into out (host int32[n_out]). */
+wn_status wn_get_tuning(int32_t *out, int32_t n_out);
 
-/* Counters of the last mixed call on this thread's device, read after the
+/*
+ * Knobs of the FP32 near-pair walk (Alg. 1 on the pairs the sweep could not
+ * settle; 0 keeps the current value):
+ *   depth_cap  12..30: subdivision depth after which a pair's undecided tail
+ *              goes to the FP64 walk.  Lemma 2 bounds the depth a pair needs
+ *              by about log2(B / max(eps, d)) for a query at distance d; a
+ *              lower cap moves more near-curve pairs to FP64, a higher one
+ *              walks longer in FP32 where the error bands may still fail.
+ *              Results do not depend on it (default 22).
+ *   chunk      pairs a warp takes from the queue per atomic, a multiple of
+ *              32 in 32..1024 (default 128).
+ *   refill     idle lanes (1..32) that make a warp load new pairs (default 16).
+ * Errors: WN_ERR_ARG for values outside those ranges.
+ */
+wn_status wn_set_near_tuning(int32_t depth_cap, int32_t chunk, int32_t refill);
+
+/*
+ * Test hook: caps on the near-pair and FP64-pair queues of the mixed path
+ * (0 = the allocated capacity).  A pair that does not fit sends its query to
+ * the FP64 recomputation, as a full queue does, so results do not change;
+ * wn_get_stats reports the pairs that did not fit in `overflow`.
+ */
+wn_status wn_set_queue_limits(int64_t near_pairs, int64_t fp64_pairs);
+
+/* Counters of the last query call on this thread's device, read after the
  * stream is synchronised: queries, near pairs, pairs escalated to FP64,
- * queries recomputed in FP64, near-queue overflows, device error word; and
- * the number of kernels the last query call (mixed or plain) launched. */
+ * queries recomputed in FP64, pairs that did not fit the near or FP64
+ * queue (their queries were recomputed in FP64), FP64 walks that reached
+ * the depth cap of 64 and were reported WN_BOUNDARY (unreachable for points
+ * farther than eps from the curve, Lemma 2); and the number of kernels the
+ * last query call (mixed or plain) launched. */
 typedef struct {
     int64_t queries;
     int64_t near_pairs;
     int64_t fp64_pairs;
     int64_t fp64_queries;
     int64_t overflow;
-    int64_t device_error;
+    int64_t depth_cap;
     int64_t kernels;
 } wn_stats;
 
 wn_status wn_get_stats(wn_stats *out);
+
+/*
+ * The queries the last mixed call on this thread's device recomputed in
+ * FP64 (the classification band or a flag of Sec. 4.1's decision, see
+ * wn_get_stats fp64_queries), for verification: *n_out receives their
+ * number and out_idx (host int64[capacity]) the first min(n, capacity)
+ * query indices of the call (cell indices j*nu + i for a grid), in no
+ * particular order.  Synchronises the device.  Errors: WN_ERR_ARG.
+ */
+wn_status wn_last_escalated(int64_t *out_idx, int64_t capacity, int64_t *n_out);
+
+/*
+ * Verification hook: the FP32 angle the mixed path assigns to a gap between
+ * consecutive segments seen from a query (its share of Eq. 3's chord angles
+ * in the crossing form), out[i] = angle of the vector (x[i], y[i]) in
+ * (-pi, pi].  For |y| <= x / 4 it is the odd series of atan(y / x) to the
+ * t^11 term (remainder below |t|^13 / 13 <= 1.2e-9) in FP32, else atan2f.
+ * y, x, out: DEVICE float[n].  Asynchronous on `stream`.  Errors: WN_ERR_ARG.
+ */
+wn_status wn_eval_gap_angle(const float *y, const float *x, float *out, int64_t n, wn_stream stream);
 
 /*
  * Per-kernel device time of the mixed path, for measurement.  With on != 0
@@ -339,6 +387,15 @@ wn_status wn_set_work_counting(int32_t on);
 wn_status wn_sweep_work(int64_t *out10);
 
 /*
+ * Work tallies of the counting build of the FP32 near-pair walk (enabled by
+ * wn_set_work_counting with the sweep's): wn_near_work writes into out4
+ * (host int64[4]) and clears
+ *   [0] nodes tested with the ellipse of Eq. 5   [1] nodes accepted as far
+ *   [2] evaluations of gamma(m)                  [3] sum of their degrees
+ */
+wn_status wn_near_work(int64_t *out4);
+
+/*
  * wn_query_noalloc -- the WN_PREC_MIXED query of wn_query for one domain,
  * without any memory allocation.  (The paper has no counterpart: this is a
  * deployment variant of the same computation.)
@@ -349,10 +406,18 @@ wn_status wn_sweep_work(int64_t *out10);
  * that forbid allocation once they have started, and processes held to a
  * fixed device-memory budget.  This entry point keeps all of its scratch
  * (per-query accumulators, the near-pair and FP64 queues, the work list)
- * in one fixed-size device array that is part of the library image: every
- * process that loads the library holds it (about 12.3 MB) on each device it
- * uses, until it exits.  The call itself makes no cudaMalloc, cudaFree or
- * other allocating call.
+ * in one fixed-size device array that is part of the library image (about
+ * 12.3 MB per device).  The library is built without relocatable device
+ * code and CUDA loads modules lazily by default, so the array and the
+ * kernels' code are placed on a device when the FIRST call on that device
+ * loads them; that call also launches every kernel a call can use once on
+ * an empty work list (loading its code and reserving its local memory), so
+ * it may allocate device memory implicitly.
+ * Make it at start-up (n = 0 is enough: it does the set-up and returns),
+ * outside allocator callbacks and stream capture, or run the process with
+ * CUDA_MODULE_LOADING=EAGER; from then on the process holds the array until
+ * it exits, and later calls make no cudaMalloc, cudaFree or other
+ * allocating call.
  *
  *   domain       from wn_create_domain (not modified).
  *   points       DEVICE double[2n], x,y interleaved, 16-byte aligned.
@@ -362,16 +427,20 @@ wn_status wn_sweep_work(int64_t *out10);
  *                (same meaning as in wn_query).
  *   stream       all work is queued on this stream; the call is asynchronous.
  *
- * Results equal wn_query(..., WN_PREC_MIXED, ...) on the same inputs.
+ * Results: the same WN_OUTSIDE / WN_INSIDE / WN_BOUNDARY states as
+ * wn_query(..., WN_PREC_MIXED, ...) on the same inputs, and windings within
+ * the mixed path's tolerance of its windings (this call runs a fixed launch
+ * shape without spatial bucketing, so warps group the queries differently).
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  Every call on a device shares the one array, and each call
  * re-initialises what it needs, so calls that may overlap on the GPU (on
  * different streams without ordering between them) race and give wrong
  * results: order them on one stream, or with events.
- * Errors: WN_ERR_ARG (NULL domain, n < 0, host or misaligned pointers),
- * WN_ERR_LIMIT (n too large), WN_ERR_CUDA.  No message is recorded for
- * wn_last_error (recording one could allocate host memory).
+ * Errors: WN_ERR_ARG (NULL domain, n < 0, host or misaligned pointers, a
+ * domain created on another device than the current one), WN_ERR_LIMIT (n
+ * too large), WN_ERR_CUDA.  No message is recorded for wn_last_error
+ * (recording one could allocate host memory).
  */
 #define WN_NOALLOC_MAX_QUERIES 65536
 wn_status wn_query_noalloc(const wn_domain *domain, const double *points, int64_t n,

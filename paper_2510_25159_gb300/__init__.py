@@ -23,7 +23,7 @@ PLAIN_FP64, MIXED = 0, 1
 MAX_DEGREE = 7
 
 _STATUS = {0: "WN_OK", 1: "WN_ERR_ARG", 2: "WN_ERR_TOPOLOGY", 3: "WN_ERR_CUDA", 4: "WN_ERR_OOM",
-           5: "WN_ERR_LIMIT", 6: "WN_ERR_DEVICE"}
+           5: "WN_ERR_LIMIT"}
 _lib = None
 
 
@@ -36,7 +36,7 @@ class WnError(RuntimeError):
 class WnStats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
                 ("fp64_pairs", ctypes.c_int64), ("fp64_queries", ctypes.c_int64),
-                ("overflow", ctypes.c_int64), ("device_error", ctypes.c_int64),
+                ("overflow", ctypes.c_int64), ("depth_cap", ctypes.c_int64),
                 ("kernels", ctypes.c_int64)]
 
 
@@ -74,14 +74,21 @@ def lib():
         L.wn_query_noalloc.argtypes = [P, P, I64, P, P, P]
         L.wn_query_noalloc.restype = ctypes.c_int
         L.wn_autotune.argtypes = [P, I32, P, P, I32, P, P]
-        L.wn_get_tuning.argtypes = [P]
+        L.wn_get_tuning.argtypes = [P, I32]
+        L.wn_set_near_tuning.argtypes = [I32, I32, I32]
+        L.wn_set_queue_limits.argtypes = [I64, I64]
+        L.wn_near_work.argtypes = [P]
+        L.wn_last_escalated.argtypes = [P, I64, P]
+        L.wn_eval_gap_angle.argtypes = [P, P, P, I64, P]
         L.wn_set_profiling.argtypes = [I32]
         L.wn_kernel_times.argtypes = [P, P]
         L.wn_set_work_counting.argtypes = [I32]
         L.wn_sweep_work.argtypes = [P]
         for f in ("wn_create_domain", "wn_create_domain_rational", "wn_query", "wn_query_batched", "wn_query_grid_bitmask",
                   "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times", "wn_autotune",
-                  "wn_get_tuning", "wn_set_work_counting", "wn_sweep_work"):
+                  "wn_get_tuning", "wn_set_work_counting", "wn_sweep_work", "wn_set_near_tuning",
+                  "wn_set_queue_limits", "wn_near_work", "wn_last_escalated",
+                  "wn_eval_gap_angle"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -201,12 +208,13 @@ def query_batched(domains, points, offsets, precision=MIXED, out_winding=None, o
     return out_winding, out_inside
 
 
-def query_grid_bitmask(domain, nu, nv, precision=MIXED, stream=None):
-    """Inside/boundary bitmask of the nu x nv cell-centre grid (device)."""
+def query_grid_bitmask(domain, nu, nv, precision=MIXED, stream=None, out_bits=None, out_boundary=None):
+    """Inside/boundary bitmask of the nu x nv cell-centre grid (device);
+    returns (bits, boundary count), into the given buffers when passed."""
     import torch
     words = (nu * nv + 31) // 32
-    bits = torch.empty(words, dtype=torch.int32, device="cuda")
-    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    bits = torch.empty(words, dtype=torch.int32, device="cuda") if out_bits is None else out_bits
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda") if out_boundary is None else out_boundary
     _check(lib().wn_query_grid_bitmask(domain.handle, int(nu), int(nv), _ptr(bits), _ptr(nb),
                                        int(precision), _stream(stream)))
     return bits, nb
@@ -265,16 +273,46 @@ def autotune(domains, points, offsets, iterations=3, stream=None):
     return float(ms[0]), get_tuning()
 
 
+TUNING = ("qpt", "sweep_ctas_per_sm", "near_ctas_per_sm", "use_graph", "tree", "cell_q", "bucket",
+          "near_depth", "near_chunk", "near_refill")
+
+
 def get_tuning():
-    t = np.zeros(7, dtype=np.int32)
-    _check(lib().wn_get_tuning(_ptr(t)))
-    return dict(zip(["qpt", "sweep_ctas_per_sm", "near_ctas_per_sm", "use_graph", "tree", "cell_q", "bucket"],
-                    t.tolist()))
+    t = np.zeros(len(TUNING), dtype=np.int32)
+    _check(lib().wn_get_tuning(_ptr(t), len(TUNING)))
+    return dict(zip(TUNING, t.tolist()))
+
+
+def set_near_tuning(depth_cap=0, chunk=0, refill=0):
+    """FP32 near-walk depth cap (12..30), pairs drawn per atomic (multiple of
+    32 in 32..1024) and refill threshold (1..32); 0 keeps a value."""
+    _check(lib().wn_set_near_tuning(int(depth_cap), int(chunk), int(refill)))
+
+
+def set_queue_limits(near_pairs=0, fp64_pairs=0):
+    """Test hook: cap the near-pair and FP64-pair queues (0 = no cap)."""
+    _check(lib().wn_set_queue_limits(int(near_pairs), int(fp64_pairs)))
 
 
 def set_tuning(qpt=0, sweep_ctas_per_sm=0, near_ctas_per_sm=0, use_graph=-1, tree=-1, bucket=-1):
     _check(lib().wn_set_tuning(int(qpt), int(sweep_ctas_per_sm), int(near_ctas_per_sm), int(use_graph),
                                int(tree), int(bucket)))
+
+
+def eval_gap_angle(y, x, stream=None):
+    """The mixed path's FP32 gap angle of (x, y) (device float32 tensors)."""
+    import torch
+    out = torch.empty_like(x)
+    _check(lib().wn_eval_gap_angle(_ptr(y), _ptr(x), _ptr(out), int(x.numel()), _stream(stream)))
+    return out
+
+
+def last_escalated(capacity=1 << 22):
+    """Query indices the last mixed call recomputed in FP64 (numpy int64)."""
+    out = np.zeros(max(int(capacity), 1), dtype=np.int64)
+    n = np.zeros(1, dtype=np.int64)
+    _check(lib().wn_last_escalated(_ptr(out), int(capacity), _ptr(n)))
+    return out[:min(int(n[0]), int(capacity))]
 
 
 def stats():
@@ -314,6 +352,16 @@ def sweep_work():
     c = np.zeros(len(WORK), dtype=np.int64)
     _check(lib().wn_sweep_work(_ptr(c)))
     return dict(zip(WORK, c.tolist()))
+
+
+NEAR_WORK = ("near_nodes", "near_far", "near_evals", "near_eval_degrees")
+
+
+def near_work():
+    """Work tallies of the FP32 near walk since the last read (see NEAR_WORK)."""
+    c = np.zeros(len(NEAR_WORK), dtype=np.int64)
+    _check(lib().wn_near_work(_ptr(c)))
+    return dict(zip(NEAR_WORK, c.tolist()))
 
 
 def version():

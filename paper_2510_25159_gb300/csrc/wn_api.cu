@@ -17,6 +17,10 @@ namespace {
 thread_local std::string g_err;
 std::mutex g_mu;
 Tuning g_tun;
+// Test hook: upper limits on the near-pair and FP64-pair queues (0: the
+// allocated capacity).  Pairs beyond a limit send their query to the FP64
+// recomputation, exactly as a full queue does.
+int64_t g_lim_near = 0, g_lim_f64 = 0;
 
 // Batch tables of one list of domains (see build_tables).
 struct Tables {
@@ -38,6 +42,7 @@ struct Tables {
 // and costs about kGroupCostMs per extra group (the latency-bound tails of
 // each group's kernels), so G = sqrt(C / kGroupCostMs), at most kMaxGroups.
 constexpr int kMaxGroups = 8;
+constexpr int kMaxGraphs = 256;
 constexpr int64_t kGroupMinQueries = 1 << 21;
 constexpr double kGroupCostMs = 0.3;
 constexpr double kCopyMsPerQuery = 25.0 / 200e9 * 1e3;
@@ -71,10 +76,11 @@ struct DevState {
     // work tallies of the counting build of the tree sweep
     bool counting = false;
     unsigned long long *d_work = nullptr;
-    // CUDA graph of the last captured mixed call, replayed while its launch
-    // parameters (batch layout, buffers, stream, tuning) are unchanged
-    std::vector<uintptr_t> graph_key;
-    cudaGraphExec_t graph_exec = nullptr;
+    // CUDA graphs of captured mixed calls, each replayed while its launch
+    // parameters (batch layout, buffers, stream, tuning) recur; at most
+    // kMaxGraphs, the oldest dropped first (a tessellation run replays one
+    // graph per face)
+    std::vector<std::pair<std::vector<uintptr_t>, cudaGraphExec_t>> graphs;
     int64_t graph_launches = 0;
 };
 DevState g_dev[64];
@@ -84,10 +90,9 @@ DevState g_dev[64];
 void drop_graphs()
 {
     for (DevState &S : g_dev)
-        if (S.graph_exec) {
-            cudaGraphExecDestroy(S.graph_exec);
-            S.graph_exec = nullptr;
-            S.graph_key.clear();
+        if (!S.graphs.empty()) {
+            for (auto &g : S.graphs) cudaGraphExecDestroy(g.second);
+            S.graphs.clear();
         }
 }
 
@@ -173,8 +178,17 @@ cudaError_t ensure_work(Work &W, int64_t n, int64_t near_expected)
         W.cap_q = nq;
     }
     // near pairs: 3 per query or twice the expected count, whichever is more
-    // (an overflowing pair sends its query to the FP64 recomputation)
-    const int64_t need_near = std::max<int64_t>(std::max<int64_t>(1 << 22, 3 * nq), 2 * near_expected);
+    // (an overflowing pair sends its query to the FP64 recomputation), but
+    // at most a quarter of the free device memory: a smaller queue only
+    // moves the pairs that do not fit to that recomputation
+    int64_t need_near = std::max<int64_t>(std::max<int64_t>(1 << 22, 3 * nq), 2 * near_expected);
+    if (need_near > W.cap_near) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const int64_t room = (int64_t)(free_b / 4 / sizeof(Item)) + W.cap_near;
+            need_near = std::max<int64_t>(std::min(need_near, room), std::min<int64_t>(need_near, 1 << 22));
+        }
+    }
     if ((e = grow(W.near_items, W.cap_near, need_near)) != cudaSuccess) return e;
     const int64_t need_f64 = std::max<int64_t>(1 << 18, nq / 8);
     if ((e = grow(W.f64_items, W.cap_f64, need_f64)) != cudaSuccess) return e;
@@ -260,6 +274,31 @@ wn_status wn_set_tuning(int32_t qpt, int32_t sweep_ctas_per_sm, int32_t near_cta
     if (use_graph >= 0) g_tun.use_graph = use_graph;
     if (tree >= 0) g_tun.tree = tree != 0;
     if (bucket >= 0) g_tun.bucket = bucket != 0;
+    return WN_OK;
+}
+
+wn_status wn_set_near_tuning(int32_t depth_cap, int32_t chunk, int32_t refill)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (depth_cap != 0 && (depth_cap < kDepthCap32Min || depth_cap > kDepthCap32Max))
+        return fail(WN_ERR_ARG, "depth_cap outside 12..30");
+    if (chunk != 0 && (chunk < kNearChunkMin || chunk > kNearChunkMax || (chunk & 31)))
+        return fail(WN_ERR_ARG, "chunk must be a multiple of 32 in 32..1024");
+    if (refill != 0 && (refill < 1 || refill > 32)) return fail(WN_ERR_ARG, "refill outside 1..32");
+    drop_graphs();
+    if (depth_cap) g_tun.near_depth = depth_cap;
+    if (chunk) g_tun.near_chunk = chunk;
+    if (refill) g_tun.near_refill = refill;
+    return WN_OK;
+}
+
+wn_status wn_set_queue_limits(int64_t near_pairs, int64_t fp64_pairs)
+{
+    if (near_pairs < 0 || fp64_pairs < 0) return fail(WN_ERR_ARG, "limits must be >= 0");
+    std::lock_guard<std::mutex> lk(g_mu);
+    drop_graphs();
+    g_lim_near = near_pairs;
+    g_lim_f64 = fp64_pairs;
     return WN_OK;
 }
 
@@ -350,10 +389,13 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
     return WN_OK;
 }
 
-// The shared scratch with one list's tables in place.
+// The shared scratch with one list's tables in place (queue capacities cut
+// to the test limits, when set).
 static Work work_with(const DevState *S, const Tables &T)
 {
     Work W = S->W;
+    if (g_lim_near > 0) W.cap_near = std::min(W.cap_near, g_lim_near);
+    if (g_lim_f64 > 0) W.cap_f64 = std::min(W.cap_f64, g_lim_f64);
     W.units = T.units;
     W.doms = T.doms;
     W.offsets = T.offsets;
@@ -381,8 +423,12 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
     if (precision != WN_PREC_PLAIN_FP64 && precision != WN_PREC_MIXED)
         return fail(WN_ERR_ARG, "precision must be WN_PREC_PLAIN_FP64 or WN_PREC_MIXED");
     if (offsets[0] != 0) return fail(WN_ERR_ARG, "point_offsets[0] must be 0");
+    int cur_dev = 0;
+    if (cudaGetDevice(&cur_dev) != cudaSuccess) return fail(WN_ERR_CUDA, "cudaGetDevice failed");
     for (int d = 0; d < n_domains; d++) {
         if (!domains[d]) return fail(WN_ERR_ARG, "NULL domain");
+        if (domains[d]->device != cur_dev)
+            return fail(WN_ERR_ARG, "a domain was created on another device than the current one");
         if (offsets[d + 1] < offsets[d]) return fail(WN_ERR_ARG, "point_offsets must be non-decreasing");
     }
     const int64_t n = offsets[n_domains];
@@ -449,10 +495,12 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             return cuda_fail(e, "memset bits");
         if (nbound && (e = cudaMemsetAsync(nbound, 0, 8, stream)) != cudaSuccess)
             return cuda_fail(e, "memset");
+        if ((e = cudaMemsetAsync(S->W.counters, 0, CNT_N * sizeof(unsigned long long), stream)) != cudaSuccess)
+            return cuda_fail(e, "memset");
         int64_t kernels = 0;
         for (int d = 0; d < n_domains; d++) {
             const int64_t q0 = offsets[d], cnt = offsets[d + 1] - offsets[d];
-            if ((e = launch_plain(domains[d]->d_self, q0, cnt, src, out, stream)) != cudaSuccess)
+            if ((e = launch_plain(domains[d]->d_self, q0, cnt, src, out, S->W.counters, stream)) != cudaSuccess)
                 return cuda_fail(e, "plain kernel");
             kernels += cnt > 0 ? 1 : 0;
         }
@@ -569,12 +617,21 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                                          (uintptr_t)T.key, (uintptr_t)g_tun.sweep_ctas_per_sm,
                                          (uintptr_t)g_tun.near_ctas_per_sm, (uintptr_t)g_tun.bucket,
                                          (uintptr_t)S->W.acc2, (uintptr_t)S->W.near_items, (uintptr_t)S->W.perm,
-                                         (uintptr_t)T.units, (uintptr_t)S->W.cell_cnt, (uintptr_t)T.bchunks};
+                                         (uintptr_t)T.units, (uintptr_t)S->W.cell_cnt, (uintptr_t)T.bchunks,
+                                         (uintptr_t)g_tun.near_depth, (uintptr_t)g_tun.near_chunk,
+                                         (uintptr_t)g_tun.near_refill, (uintptr_t)Wl.cap_near,
+                                         (uintptr_t)Wl.cap_f64};
             for (int d = 0; d < n_domains; d++) gk.push_back((uintptr_t)domains[d]);
-            if (!S->graph_exec || gk != S->graph_key) {
-                if (S->graph_exec) {
-                    cudaGraphExecDestroy(S->graph_exec);
-                    S->graph_exec = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            for (auto &g : S->graphs)
+                if (g.first == gk) {
+                    exec = g.second;
+                    break;
+                }
+            if (!exec) {
+                if (S->graphs.size() >= (size_t)kMaxGraphs) {
+                    cudaGraphExecDestroy(S->graphs.front().second);
+                    S->graphs.erase(S->graphs.begin());
                 }
                 cudaGraph_t g = nullptr;
                 if ((e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
@@ -585,15 +642,12 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                     if (g) cudaGraphDestroy(g);
                     return cuda_fail(e != cudaSuccess ? e : e2, "capture");
                 }
-                e = cudaGraphInstantiate(&S->graph_exec, g, 0);
+                e = cudaGraphInstantiate(&exec, g, 0);
                 cudaGraphDestroy(g);
-                if (e != cudaSuccess) {
-                    S->graph_exec = nullptr;
-                    return cuda_fail(e, "graph instantiate");
-                }
-                S->graph_key = gk;
+                if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+                S->graphs.push_back({gk, exec});
             }
-            if ((e = cudaGraphLaunch(S->graph_exec, stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+            if ((e = cudaGraphLaunch(exec, stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
             S->graph_launches++;
         } else if ((e = launch_mixed(Wl, d_doms, n_domains, T.units, T.n_units, T.offsets, n, src, out, cfg,
                                      stream)) != cudaSuccess) {
@@ -704,15 +758,26 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains, const 
     };
     double best_t = 0.0;
     wn_status r = trial(best, best_t);
-    const int qpts[] = {1, 2}, sweeps[] = {2, 3, 4, 6}, nears[] = {4, 8, 16}, cells[] = {32, 64, 128},
-              buckets[] = {1, 0};
-    for (int knob = 0; knob < 5 && r == WN_OK; knob++) {
-        const int *vals = knob == 0 ? qpts : knob == 1 ? sweeps : knob == 2 ? nears : knob == 3 ? cells : buckets;
-        const int nv = (knob == 0 || knob == 4) ? 2 : knob == 1 ? 4 : 3;
-        for (int i = 0; i < nv && r == WN_OK; i++) {
+    // coordinate descent, one knob at a time from the current best
+    struct Knob {
+        int Tuning::*field;
+        int n;
+        int vals[4];
+    };
+    const Knob knobs[] = {{&Tuning::qpt, 2, {1, 2}},
+                          {&Tuning::sweep_ctas_per_sm, 4, {2, 3, 4, 6}},
+                          {&Tuning::near_ctas_per_sm, 3, {4, 8, 16}},
+                          {&Tuning::cell_q, 3, {32, 64, 128}},
+                          {&Tuning::bucket, 2, {1, 0}},
+                          {&Tuning::near_depth, 3, {16, 22, 28}},
+                          {&Tuning::near_chunk, 3, {64, 128, 256}},
+                          {&Tuning::near_refill, 3, {8, 16, 24}}};
+    for (const Knob &kb : knobs) {
+        if (r != WN_OK) break;
+        for (int i = 0; i < kb.n && r == WN_OK; i++) {
             Tuning t = best;
-            int &field = knob == 0 ? t.qpt : knob == 1 ? t.sweep_ctas_per_sm : knob == 2 ? t.near_ctas_per_sm
-                       : knob == 3 ? t.cell_q : t.bucket;
+            int &field = t.*(kb.field);
+            const int *vals = kb.vals;
             if (field == vals[i]) continue;
             field = vals[i];
             double ms = 0.0;
@@ -737,17 +802,14 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains, const 
     return r;
 }
 
-wn_status wn_get_tuning(int32_t *out7)
+wn_status wn_get_tuning(int32_t *out, int32_t n_out)
 {
-    if (!out7) return fail(WN_ERR_ARG, "out is NULL");
+    if (!out || n_out < 0) return fail(WN_ERR_ARG, "out is NULL or n_out < 0");
     std::lock_guard<std::mutex> lk(g_mu);
-    out7[0] = g_tun.qpt;
-    out7[1] = g_tun.sweep_ctas_per_sm;
-    out7[2] = g_tun.near_ctas_per_sm;
-    out7[3] = g_tun.use_graph;
-    out7[4] = g_tun.tree;
-    out7[5] = g_tun.cell_q;
-    out7[6] = g_tun.bucket;
+    const int32_t v[10] = {g_tun.qpt, g_tun.sweep_ctas_per_sm, g_tun.near_ctas_per_sm, g_tun.use_graph,
+                           g_tun.tree, g_tun.cell_q, g_tun.bucket, g_tun.near_depth, g_tun.near_chunk,
+                           g_tun.near_refill};
+    for (int i = 0; i < n_out && i < 10; i++) out[i] = v[i];
     return WN_OK;
 }
 
@@ -783,9 +845,10 @@ wn_status wn_set_work_counting(int32_t on)
     return WN_OK;
 }
 
-wn_status wn_sweep_work(int64_t *out10)
+// Read tallies [first, first + count) of the counting builds and clear them.
+static wn_status read_work(int first, int count, int64_t *out)
 {
-    if (!out10) return fail(WN_ERR_ARG, "out10 is NULL");
+    if (!out) return fail(WN_ERR_ARG, "out is NULL");
     std::lock_guard<std::mutex> lk(g_mu);
     wn_status st;
     DevState *S = dev_state(st);
@@ -793,13 +856,19 @@ wn_status wn_sweep_work(int64_t *out10)
     unsigned long long c[WK_N] = {};
     cudaError_t e;
     if (S->d_work) {
-        if ((e = cudaMemcpy(c, S->d_work, sizeof c, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        if ((e = cudaMemcpy(c, S->d_work + first, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost)) !=
+            cudaSuccess)
             return cuda_fail(e, "read work tallies");
-        if ((e = cudaMemset(S->d_work, 0, sizeof c)) != cudaSuccess) return cuda_fail(e, "work tallies");
+        if ((e = cudaMemset(S->d_work + first, 0, count * sizeof(unsigned long long))) != cudaSuccess)
+            return cuda_fail(e, "work tallies");
     }
-    for (int i = 0; i < WK_N; i++) out10[i] = (int64_t)c[i];
+    for (int i = 0; i < count; i++) out[i] = (int64_t)c[i];
     return WN_OK;
 }
+
+wn_status wn_sweep_work(int64_t *out10) { return read_work(0, WK_SWEEP_N, out10); }
+
+wn_status wn_near_work(int64_t *out4) { return read_work(WK_NEAR_NODE, WK_N - WK_NEAR_NODE, out4); }
 
 wn_status wn_kernel_times(double *ms6, int64_t *n_calls)
 {
@@ -827,6 +896,38 @@ wn_status wn_kernel_times(double *ms6, int64_t *n_calls)
     return WN_OK;
 }
 
+wn_status wn_eval_gap_angle(const float *y, const float *x, float *out, int64_t n, wn_stream stream)
+{
+    if (n < 0) return fail(WN_ERR_ARG, "n < 0");
+    if (n == 0) return WN_OK;
+    if (!y || !x || !out || !is_device_ptr(y) || !is_device_ptr(x) || !is_device_ptr(out))
+        return fail(WN_ERR_ARG, "y, x and out must be device memory");
+    cudaError_t e = launch_gap_angle(y, x, out, n, (cudaStream_t)stream);
+    return e == cudaSuccess ? WN_OK : cuda_fail(e, "gap angle kernel");
+}
+
+wn_status wn_last_escalated(int64_t *out_idx, int64_t capacity, int64_t *n_out)
+{
+    if (!n_out || capacity < 0 || (capacity > 0 && !out_idx)) return fail(WN_ERR_ARG, "bad output buffer");
+    std::lock_guard<std::mutex> lk(g_mu);
+    wn_status st;
+    DevState *S = dev_state(st);
+    if (!S) return st;
+    unsigned long long c[CNT_N];
+    cudaError_t e = cudaMemcpy(c, S->W.counters, sizeof c, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read counters");
+    const int64_t n = std::min<int64_t>((int64_t)c[CNT_ESC], S->W.cap_q);
+    *n_out = n;
+    const int64_t m = std::min(n, capacity);
+    if (m > 0) {
+        std::vector<uint2> v((size_t)m);
+        if ((e = cudaMemcpy(v.data(), S->W.esc_q, m * sizeof(uint2), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "read escalated queries");
+        for (int64_t i = 0; i < m; i++) out_idx[i] = (int64_t)v[i].x;
+    }
+    return WN_OK;
+}
+
 wn_status wn_get_stats(wn_stats *out)
 {
     if (!out) return fail(WN_ERR_ARG, "out is NULL");
@@ -841,8 +942,11 @@ wn_status wn_get_stats(wn_stats *out)
     out->near_pairs = c[CNT_NEAR];
     out->fp64_pairs = c[CNT_F64];
     out->fp64_queries = c[CNT_ESC];
-    out->overflow = (c[CNT_NEAR] > (unsigned long long)S->W.cap_near) ? (int64_t)(c[CNT_NEAR] - S->W.cap_near) : 0;
-    out->device_error = c[CNT_ERR];
+    const int64_t cap_near = g_lim_near > 0 ? std::min(S->W.cap_near, g_lim_near) : S->W.cap_near;
+    const int64_t cap_f64 = g_lim_f64 > 0 ? std::min(S->W.cap_f64, g_lim_f64) : S->W.cap_f64;
+    out->overflow = ((c[CNT_NEAR] > (unsigned long long)cap_near) ? (int64_t)(c[CNT_NEAR] - cap_near) : 0) +
+                    ((c[CNT_F64] > (unsigned long long)cap_f64) ? (int64_t)(c[CNT_F64] - cap_f64) : 0);
+    out->depth_cap = c[CNT_DEPTH];
     out->kernels = S->last.kernels;
     return WN_OK;
 }

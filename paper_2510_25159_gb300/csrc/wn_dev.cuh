@@ -22,7 +22,9 @@ namespace wn {
 constexpr int kMaxDeg = 7;
 constexpr int kNcp = kMaxDeg + 1;
 constexpr int kDepthCap64 = 64;   // FP64 recursion cap: reported as BOUNDARY
-constexpr int kDepthCap32 = 22;   // FP32 recursion cap: the pair goes to FP64
+constexpr int kDepthCap32Max = 30;  // largest FP32 recursion cap: the pair then goes to FP64
+// What an FP64 walk of Algorithm 1 ended in.
+enum : int { WALK_DONE = 0, WALK_BOUNDARY = 1, WALK_DEPTH = 2 };
 
 enum : int { DK_PLANAR = 0, DK_UNI_U = 1, DK_UNI_V = 2, DK_BI = 3 };
 enum : int { IT_ALL = 0, IT_BOX = 1, IT_PE = 2, IT_LINE = 3 };
@@ -482,10 +484,10 @@ struct FarCross {
 
 // Algorithm 1 over [0,1] of one segment, query (px,py), in FP64.  Points are
 // handled relative to p after evaluation in absolute coordinates.  Returns
-// true when the query is on the boundary (an evaluated point closer than eps,
-// or the depth cap).
+// WALK_BOUNDARY when an evaluated point is closer than eps, WALK_DEPTH at the
+// depth cap (both mean the query is on the boundary), else WALK_DONE.
 template <class Far>
-__device__ bool alg1_fp64(const double *P, const double *Wt, int n, int nmax, double B, double px, double py,
+__device__ int alg1_fp64(const double *P, const double *Wt, int n, int nmax, double B, double px, double py,
                           double eps, Far &far)
 {
     SegF64 sg;              // loaded at the first evaluation: most segments are far at the root
@@ -505,14 +507,14 @@ __device__ bool alg1_fp64(const double *P, const double *Wt, int n, int nmax, do
         double b = st_t[sp - 1], bx = st_x[sp - 1], by = st_y[sp - 1];
         int d = st_d[sp - 1];
         double rb = sqrt(bx * bx + by * by);
-        if (ra < eps || rb < eps) return true;
+        if (ra < eps || rb < eps) return WALK_BOUNDARY;
         if (ra + rb > B * (b - a)) {
             far.chord(ax, ay, bx, by);
             a = b; ax = bx; ay = by; ra = rb;
             sp--;
             continue;
         }
-        if (d >= kDepthCap64) return true;
+        if (d >= kDepthCap64) return WALK_DEPTH;
         if (!loaded) {
             sg.load(P, Wt, n, nmax);
             loaded = true;
@@ -523,7 +525,7 @@ __device__ bool alg1_fp64(const double *P, const double *Wt, int n, int nmax, do
         st_t[sp] = m; st_x[sp] = mx - px; st_y[sp] = my - py; st_d[sp] = d + 1;
         sp++;
     }
-    return false;
+    return WALK_DONE;
 }
 
 // Algorithm 1 in FP64 on the sub-interval [a0, b0] of a polynomial segment
@@ -541,7 +543,7 @@ __device__ bool alg1_fp64(const double *P, const double *Wt, int n, int nmax, do
 //     4 ra^2 rb^2 > S^2 (both sides of ra + rb > L are non-negative).
 // Each decision is the exact one up to FP64 rounding of its operands.
 template <int NM>
-__device__ __noinline__ bool alg1_fp64_sub_pow(const double *P, int n, double B, double px, double py,
+__device__ __noinline__ int alg1_fp64_sub_pow(const double *P, int n, double B, double px, double py,
                                                   double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
 {
     double cx[NM + 1], cy[NM + 1];
@@ -600,7 +602,7 @@ __device__ __noinline__ bool alg1_fp64_sub_pow(const double *P, int n, double B,
         by = st_y[sp - 1];
         const int d = st_d[sp - 1];
         const double qb = bx * bx + by * by;
-        if (qa < eps2 || qb < eps2) return true;
+        if (qa < eps2 || qb < eps2) return WALK_BOUNDARY;
         const bool sb = (b == b0) ? sb0 : (by > 0.0);
         const double L = B * (b - a);
         const double S = L * L - (qa + qb);
@@ -614,7 +616,7 @@ __device__ __noinline__ bool alg1_fp64_sub_pow(const double *P, int n, double B,
             sp--;
             continue;
         }
-        if (d >= kDepthCap64) return true;
+        if (d >= kDepthCap64) return WALK_DEPTH;
         const double m = 0.5 * (a + b);
         double mx, my;
         eval(m, mx, my);
@@ -622,7 +624,7 @@ __device__ __noinline__ bool alg1_fp64_sub_pow(const double *P, int n, double B,
         st_t[sp] = m; st_x[sp] = mx; st_y[sp] = my; st_d[sp] = d + 1;
         sp++;
     }
-    return false;
+    return WALK_DONE;
 }
 
 // The same walk for a rational segment (weights w_i > 0): gamma(t) - p =
@@ -632,7 +634,7 @@ __device__ __noinline__ bool alg1_fp64_sub_pow(const double *P, int n, double B,
 // eps and far tests are those of the polynomial walk multiplied through by
 // the squared weights (|Q|^2 = |gamma - p|^2 W^2), so no node divides.
 template <int NM>
-__device__ __noinline__ bool alg1_fp64_sub_rpow(const double *P, const double *Wt, int n, double B, double px,
+__device__ __noinline__ int alg1_fp64_sub_rpow(const double *P, const double *Wt, int n, double B, double px,
                                                 double py, double eps, double a0, double b0, bool sa0, bool sb0,
                                                 int &cnt)
 {
@@ -699,7 +701,7 @@ __device__ __noinline__ bool alg1_fp64_sub_rpow(const double *P, const double *W
         bw = st_w[sp - 1];
         const int d = st_d[sp - 1];
         const double nb = bx * bx + by * by, wb2 = bw * bw;
-        if (na < eps2 * wa2 || nb < eps2 * wb2) return true;
+        if (na < eps2 * wa2 || nb < eps2 * wb2) return WALK_BOUNDARY;
         const bool sb = (b == b0) ? sb0 : (by > 0.0);
         const double L = B * (b - a);
         const double S = L * L * wa2 * wb2 - (na * wb2 + nb * wa2);
@@ -713,7 +715,7 @@ __device__ __noinline__ bool alg1_fp64_sub_rpow(const double *P, const double *W
             sp--;
             continue;
         }
-        if (d >= kDepthCap64) return true;
+        if (d >= kDepthCap64) return WALK_DEPTH;
         const double m = 0.5 * (a + b);
         double mx, my, mw;
         eval(m, mx, my, mw);
@@ -721,14 +723,15 @@ __device__ __noinline__ bool alg1_fp64_sub_rpow(const double *P, const double *W
         st_t[sp] = m; st_x[sp] = mx; st_y[sp] = my; st_w[sp] = mw; st_d[sp] = d + 1;
         sp++;
     }
-    return false;
+    return WALK_DONE;
 }
 
 // Algorithm 1 in FP64 on the sub-interval [a0, b0] of one segment, adding
 // the signed crossings of the +x ray from (px, py) by its chords; the end
 // points take the given signs (those of the FP32 chain around it).
-// Returns true when the query is on the boundary.
-__device__ inline bool alg1_fp64_sub(const double *P, const double *Wt, int n, int nmax, double B, double px,
+// Returns WALK_DONE, or WALK_BOUNDARY / WALK_DEPTH when the query is on the
+// boundary.
+__device__ inline int alg1_fp64_sub(const double *P, const double *Wt, int n, int nmax, double B, double px,
                                      double py, double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
 {
     if (!Wt) {

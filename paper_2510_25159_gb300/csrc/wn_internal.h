@@ -71,7 +71,10 @@ constexpr int kBinMaxG = 110;
 constexpr int kBinSmemCells = 12288;
 static_assert(kBinMaxG * kBinMaxG <= kBinSmemCells, "cell counters must fit shared memory");
 
-enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_ERR = 4, CNT_OVF = 5,
+// Device counters of one mixed call.  CNT_DEPTH counts FP64 walks that
+// reached the depth cap (reported BOUNDARY: the oracle's reading of a walk
+// that cannot end, unreachable for d > eps by Lemma 2).
+enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_DEPTH = 4, CNT_OVF = 5,
        CNT_NEAR_CURSOR = 7, CNT_N = 8 };
 
 // Work tallies of the counting build of the tree sweep (per query slot):
@@ -79,9 +82,19 @@ enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_ERR = 4, CNT_OV
 // their terms, record tests with the near check (Alg. 1's root step), record
 // tests for crossings and gap angle, record tests for crossings only, exact
 // FP64 recomputations, ellipse tests of records whose circle held the query,
-// control-point box tests of records whose ellipse held it.
+// control-point box tests of records whose ellipse held it.  Then the
+// tallies of the counting build of the FP32 near walk: nodes tested (Eq. 5),
+// nodes accepted as far (a chord each), evaluations of gamma(m) and the sum
+// of their segments' degrees.
 enum { WK_NODE = 0, WK_TELE = 1, WK_EXPANSION = 2, WK_TERMS = 3, WK_REC_NEAR = 4, WK_REC_FAR = 5,
-       WK_REC_CROSS = 6, WK_EXACT = 7, WK_ELLIPSE = 8, WK_BOX = 9, WK_N = 10 };
+       WK_REC_CROSS = 6, WK_EXACT = 7, WK_ELLIPSE = 8, WK_BOX = 9, WK_SWEEP_N = 10,
+       WK_NEAR_NODE = 10, WK_NEAR_FAR = 11, WK_NEAR_EVAL = 12, WK_NEAR_DEG = 13, WK_N = 14 };
+
+// FP32 walk depth: the cap is a tuning knob (the stack holds kDepthCap32Max
+// levels); Lemma 2 bounds the depth a pair needs by log2(B / max(eps, d)),
+// and a pair that reaches the cap hands its tail to the FP64 walk.
+constexpr int kDepthCap32Min = 12;
+constexpr int kNearChunkMin = 32, kNearChunkMax = 1024;
 
 struct Tuning {
     int qpt = 2;               // queries per sweep thread
@@ -91,6 +104,9 @@ struct Tuning {
     int tree = 1;              // 1: cluster sweep with gap-angle expansions; 0: flat sweep
     int bucket = 1;            // 1: bucket queries spatially before the sweep
     int cell_q = 64;           // target queries per bucket cell
+    int near_depth = 22;       // FP32 near-walk depth cap (kDepthCap32Min..kDepthCap32Max)
+    int near_chunk = 128;      // near pairs a warp draws per atomic (32..1024, multiple of 32)
+    int near_refill = 16;      // idle lanes that trigger a refill (1..32)
 };
 
 constexpr int kProfEvents = 7;   // events per profiled mixed call (6 intervals)
@@ -110,8 +126,10 @@ int mixed_kernel_count(const Work &W, const LaunchCfg &cfg);    // kernels one l
 cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const int4 *d_units,
                          int n_units, const int64_t *d_offsets, int64_t n_queries, PointSrc src,
                          OutDst out, const LaunchCfg &cfg, cudaStream_t s);
+// The sweep's gap angle (gap_angle in wn_kernels.cu) on n device values.
+cudaError_t launch_gap_angle(const float *y, const float *x, float *out, int64_t n, cudaStream_t s);
 cudaError_t launch_plain(const DomDev *d_dom, int64_t q0, int64_t n, PointSrc src, OutDst out,
-                         cudaStream_t s);
+                         unsigned long long *counters, cudaStream_t s);
 struct PeReq {
     int a, b;
     long long IA, JA, IB, JB;

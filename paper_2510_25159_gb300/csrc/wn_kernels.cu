@@ -1207,8 +1207,8 @@ struct NearWalk {                      // scalars and control points (registers)
 };
 
 struct NearStack {                     // the walk's stack (dynamically indexed: local memory)
-    float t[kDepthCap32 + 2], x[kDepthCap32 + 2], y[kDepthCap32 + 2];
-    int d[kDepthCap32 + 2];
+    float t[kDepthCap32Max + 2], x[kDepthCap32Max + 2], y[kDepthCap32Max + 2];
+    int d[kDepthCap32Max + 2];
 };
 
 struct NearArgs {
@@ -1221,6 +1221,10 @@ struct NearArgs {
     SubItem *f64_items;
     long long cap_f64;
     unsigned long long *counters;
+    int depth_cap;              // FP32 walk depth cap (kDepthCap32Min..kDepthCap32Max)
+    int chunk;                  // pairs a warp draws per atomic (multiple of 32)
+    int refill;                 // idle lanes that trigger a refill
+    unsigned long long *work;   // WK_NEAR_* tallies of the counting build, or null
 };
 
 __device__ __forceinline__ void item_query(const DomDev *Dp, const PointSrc &src, const Item &it,
@@ -1354,9 +1358,12 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
 }
 
 // One node of the walk.  Returns 0 while walking, 1 when finished, 2 when the
-// query is certainly on the boundary.
-template <bool RAT>
-__device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S)
+// query is certainly on the boundary.  The counting build (CNT) adds the
+// node's work to wk: one far test per node, a chord per far node, one
+// evaluation of gamma(m) (and its degree) per split.
+template <bool RAT, bool CNT>
+__device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S,
+                                         uint32_t *wk)
 {
     const int sp = W.sp;
     const float b = S.t[sp - 1], bx = S.x[sp - 1], by = S.y[sp - 1];
@@ -1383,9 +1390,13 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
                 else if (!W.sa && sb && D > 0.f) W.cnt++;
                 else if (W.sa && !sb && D < 0.f) W.cnt--;
             }
-        } else if (s >= -es || d >= kDepthCap32) {
+        } else if (s >= -es || d >= A.depth_cap) {
             undecided = true;
         }
+    }
+    if constexpr (CNT) {
+        wk[0]++;
+        if (far && !undecided) wk[1]++;
     }
     if (undecided) {
         // [0, a] is done (its crossings stay in W.cnt); [a, 1] goes to FP64
@@ -1418,6 +1429,10 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
     } else {
         bez_eval<float>(W.qx, W.qy, W.n, W.nmax, m, mx, my);
     }
+    if constexpr (CNT) {
+        wk[2]++;
+        wk[3] += (uint32_t)W.n;
+    }
     S.d[sp - 1] = d + 1;
     S.t[sp] = m;
     S.x[sp] = mx;
@@ -1433,26 +1448,24 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
 // its walk takes a new pair instead of waiting for the warp's longest walk.
 // Starting a pair costs three dependent global loads (pair, segment, control
 // points), so idle lanes are refilled together, once at least kNearRefill of
-// them wait, and one load latency serves them all; every iteration then
-// advances each busy lane by one node.  A warp draws up to kNearChunk pairs
-// at a time from the queue (one atomic per draw), fewer when the queue is
-// short, so that every warp of the grid gets pairs; consecutive pairs come
-// from neighbouring queries of one tile, so the lanes' walks stay close in
-// memory.
-constexpr int kNearChunk = 128;
-constexpr int kNearRefill = 16;
-
-template <bool RAT>
+// them wait (A.refill, a tuning knob), and one load latency serves them
+// all; every iteration then advances each busy lane by one node.  A warp
+// draws up to A.chunk pairs at a time from the queue (one atomic per draw,
+// a tuning knob), fewer when the queue is short, so that every warp of the
+// grid gets pairs; consecutive pairs come from neighbouring queries of one
+// tile, so the lanes' walks stay close in memory.
+template <bool RAT, bool CNT>
 __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
 {
     unsigned long long n = A.counters[CNT_NEAR];
     if (n > (unsigned long long)A.cap_near) n = (unsigned long long)A.cap_near;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    // pairs per draw: the queue spread over the grid's warps, 32 to kNearChunk
+    // pairs per draw: the queue spread over the grid's warps, 32 to A.chunk
     const unsigned long long n_warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const unsigned long long chunk =
-        min((unsigned long long)kNearChunk, max(32ULL, (n / n_warps) & ~31ULL));
+        min((unsigned long long)A.chunk, max(32ULL, (n / n_warps) & ~31ULL));
+    uint32_t wk[4] = {0u, 0u, 0u, 0u};
     NearWalk W;
     NearStack S;
     Item it;
@@ -1460,7 +1473,7 @@ __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
     unsigned long long pool = 0, pool_end = 0;        // the warp's drawn range (warp-uniform)
     for (;;) {
         const unsigned idle = __ballot_sync(0xffffffffu, !busy);
-        if (__popc(idle) >= kNearRefill && !dry) {
+        if (__popc(idle) >= A.refill && !dry) {
             if (pool >= pool_end) {
                 unsigned long long b = 0;
                 if (lane == 0) b = atomicAdd(&A.counters[CNT_NEAR_CURSOR], chunk);
@@ -1490,12 +1503,19 @@ __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
             continue;
         }
         if (busy) {
-            const int r = near_step<RAT>(A, it, W, S);
+            const int r = near_step<RAT, CNT>(A, it, W, S, wk);
             if (r != 0) {
                 if (r == 2) atomicOr(&A.flags[it.q], QF_BOUNDARY);
                 else if (W.cnt) atomicAdd(&A.acc2[it.q], 2 * W.cnt);
                 busy = false;
             }
+        }
+    }
+    if constexpr (CNT) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, wk[i]);
+            if (lane == 0 && v) atomicAdd(&A.work[WK_NEAR_NODE + i], (unsigned long long)v);
         }
     }
 }
@@ -1520,23 +1540,27 @@ __global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
         const bool sa = si.a == 0.f ? P[1] > pyp : (si.signs & 1u) != 0;
         const bool sb = si.b == 1.f ? P[2 * deg + 1] > pyp : (si.signs & 2u) != 0;
         int cnt = 0;
-        const bool bnd = alg1_fp64_sub(P, seg_weights(*Dp, s), deg, Dp->max_deg, Dp->seg_B[s], pxp, pyp, Dp->eps,
-                                       (double)si.a,
-                                       (double)si.b, sa, sb, cnt);
-        if (bnd) atomicOr(&A.flags[it.q], QF_BOUNDARY);
-        else if (cnt) atomicAdd(&A.acc2[it.q], 2 * cnt);
+        const int res = alg1_fp64_sub(P, seg_weights(*Dp, s), deg, Dp->max_deg, Dp->seg_B[s], pxp, pyp, Dp->eps,
+                                      (double)si.a, (double)si.b, sa, sb, cnt);
+        if (res != WALK_DONE) {
+            atomicOr(&A.flags[it.q], QF_BOUNDARY);
+            if (res == WALK_DEPTH) atomicAdd(&A.counters[CNT_DEPTH], 1ULL);
+        } else if (cnt) {
+            atomicAdd(&A.acc2[it.q], 2 * cnt);
+        }
     }
 }
 
 // ------------------------------------------------------------------ plain FP64
 // Sum over every instance the query sees of Algorithm 1 (FP64, atan2 chord
 // angles), the chord corrections and line terms of Eq. 9.
-__device__ void plain_query(const DomDev *Dp, double x0, double y0, double &om, int &state)
+__device__ void plain_query(const DomDev *Dp, double x0, double y0, double &om, int &state, bool &depth)
 {
     const double x = reduce_period(x0, Dp->Pu), y = reduce_period(y0, Dp->Pv);
     FarAngle fa;
     long long half = 0;
     bool bnd = false;
+    depth = false;
     const double eps = Dp->eps;
     for (int j = 0; j < Dp->n_inst && !bnd; j++) {
         const InstDev in = Dp->inst[j];
@@ -1551,10 +1575,12 @@ __device__ void plain_query(const DomDev *Dp, double x0, double y0, double &om, 
         const double qx = xsub(x, in.Tx), qy = xsub(y, in.Ty);
         // the planar instance covers every loop of the domain
         const int sb = (in.type == IT_ALL) ? 0 : L.s0, se = (in.type == IT_ALL) ? Dp->n_segs : L.s1;
-        for (int s = sb; s < se && !bnd; s++)
-            bnd = alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]), seg_weights(*Dp, s), __ldg(&Dp->seg_deg[s]),
-                            Dp->max_deg,
-                            __ldg(&Dp->seg_B[s]), qx, qy, eps, fa);
+        for (int s = sb; s < se && !bnd; s++) {
+            const int res = alg1_fp64(Dp->cp + 2 * (size_t)__ldg(&Dp->seg_cp[s]), seg_weights(*Dp, s),
+                                      __ldg(&Dp->seg_deg[s]), Dp->max_deg, __ldg(&Dp->seg_B[s]), qx, qy, eps, fa);
+            bnd = res != WALK_DONE;
+            depth = res == WALK_DEPTH;
+        }
         if (in.type == IT_PE && !bnd) {
             const double ax = L.g0x - qx, ay = L.g0y - qy, bx = L.g0vx - qx, by = L.g0vy - qy;
             fa.ang -= atan2(ax * by - ay * bx, ax * bx + ay * by);
@@ -1580,15 +1606,17 @@ __device__ __forceinline__ void write_out(const OutDst &o, uint32_t q, double om
 }
 
 __global__ void __launch_bounds__(128) k_plain(const DomDev *Dp, long long q0, long long n,
-                                               PointSrc src, OutDst out)
+                                               PointSrc src, OutDst out, unsigned long long *counters)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const uint32_t q = (uint32_t)(q0 + i);
         double x, y, om;
         int st;
+        bool depth;
         get_point(src, q, x, y);
-        plain_query(Dp, x, y, om, st);
+        plain_query(Dp, x, y, om, st, depth);
+        if (depth && counters) atomicAdd(&counters[CNT_DEPTH], 1ULL);
         write_out(out, q, om, st, true);
     }
 }
@@ -1679,7 +1707,7 @@ struct EscArgs {
     const DomDev *doms;
     PointSrc src;
     const uint2 *esc;
-    const unsigned long long *counters;
+    unsigned long long *counters;
     OutDst out;
 };
 
@@ -1700,9 +1728,9 @@ constexpr int kEscCluster = 8;              // CTAs (one per SM) per escalated q
 
 // One record against the query (p relative to the instance) in FP64: the
 // crossings of its segment's Algorithm 1 chords (or of the closing chord),
-// its gap's crossing and angle.  Returns true when the query is on the
-// boundary.
-__device__ __noinline__ bool record_f64(const DomDev *__restrict__ Dp, int r, double pxp, double pyp, int &c,
+// its gap's crossing and angle.  Returns WALK_DONE, or WALK_BOUNDARY /
+// WALK_DEPTH when the query is on the boundary.
+__device__ __noinline__ int record_f64(const DomDev *__restrict__ Dp, int r, double pxp, double pyp, int &c,
                                         double &dth)
 {
     const uint32_t fl = __float_as_uint(Dp->rec[4 * r + 1].w);
@@ -1716,15 +1744,15 @@ __device__ __noinline__ bool record_f64(const DomDev *__restrict__ Dp, int r, do
         const double ax = a.x - pxp, ay = a.y - pyp, bx = b.x - pxp, by = b.y - pyp;
         const double qa = ax * ax + ay * ay, qb = bx * bx + by * by;
         const double eps = Dp->eps;
-        if (qa < eps * eps || qb < eps * eps) return true;
+        if (qa < eps * eps || qb < eps * eps) return WALK_BOUNDARY;
         const double L = Dp->seg_B[s];
         const double S = L * L - (qa + qb);
         if (!(S < 0.0 || 4.0 * qa * qb > S * S)) {
             // inside the root ellipse: the FP64 walk
             int cnt = 0;
-            if (alg1_fp64_sub(Dp->cp + 2 * (size_t)Dp->seg_cp[s], seg_weights(*Dp, s), Dp->seg_deg[s], Dp->max_deg,
-                              L, pxp, pyp, eps, 0.0, 1.0, sa, sb, cnt))
-                return true;
+            const int res = alg1_fp64_sub(Dp->cp + 2 * (size_t)Dp->seg_cp[s], seg_weights(*Dp, s), Dp->seg_deg[s],
+                                          Dp->max_deg, L, pxp, pyp, eps, 0.0, 1.0, sa, sb, cnt);
+            if (res != WALK_DONE) return res;
             c = cnt;
             chord = false;
         }
@@ -1742,7 +1770,7 @@ __device__ __noinline__ bool record_f64(const DomDev *__restrict__ Dp, int r, do
         }
         dth = atan2(d, ux * vx + uy * vy);
     }
-    return false;
+    return WALK_DONE;
 }
 
 __global__ void __cluster_dims__(kEscCluster, 1, 1) __launch_bounds__(kEscThreads) k_f64query(const EscArgs A)
@@ -1780,7 +1808,9 @@ __global__ void __cluster_dims__(kEscCluster, 1, 1) __launch_bounds__(kEscThread
             for (int r = in.r0 + rank * kEscThreads + tid; r < in.r1 && !bnd; r += kEscCluster * kEscThreads) {
                 int c;
                 double dth;
-                bnd |= record_f64(Dp, r, qx, qy, c, dth);
+                const int res = record_f64(Dp, r, qx, qy, c, dth);
+                if (res == WALK_DEPTH) atomicAdd(&A.counters[CNT_DEPTH], 1ULL);
+                bnd |= res != WALK_DONE;
                 acc += 2 * c;
                 th += dth;
             }
@@ -1969,9 +1999,21 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     na.f64_items = W.f64_items;
     na.cap_f64 = W.cap_f64;
     na.counters = W.counters;
+    na.depth_cap = std::min(std::max(cfg.tun.near_depth, kDepthCap32Min), kDepthCap32Max);
+    na.chunk = std::min(std::max(cfg.tun.near_chunk, kNearChunkMin), kNearChunkMax) & ~31;
+    na.refill = std::min(std::max(cfg.tun.near_refill, 1), 32);
+    na.work = cfg.work;
     mark(2);
-    if (cfg.rational) k_near<true><<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
-    else k_near<false><<<cfg.n_sm * cfg.tun.near_ctas_per_sm, 256, 0, s>>>(na);
+    {
+        const int g = cfg.n_sm * cfg.tun.near_ctas_per_sm;
+        if (cfg.work) {
+            if (cfg.rational) k_near<true, true><<<g, 256, 0, s>>>(na);
+            else k_near<false, true><<<g, 256, 0, s>>>(na);
+        } else {
+            if (cfg.rational) k_near<true, false><<<g, 256, 0, s>>>(na);
+            else k_near<false, false><<<g, 256, 0, s>>>(na);
+        }
+    }
     mark(3);
     k_f64items<<<cfg.n_sm * 16, 128, 0, s>>>(na);
     mark(4);
@@ -1999,12 +2041,27 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     return cudaGetLastError();
 }
 
+__global__ void k_gap_angle(const float *y, const float *x, float *out, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = gap_angle(y[i], x[i]);
+}
+
+cudaError_t launch_gap_angle(const float *y, const float *x, float *out, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long blocks = std::min((n + 255) / 256, (int64_t)4096);
+    k_gap_angle<<<(int)blocks, 256, 0, s>>>(y, x, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_plain(const DomDev *d_dom, int64_t q0, int64_t n, PointSrc src, OutDst out,
-                         cudaStream_t s)
+                         unsigned long long *counters, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const long long blocks = std::min((long long)(n + 127) / 128, 1LL << 20);
-    k_plain<<<(int)blocks, 128, 0, s>>>(d_dom, q0, n, src, out);
+    k_plain<<<(int)blocks, 128, 0, s>>>(d_dom, q0, n, src, out, counters);
     return cudaGetLastError();
 }
 

@@ -9,8 +9,14 @@
 // processes that run with a hard device-memory budget where a first-call
 // cudaMalloc of the scratch buffers could fail or evict something else.
 //
-// Cost: every process that loads the library holds kScratchBytes of device
-// memory on each device it uses, until it exits.
+// Cost: kScratchBytes of device memory on each device the process calls it
+// on, held until the process exits.  The library has no relocatable device
+// code and CUDA loads modules lazily, so the array is placed on a device
+// when the first call there loads this module (an implicit allocation),
+// and kernels load (and reserve local memory) at their first launch: the
+// first call on a device places the array and launches every kernel a
+// call can use once on an empty work list, so callers make it at start-up
+// (n = 0 does only this set-up).
 #include <cstdint>
 #include <mutex>
 
@@ -45,60 +51,13 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
 bool g_ready[64];
-unsigned char *g_addr[64];
 
-// Work list of one domain: tiles of `tile` queries, and the offsets {0, n}.
-__global__ void k_fill_units(int4 *units, int64_t *offsets, int n_units, int tile, int n)
+// The scratch array's device address per device (set once per device).
+unsigned char *g_base[64];
+
+// The mixed path's scratch carved out of the array at `base`.
+Work scratch_work(unsigned char *base)
 {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u < n_units) units[u] = make_int4(0, u * tile, min(tile, n - u * tile), 0);
-    if (u == 0) {
-        offsets[0] = 0;
-        offsets[1] = n;
-    }
-}
-
-bool device_ptr(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-}  // namespace
-
-extern "C" wn_status wn_query_noalloc(const wn_domain *domain, const double *points, int64_t n,
-                                      double *out_winding, uint8_t *out_inside, wn_stream stream)
-{
-    if (!domain) return WN_ERR_ARG;
-    if (n < 0) return WN_ERR_ARG;
-    if (n > kMaxQ) return WN_ERR_LIMIT;      // more than WN_NOALLOC_MAX_QUERIES: split the call
-    if (n == 0) return WN_OK;
-    if (!points || !device_ptr(points) || (out_winding && !device_ptr(out_winding)) ||
-        (out_inside && !device_ptr(out_inside)))
-        return WN_ERR_ARG;
-    if (reinterpret_cast<uintptr_t>(points) & 15) return WN_ERR_ARG;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) return WN_ERR_CUDA;
-    int n_sm = 0;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_ready[dev]) {
-            // once per device, with that device current
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_scratch);
-            if (e != cudaSuccess) return WN_ERR_CUDA;
-            g_addr[dev] = static_cast<unsigned char *>(p);
-            g_ready[dev] = true;
-        }
-    }
-    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return WN_ERR_CUDA;
-    unsigned char *base = g_addr[dev];
     Work W;
     W.counters = reinterpret_cast<unsigned long long *>(base + kOffCounters);
     W.units = reinterpret_cast<int4 *>(base + kOffUnits);
@@ -112,9 +71,90 @@ extern "C" wn_status wn_query_noalloc(const wn_domain *domain, const double *poi
     W.cap_q = kMaxQ;
     W.cap_near = kNearCap;
     W.cap_f64 = kF64Cap;
-    Tuning tun;                       // fixed shape: tree sweep, 2 queries per thread
+    return W;
+}
+
+// The fixed launch shape: tree sweep, 2 queries per thread, no bucketing.
+Tuning fixed_tuning()
+{
+    Tuning tun;
     tun.qpt = 2;
     tun.tree = 1;
+    return tun;
+}
+
+// Work list of one domain: tiles of `tile` queries, and the offsets {0, n}.
+__global__ void k_fill_units(int4 *units, int64_t *offsets, int n_units, int tile, int n)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n_units) units[u] = make_int4(0, u * tile, min(tile, n - u * tile), 0);
+    if (u == 0) {
+        offsets[0] = 0;
+        offsets[1] = n;
+    }
+}
+
+// A failed lookup leaves its error for the caller to see (the call then
+// returns WN_ERR_ARG before anything else runs).
+bool device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) return false;
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" wn_status wn_query_noalloc(const wn_domain *domain, const double *points, int64_t n,
+                                      double *out_winding, uint8_t *out_inside, wn_stream stream)
+{
+    if (!domain) return WN_ERR_ARG;
+    if (n < 0) return WN_ERR_ARG;
+    if (n > kMaxQ) return WN_ERR_LIMIT;      // more than WN_NOALLOC_MAX_QUERIES: split the call
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) return WN_ERR_CUDA;
+    if (domain->device != dev) return WN_ERR_ARG;
+    int n_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_ready[dev]) {
+            // once per device, with that device current: the array's address
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_scratch);
+            if (e != cudaSuccess) return WN_ERR_CUDA;
+            g_base[dev] = static_cast<unsigned char *>(p);
+            // then every kernel a call can launch, once on an empty work
+            // list: each launch loads the kernel's code and reserves its
+            // local memory now, so that later calls allocate nothing
+            e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return WN_ERR_CUDA;
+            Work W0 = scratch_work(g_base[dev]);
+            cudaStream_t s0 = (cudaStream_t)stream;
+            k_fill_units<<<1, 128, 0, s0>>>(W0.units, W0.offsets, 0, 64, 0);
+            if ((e = cudaGetLastError()) != cudaSuccess) return WN_ERR_CUDA;
+            for (int rat = 0; rat < 2; rat++) {
+                LaunchCfg c0{n_sm, fixed_tuning(), nullptr};
+                c0.rational = rat != 0;
+                PointSrc src0{};
+                OutDst out0{};
+                if (launch_mixed(W0, domain->d_self, 1, W0.units, 0, W0.offsets, 0, src0, out0, c0, s0) !=
+                    cudaSuccess)
+                    return WN_ERR_CUDA;
+            }
+            g_ready[dev] = true;
+        }
+    }
+    // n == 0 after the set-up: the start-up call that places the array
+    if (n == 0) return WN_OK;
+    if (!points || !device_ptr(points) || (out_winding && !device_ptr(out_winding)) ||
+        (out_inside && !device_ptr(out_inside)))
+        return WN_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(points) & 15) return WN_ERR_ARG;
+    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return WN_ERR_CUDA;
+    Work W = scratch_work(g_base[dev]);
+    const Tuning tun = fixed_tuning();
     const int tile = 32 * tun.qpt;    // the tree sweep gives each warp one unit
     const int n_units = (int)((n + tile - 1) / tile);
     cudaStream_t s = (cudaStream_t)stream;

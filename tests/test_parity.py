@@ -286,7 +286,7 @@ def test_stats_and_profiling(wn):
     st = wn.stats()
     assert n == 1 and t["sweep"] > 0 and t["bucket"] >= 0
     assert st["queries"] == sum(len(q) for q in qs)
-    assert st["overflow"] == 0 and st["device_error"] == 0
+    assert st["overflow"] == 0 and st["depth_cap"] == 0
 
 
 def test_work_counting_build(wn):
