@@ -229,22 +229,37 @@ def stratified_sample(qs, per_domain, rng):
 
 
 def oracle_run(doms, qs, picks, threads, budget_s=None):
-    """The FP64 oracle on the picked queries of each domain; stops after
-    budget_s seconds when given.  Returns ({domain: (idx, w, state, margin)},
-    queries done, seconds)."""
+    """The FP64 oracle on the picked queries of each domain, on `threads`
+    host threads: a domain with many picked queries splits them over the
+    oracle's own threads, the others run one domain per thread (larger
+    samples first).  Stops taking new domains after budget_s seconds when
+    given.  Returns ({domain: (idx, w, state, margin)}, queries done,
+    seconds)."""
+    import concurrent.futures as cf
+
     import oracle
     res = {}
-    done = 0
+    order = sorted((d for d in range(len(doms)) if len(picks[d])), key=lambda d: -len(picks[d]))
+    big = [d for d in order if len(picks[d]) >= 256 * threads] if threads > 1 else []
+    small = [d for d in order if d not in set(big)]
     t0 = time.perf_counter()
-    for d, (dom, q, i) in enumerate(zip(doms, qs, picks)):
-        if len(i) == 0:
-            continue
-        w, s, mg = oracle.query(dom, q[i], threads=threads, margins=True)
-        res[d] = (i, w, s, mg)
-        done += len(i)
+
+    def one(d, th):
         if budget_s is not None and time.perf_counter() - t0 > budget_s:
-            break
-    return res, done, time.perf_counter() - t0
+            return
+        w, s, mg = oracle.query(doms[d], qs[d][picks[d]], threads=th, margins=True)
+        res[d] = (picks[d], w, s, mg)
+
+    for d in big:
+        one(d, threads)
+    if threads > 1:
+        with cf.ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda d: one(d, 1), small))
+    else:
+        for d in small:
+            one(d, 1)
+    dt = time.perf_counter() - t0
+    return res, sum(len(v[0]) for v in res.values()), dt
 
 
 def calibrate_oracle(doms, qs, threads, rng, budget_s):
@@ -479,7 +494,13 @@ def main():
     s8d_sweep = sum(S8D_PER_TALLY.get(k, 0.0) * v for k, v in work.items()) - CHORD * near_pairs
     s8d_near = (FAR_TEST * nwork["near_nodes"] + CHORD * nwork["near_far"] +
                 4.0 * nwork["near_eval_degrees"] + 4.0 * nwork["near_evals"])
-    impl_sweep = sum(IMPL_FLOPS[k] * v for k, v in work.items())
+    impl_sweep = sum(IMPL_FLOPS.get(k, 0.0) * v for k, v in work.items())
+    # SIMT efficiency of the tree walk: query-slot tests over the slots the
+    # warps' visits and record iterations offer (32 x queries per thread)
+    slots = 32 * int(tuning.get("qpt", 1))
+    simt = {"nodes": work["node_tests"] / max(1, slots * work.get("warp_node_visits", 0)),
+            "records": (work["record_tests_near"] + work["record_tests_far"] + work["record_tests_cross"]) /
+                       max(1, slots * work.get("warp_record_iterations", 0))}
     achieved = s8d_sweep / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None
     traffic = None
     tf = os.path.join(ROOT, "profiles", "sweep_traffic.json")
@@ -504,6 +525,7 @@ def main():
             "whole_step_tflops": (s8d_sweep + s8d_near) / (ms / 1e3) / 1e12,
             "implementation_ops": {"flops_per_step": impl_sweep, "per_tally": IMPL_FLOPS,
                                    "tflops": impl_sweep / (sweep_ms / 1e3) / 1e12 if sweep_ms > 0 else None},
+            "simt_efficiency": simt,
             "brute_force_pairs_per_step": pairs,
             "kernel_ms_per_step": {k: v * calls_per_step for k, v in kernel_ms.items()}}
 
@@ -645,7 +667,7 @@ def main():
             res_p, n_p, dt_p = oracle_run(doms, qs, proportional_sample(qs, m, rng), threads)
             per_dom = int(np.clip(m // max(1, len(doms)), 8, 20000))
             res_s, n_s, dt_s = oracle_run(doms, qs, stratified_sample(qs, per_dom, rng), threads)
-            res_1, n_1, dt_1 = oracle_run(doms, qs, proportional_sample(qs, max(1000, m // (4 * threads)), rng), 1,
+            res_1, n_1, dt_1 = oracle_run(doms, qs, proportional_sample(qs, max(1000, m // threads), rng), 1,
                                           budget_s=args.cpu_budget / 2)
             par_p = parity_check(doms, res_p, w_all, s_all, off)
             par_s = parity_check(doms, res_s, w_all, s_all, off)

@@ -270,8 +270,9 @@ wn_status wn_set_tuning(int32_t tile_queries_per_thread, int32_t sweep_ctas_per_
  * coordinate descent from the current setting over queries per sweep thread
  * {1, 2}, sweep CTAs per SM {2, 3, 4, 6}, near-pair CTAs per SM {4, 8, 16},
  * the spatial bucket size {32, 64, 128} queries, bucketing on / off, the
- * FP32 near-walk depth cap {16, 22, 28}, the near-pair draw {64, 128, 256}
- * and the refill threshold {8, 16, 24} (see wn_set_near_tuning);
+ * FP32 near-walk depth cap {16, 22, 28}, the near-pair draw {64, 128, 256},
+ * the refill threshold {8, 16, 24} (see wn_set_near_tuning) and the
+ * flat-sweep record limit {0, 16, 32} (see wn_set_flat_records);
  * each candidate runs one
  * warm-up call and `iterations` timed calls (CUDA events on `stream`).
  *   domains, n_domains, point_offsets, points: as in wn_query_batched, with
@@ -284,10 +285,11 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains,
                       const int64_t *point_offsets, const double *points, int32_t iterations,
                       double *best_ms, wn_stream stream);
 
-/* Current tuning: the first min(n_out, 10) of (queries per sweep thread,
+/* Current tuning: the first min(n_out, 11) of (queries per sweep thread,
  * sweep CTAs per SM, near-pair CTAs per SM, graph replay, tree sweep, bucket
  * cell size in queries, spatial bucketing on/off, FP32 near-walk depth cap,
- * near-pair draw, refill threshold) into out (host int32[n_out]). */
+ * near-pair draw, refill threshold, flat-sweep record limit) into out (host
+ * int32[n_out]). */
 wn_status wn_get_tuning(int32_t *out, int32_t n_out);
 
 /*
@@ -305,6 +307,18 @@ wn_status wn_get_tuning(int32_t *out, int32_t n_out);
  * Errors: WN_ERR_ARG for values outside those ranges.
  */
 wn_status wn_set_near_tuning(int32_t depth_cap, int32_t chunk, int32_t refill);
+
+/*
+ * With the tree sweep on, planar domains of at most max_records records
+ * (0..4096; 0 = none) take the flat sweep instead: every query against every
+ * record, staged in shared memory, without spatial bucketing.  For a few
+ * dozen segments that costs less than the tree's dependent node steps.
+ * Results do not depend on it beyond rounding of the gap angles (the flat
+ * sweep sums them per record, the tree per record or by expansions).
+ * Default 0: on the batched B-Rep-shaped workload the tree sweep was as
+ * fast or faster for every limit tried.  Errors: WN_ERR_ARG outside 0..4096.
+ */
+wn_status wn_set_flat_records(int32_t max_records);
 
 /*
  * Test hook: caps on the near-pair and FP64-pair queues of the mixed path
@@ -370,9 +384,9 @@ wn_status wn_kernel_times(double *ms6, int64_t *n_calls);
  * Work tallies of the tree sweep, for measurement (no counterpart in the
  * paper).  With on != 0 the following WN_PREC_MIXED calls on this thread's
  * device run a counting build of the sweep kernel -- the same decisions and
- * arithmetic, plus per-warp tallies -- and add to ten counters, which
- * wn_set_work_counting also clears.  wn_sweep_work synchronises, writes them
- * into out10 (host int64[10]) and clears them:
+ * arithmetic, plus per-warp tallies -- and add to twelve counters, which
+ * wn_set_work_counting also clears.  wn_sweep_work synchronises, writes the
+ * first min(n_out, 12) into out (host int64[n_out]) and clears them:
  *   [0] (query, node) tests          [1] nodes whose crossings telescoped
  *   [2] gap-angle expansion sums     [3] their terms
  *   [4] (query, record) tests with the near check (Alg. 1's first step)
@@ -381,10 +395,13 @@ wn_status wn_kernel_times(double *ms6, int64_t *n_calls);
  *   [7] exact FP64 recomputations of a sign
  *   [8] ellipse tests (Eq. 5) of records whose enclosing circle held the query
  *   [9] control-point box tests of records whose ellipse held the query
+ *   [10] node visits of warps and [11] record iterations of warps in the
+ *        leaves (per warp, each serving its 32 or 64 query slots: [0] and
+ *        [4]-[6] over these, divided by the slots, is the SIMT efficiency)
  * Zeros when the flat sweep ran (wn_set_tuning tree = 0) or nothing ran.
  */
 wn_status wn_set_work_counting(int32_t on);
-wn_status wn_sweep_work(int64_t *out10);
+wn_status wn_sweep_work(int64_t *out, int32_t n_out);
 
 /*
  * Work tallies of the counting build of the FP32 near-pair walk (enabled by
@@ -407,7 +424,7 @@ wn_status wn_near_work(int64_t *out4);
  * fixed device-memory budget.  This entry point keeps all of its scratch
  * (per-query accumulators, the near-pair and FP64 queues, the work list)
  * in one fixed-size device array that is part of the library image (about
- * 12.3 MB per device).  The library is built without relocatable device
+ * 12.3 MiB per device).  The library is built without relocatable device
  * code and CUDA loads modules lazily by default, so the array and the
  * kernels' code are placed on a device when the FIRST call on that device
  * loads them; that call also launches every kernel a call can use once on

@@ -77,18 +77,19 @@ def lib():
         L.wn_get_tuning.argtypes = [P, I32]
         L.wn_set_near_tuning.argtypes = [I32, I32, I32]
         L.wn_set_queue_limits.argtypes = [I64, I64]
+        L.wn_set_flat_records.argtypes = [I32]
         L.wn_near_work.argtypes = [P]
         L.wn_last_escalated.argtypes = [P, I64, P]
         L.wn_eval_gap_angle.argtypes = [P, P, P, I64, P]
         L.wn_set_profiling.argtypes = [I32]
         L.wn_kernel_times.argtypes = [P, P]
         L.wn_set_work_counting.argtypes = [I32]
-        L.wn_sweep_work.argtypes = [P]
+        L.wn_sweep_work.argtypes = [P, I32]
         for f in ("wn_create_domain", "wn_create_domain_rational", "wn_query", "wn_query_batched", "wn_query_grid_bitmask",
                   "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times", "wn_autotune",
                   "wn_get_tuning", "wn_set_work_counting", "wn_sweep_work", "wn_set_near_tuning",
                   "wn_set_queue_limits", "wn_near_work", "wn_last_escalated",
-                  "wn_eval_gap_angle"):
+                  "wn_eval_gap_angle", "wn_set_flat_records"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -274,7 +275,7 @@ def autotune(domains, points, offsets, iterations=3, stream=None):
 
 
 TUNING = ("qpt", "sweep_ctas_per_sm", "near_ctas_per_sm", "use_graph", "tree", "cell_q", "bucket",
-          "near_depth", "near_chunk", "near_refill")
+          "near_depth", "near_chunk", "near_refill", "flat_max")
 
 
 def get_tuning():
@@ -287,6 +288,12 @@ def set_near_tuning(depth_cap=0, chunk=0, refill=0):
     """FP32 near-walk depth cap (12..30), pairs drawn per atomic (multiple of
     32 in 32..1024) and refill threshold (1..32); 0 keeps a value."""
     _check(lib().wn_set_near_tuning(int(depth_cap), int(chunk), int(refill)))
+
+
+def set_flat_records(max_records):
+    """Planar domains with at most max_records records take the flat sweep
+    (0: none)."""
+    _check(lib().wn_set_flat_records(int(max_records)))
 
 
 def set_queue_limits(near_pairs=0, fp64_pairs=0):
@@ -339,7 +346,7 @@ def kernel_times():
 
 WORK = ("node_tests", "telescoped_nodes", "expansions", "expansion_terms", "record_tests_near",
         "record_tests_far", "record_tests_cross", "exact_fp64", "ellipse_tests",
-        "box_tests")
+        "box_tests", "warp_node_visits", "warp_record_iterations")
 
 
 def set_work_counting(on=True):
@@ -350,7 +357,7 @@ def set_work_counting(on=True):
 def sweep_work():
     """Work tallies of the tree sweep since the last read (see WORK)."""
     c = np.zeros(len(WORK), dtype=np.int64)
-    _check(lib().wn_sweep_work(_ptr(c)))
+    _check(lib().wn_sweep_work(_ptr(c), len(WORK)))
     return dict(zip(WORK, c.tolist()))
 
 

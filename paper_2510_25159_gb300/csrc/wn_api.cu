@@ -27,7 +27,8 @@ struct Tables {
     std::vector<const wn_domain *> key_doms;
     std::vector<int64_t> key_offsets;
     int key = 0;
-    int n_units = 0, n_cells = 0, n_bchunks = 0;
+    int n_units = 0, n_flat = 0, n_cells = 0, n_bchunks = 0;
+    bool flat0 = false;                 // a one-domain list: its domain takes the flat sweep
     int4 *units = nullptr;
     DomDev *doms = nullptr;
     int64_t *offsets = nullptr;
@@ -292,6 +293,15 @@ wn_status wn_set_near_tuning(int32_t depth_cap, int32_t chunk, int32_t refill)
     return WN_OK;
 }
 
+wn_status wn_set_flat_records(int32_t max_records)
+{
+    if (max_records < 0 || max_records > 4096) return fail(WN_ERR_ARG, "max_records outside 0..4096");
+    std::lock_guard<std::mutex> lk(g_mu);
+    drop_graphs();
+    g_tun.flat_max = max_records;
+    return WN_OK;
+}
+
 wn_status wn_set_queue_limits(int64_t near_pairs, int64_t fp64_pairs)
 {
     if (near_pairs < 0 || fp64_pairs < 0) return fail(WN_ERR_ARG, "limits must be >= 0");
@@ -302,16 +312,27 @@ wn_status wn_set_queue_limits(int64_t near_pairs, int64_t fp64_pairs)
     return WN_OK;
 }
 
+// Small planar domains take the flat sweep (every query against every
+// record, staged in shared memory): a handful of records costs less swept
+// flat than walked as a tree, whose node steps wait on dependent loads.
+static bool flat_domain(const wn_domain *d, bool grid_tiled)
+{
+    return !grid_tiled && g_tun.tree && g_tun.flat_max > 0 && d->dev.kind == DK_PLANAR &&
+           d->sweep_records <= g_tun.flat_max;
+}
+
 // The batch tables of one list of domains: the work list of (domain, query
-// tile) units in decreasing cost order, the domain records, the offsets and
-// the bucketing layout, uploaded once and reused while the list, its query
+// tile) units in decreasing cost order (the tree sweep's units, then the
+// flat sweep's), the domain records, the offsets and the bucketing layout
+// (tree domains only), uploaded once and reused while the list, its query
 // offsets and the launch shape are unchanged.
 static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *domains, int32_t n_domains,
                               const int64_t *offsets, int key, bool grid_tiled, const PointSrc &src,
                               int32_t grid_nv, int64_t tile)
 {
     const bool same = T.key == key && T.key_doms.size() == (size_t)n_domains &&
-                      (n_domains == 1 || std::equal(T.key_doms.begin(), T.key_doms.end(), domains)) &&
+                      (n_domains == 1 ? T.flat0 == flat_domain(domains[0], grid_tiled)
+                                      : std::equal(T.key_doms.begin(), T.key_doms.end(), domains)) &&
                       T.key_offsets.size() == (size_t)n_domains + 1 &&
                       std::equal(T.key_offsets.begin(), T.key_offsets.end(), offsets);
     cudaError_t e;
@@ -324,24 +345,35 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
     }
     T.key_doms.clear();
     std::vector<DomDev> h_doms(n_domains);
-    std::vector<std::pair<double, int4>> u;
+    std::vector<std::pair<double, int4>> u, uf;
+    std::vector<char> flat(n_domains);
+    // a tree unit's .w: its first position in the bucketed order, which
+    // holds the tree domains' queries only (the flat ones are not bucketed)
+    int64_t pbase = 0;
     for (int d = 0; d < n_domains; d++) {
         h_doms[d] = domains[d]->dev;
+        flat[d] = flat_domain(domains[d], grid_tiled);
         // positions to sweep: the queries, or the cells of every tile of the grid
         const int64_t cnt = grid_tiled ? (int64_t)src.tiles_x * ((grid_nv + 7) / 8) * 64 : offsets[d + 1] - offsets[d];
         // sweep cost of one query of this domain: records of every instance
         const double work = (double)std::max<int64_t>(domains[d]->sweep_records, 1);
-        for (int64_t q0 = 0; q0 < cnt; q0 += tile) {
-            const int64_t c = std::min(tile, cnt - q0);
-            u.push_back({work * (double)c, make_int4(d, (int)(offsets[d] + q0), (int)c, 0)});
+        const int64_t t = flat[d] ? (int64_t)kSweepThreads * kFlatQpt : tile;
+        for (int64_t q0 = 0; q0 < cnt; q0 += t) {
+            const int64_t c = std::min(t, cnt - q0);
+            (flat[d] ? uf : u).push_back({work * (double)c, make_int4(d, (int)(offsets[d] + q0), (int)c,
+                                                                      flat[d] ? 0 : (int)(pbase + q0))});
         }
+        if (!flat[d]) pbase += cnt;
     }
-    std::stable_sort(u.begin(), u.end(), [](const std::pair<double, int4> &a, const std::pair<double, int4> &b) {
-        return a.first > b.first;
-    });
+    auto by_cost = [](const std::pair<double, int4> &a, const std::pair<double, int4> &b) { return a.first > b.first; };
+    std::stable_sort(u.begin(), u.end(), by_cost);
+    std::stable_sort(uf.begin(), uf.end(), by_cost);
+    T.n_units = (int)u.size();
+    T.n_flat = (int)uf.size();
+    T.flat0 = n_domains == 1 && flat[0];
+    u.insert(u.end(), uf.begin(), uf.end());
     std::vector<int4> h_units(u.size());
     for (size_t i = 0; i < u.size(); i++) h_units[i] = u[i].second;
-    T.n_units = (int)u.size();
     if ((e = grow(T.units, T.cap_units, (int64_t)u.size())) != cudaSuccess) return cuda_fail(e, "units");
     if ((e = grow(T.doms, T.cap_doms, (int64_t)n_domains)) != cudaSuccess) return cuda_fail(e, "doms");
     if ((e = grow(T.offsets, T.cap_off, (int64_t)n_domains + 1)) != cudaSuccess) return cuda_fail(e, "offsets");
@@ -361,8 +393,8 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
     std::vector<int4> bch;
     int64_t ncell = 0;
     for (int d = 0; d < n_domains; d++) {
-        const int64_t cnt = offsets[d + 1] - offsets[d];
-        const int G = (int)std::min<double>((double)kBinMaxG, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
+        const int64_t cnt = flat[d] ? 0 : offsets[d + 1] - offsets[d];    // the flat sweep needs no bucketing
+        const int G = cnt == 0 ? 0 : (int)std::min<double>((double)kBinMaxG, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
         dcell[d] = make_int4((int)ncell, G, 0, 0);
         ncell += (int64_t)G * G;
         const int64_t csz = std::min<int64_t>(32768, std::max<int64_t>(4096, 2LL * G * G));
@@ -509,7 +541,8 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
         const int qpt = g_tun.tree ? std::min(g_tun.qpt, 2) : g_tun.qpt;
         // the tree sweep gives each warp its own unit, the flat sweep each CTA
         const int64_t tile = (g_tun.tree ? 32LL : 256LL) * qpt;
-        const int key = ((qpt * 2 + (g_tun.tree ? 1 : 0)) * 4096 + g_tun.cell_q) * 2 + (grid_tiled ? 1 : 0);
+        const int key = (((qpt * 2 + (g_tun.tree ? 1 : 0)) * 4096 + g_tun.cell_q) * 2 + (grid_tiled ? 1 : 0)) * 8192 +
+                        std::min(g_tun.flat_max, 8191);
         if (grouped) {
             // groups of consecutive domains with about n / G queries each
             const int G = n_groups;
@@ -570,6 +603,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                 if (out.w) og_out.w = out.w + q0;
                 if (out.st) og_out.st = out.st + q0;
                 LaunchCfg cfg{S->n_sm, g_tun, nullptr};
+                cfg.n_flat = T.n_flat;
                 for (int d = d0; d < d0 + nd; d++) cfg.rational |= domains[d]->dev.w != nullptr;
                 const DomDev *d_doms = nd == 1 ? domains[d0]->d_self : T.doms;
                 if ((e = cudaStreamWaitEvent(stream, S->ev[g], 0)) != cudaSuccess)
@@ -603,6 +637,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
             return cuda_fail(e, "scratch");
         Work Wl = work_with(S, T);
         LaunchCfg cfg{S->n_sm, g_tun, S->profiling ? &S->events : nullptr};
+        cfg.n_flat = T.n_flat;
         if (S->counting) cfg.work = S->d_work;
         cfg.grid_tiled = grid_tiled;
         for (int d = 0; d < n_domains; d++) cfg.rational |= domains[d]->dev.w != nullptr;
@@ -771,7 +806,8 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains, const 
                           {&Tuning::bucket, 2, {1, 0}},
                           {&Tuning::near_depth, 3, {16, 22, 28}},
                           {&Tuning::near_chunk, 3, {64, 128, 256}},
-                          {&Tuning::near_refill, 3, {8, 16, 24}}};
+                          {&Tuning::near_refill, 3, {8, 16, 24}},
+                          {&Tuning::flat_max, 3, {0, 16, 32}}};
     for (const Knob &kb : knobs) {
         if (r != WN_OK) break;
         for (int i = 0; i < kb.n && r == WN_OK; i++) {
@@ -806,10 +842,10 @@ wn_status wn_get_tuning(int32_t *out, int32_t n_out)
 {
     if (!out || n_out < 0) return fail(WN_ERR_ARG, "out is NULL or n_out < 0");
     std::lock_guard<std::mutex> lk(g_mu);
-    const int32_t v[10] = {g_tun.qpt, g_tun.sweep_ctas_per_sm, g_tun.near_ctas_per_sm, g_tun.use_graph,
+    const int32_t v[11] = {g_tun.qpt, g_tun.sweep_ctas_per_sm, g_tun.near_ctas_per_sm, g_tun.use_graph,
                            g_tun.tree, g_tun.cell_q, g_tun.bucket, g_tun.near_depth, g_tun.near_chunk,
-                           g_tun.near_refill};
-    for (int i = 0; i < n_out && i < 10; i++) out[i] = v[i];
+                           g_tun.near_refill, g_tun.flat_max};
+    for (int i = 0; i < n_out && i < 11; i++) out[i] = v[i];
     return WN_OK;
 }
 
@@ -866,7 +902,15 @@ static wn_status read_work(int first, int count, int64_t *out)
     return WN_OK;
 }
 
-wn_status wn_sweep_work(int64_t *out10) { return read_work(0, WK_SWEEP_N, out10); }
+wn_status wn_sweep_work(int64_t *out, int32_t n_out)
+{
+    if (n_out < 0) return fail(WN_ERR_ARG, "n_out < 0");
+    int64_t all[WK_SWEEP_N];
+    const wn_status st = read_work(0, WK_SWEEP_N, out ? all : nullptr);
+    if (st != WN_OK) return st;
+    for (int i = 0; i < n_out && i < WK_SWEEP_N; i++) out[i] = all[i];
+    return WN_OK;
+}
 
 wn_status wn_near_work(int64_t *out4) { return read_work(WK_NEAR_NODE, WK_N - WK_NEAR_NODE, out4); }
 

@@ -100,7 +100,7 @@ struct DomDev {
     double ox, oy;              // origin of the FP32 coordinates
     double nx, ny, PP;          // family normal and Pu*Pv (bi-periodic)
     float M;                    // max |P - o|_inf over lifted control points
-    float pad2;
+    float Tm;                   // max |lattice shift|_inf over the instances (0 planar)
     float Mq;                   // queries with |p' - o|_inf > Mq go to FP64
     float pad1;
     const int *seg_deg;         // [n_segs]
@@ -228,6 +228,14 @@ __host__ __device__ __forceinline__ double xdiv(double a, double b)
 // Reduce a coordinate into [0, P) (identity when P <= 0).
 __host__ __device__ __forceinline__ double reduce_period(double x, double P)
 {
+#ifdef __CUDA_ARCH__
+    // the common cases decided with integer instructions (GB300's FP64 unit
+    // is narrow): the bit patterns of non-negative doubles order as their
+    // values, and P is never NaN
+    const long long pb = __double_as_longlong(P), xb = __double_as_longlong(x);
+    if (pb <= 0) return x;                  // P <= 0: no period on this axis
+    if (xb >= 0 && xb < pb) return x;       // +0 <= x < P (NaN and -0 take the general path)
+#endif
     if (!(P > 0)) return x;
     if (x >= 0.0 && x < P) return x;        // already in the base tile: fmod(x, P) == x
     double r = fmod(x, P);

@@ -948,6 +948,7 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             g.lvy = (float)L.v[1];
         }
         instf[j] = g;
+        dv.Tm = std::fmax(dv.Tm, (float)std::fmax(std::fabs(in.Tx), std::fabs(in.Ty)));
     }
     dv.cull = up.up(cull);
     dv.instf = up.up(instf);

@@ -49,7 +49,7 @@ struct Work {
     SubItem *f64_items = nullptr;
     uint2 *esc_q = nullptr;    // (query, batch entry) recomputed in FP64
     unsigned long long *counters = nullptr;  // see CNT_*
-    int4 *units = nullptr;     // (dom, q0, count, 0)
+    int4 *units = nullptr;     // (dom, first query, count, first position in the bucketed order)
     DomDev *doms = nullptr;
     int64_t *offsets = nullptr;  // device copy of point offsets
     // spatial bucketing of the queries (null: sweep in input order)
@@ -75,20 +75,22 @@ static_assert(kBinMaxG * kBinMaxG <= kBinSmemCells, "cell counters must fit shar
 // reached the depth cap (reported BOUNDARY: the oracle's reading of a walk
 // that cannot end, unreachable for d > eps by Lemma 2).
 enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_DEPTH = 4, CNT_OVF = 5,
-       CNT_NEAR_CURSOR = 7, CNT_N = 8 };
+       CNT_FLAT_UNIT = 6, CNT_NEAR_CURSOR = 7, CNT_N = 8 };
 
 // Work tallies of the counting build of the tree sweep (per query slot):
 // node tests, nodes whose crossings telescoped, expansion evaluations and
 // their terms, record tests with the near check (Alg. 1's root step), record
 // tests for crossings and gap angle, record tests for crossings only, exact
 // FP64 recomputations, ellipse tests of records whose circle held the query,
-// control-point box tests of records whose ellipse held it.  Then the
-// tallies of the counting build of the FP32 near walk: nodes tested (Eq. 5),
-// nodes accepted as far (a chord each), evaluations of gamma(m) and the sum
-// of their segments' degrees.
+// control-point box tests of records whose ellipse held it; then per warp
+// (not per query slot): node visits and record iterations of the leaves,
+// each serving the warp's 32 * QPT query slots.  Then the tallies of the
+// counting build of the FP32 near walk: nodes tested (Eq. 5), nodes
+// accepted as far (a chord each), evaluations of gamma(m) and the sum of
+// their segments' degrees.
 enum { WK_NODE = 0, WK_TELE = 1, WK_EXPANSION = 2, WK_TERMS = 3, WK_REC_NEAR = 4, WK_REC_FAR = 5,
-       WK_REC_CROSS = 6, WK_EXACT = 7, WK_ELLIPSE = 8, WK_BOX = 9, WK_SWEEP_N = 10,
-       WK_NEAR_NODE = 10, WK_NEAR_FAR = 11, WK_NEAR_EVAL = 12, WK_NEAR_DEG = 13, WK_N = 14 };
+       WK_REC_CROSS = 6, WK_EXACT = 7, WK_ELLIPSE = 8, WK_BOX = 9, WK_WARP_NODE = 10, WK_WARP_REC = 11,
+       WK_SWEEP_N = 12, WK_NEAR_NODE = 12, WK_NEAR_FAR = 13, WK_NEAR_EVAL = 14, WK_NEAR_DEG = 15, WK_N = 16 };
 
 // FP32 walk depth: the cap is a tuning knob (the stack holds kDepthCap32Max
 // levels); Lemma 2 bounds the depth a pair needs by log2(B / max(eps, d)),
@@ -107,7 +109,13 @@ struct Tuning {
     int near_depth = 22;       // FP32 near-walk depth cap (kDepthCap32Min..kDepthCap32Max)
     int near_chunk = 128;      // near pairs a warp draws per atomic (32..1024, multiple of 32)
     int near_refill = 16;      // idle lanes that trigger a refill (1..32)
+    int flat_max = 0;          // planar domains with at most this many records take the flat sweep (0: none)
 };
+
+constexpr int kSweepThreads = 256;   // threads of a sweep CTA
+// Queries per thread of the flat sweep when it shares a batch with the tree
+// sweep (a unit is one CTA's kSweepThreads * kFlatQpt queries).
+constexpr int kFlatQpt = 2;
 
 constexpr int kProfEvents = 7;   // events per profiled mixed call (6 intervals)
 
@@ -118,6 +126,7 @@ struct LaunchCfg {
     unsigned long long *work = nullptr; // non-null: counting build of the tree sweep adds WK_* here
     bool grid_tiled = false;            // grid positions in 8 x 8 tiles instead of bucketing
     bool rational = false;              // some domain of the batch has rational segments
+    int n_flat = 0;                     // flat-sweep units after the tree units in the unit list
 };
 
 // Kernels (wn_kernels.cu)

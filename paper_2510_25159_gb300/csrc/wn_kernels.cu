@@ -46,7 +46,6 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr float kOmegaBandF = 1e-4f;               // classification band of the mixed path
 constexpr float kInv2PiF = 0.15915494309189533577f;
 constexpr float kInv2PiLoF = 6.4206382432985265e-09f;   // 1/(2 pi) - kInv2PiF
-constexpr int kSweepThreads = 256;
 constexpr int kChunk = 64;                          // records per shared-memory stage
 
 __device__ __forceinline__ void get_point(const PointSrc &s, uint32_t q, double &x, double &y)
@@ -122,6 +121,50 @@ __device__ __forceinline__ double exact_cross(double2 a, double2 b, double px, d
     return ax * by - ay * bx;
 }
 
+__device__ __forceinline__ void write_out(const OutDst &o, uint32_t q, double om, int st, bool atomic_bits)
+{
+    if (o.w) o.w[q] = om;
+    if (o.st) o.st[q] = (uint8_t)st;
+    if (o.bits && atomic_bits) {
+        if (st != 0) atomicOr(&o.bits[q >> 5], 1u << (q & 31));
+        if (st == 2 && o.nbound) atomicAdd(o.nbound, 1ull);
+    }
+}
+
+// The final step of one query in the mixed path (Sec. 4.1's decision, the
+// finalize kernel):
+// omega = a2 / 2 - theta / 2 pi from the doubled crossings and line halves
+// a2 and the sum of gap angles theta.  Returns the state (0 outside, 1
+// inside, 2 boundary) and omega in *om (when want_w), or -1 when the query
+// must be recomputed in FP64: a kernel flagged it, or omega lies within the
+// classification band of 1/2.  The classification runs in FP32 (its error,
+// ~1e-7 of the terms, is far inside the band); omega is formed as an exact
+// FP32 pair (product residual, TwoSum, 1/(2 pi) split in two floats) so
+// that its FP64 value costs one FP64 addition.
+__device__ __forceinline__ int settle(int32_t a2, float th, uint32_t f, bool want_w, double &om)
+{
+    om = 0.0;
+    if (f & QF_ESCALATE) return -1;
+    if (f & QF_BOUNDARY) {
+        om = __longlong_as_double(0x7ff8000000000000ULL);
+        return 2;
+    }
+    const float om32 = fmaf(-th, kInv2PiF, 0.5f * (float)a2);
+    const float band = kOmegaBandF + 1e-6f * (fabsf(0.5f * (float)a2) + fabsf(th) * kInv2PiF);
+    if (fabsf(om32 - 0.5f) < band) return -1;
+    if (want_w) {
+        const float h = 0.5f * (float)a2;
+        const float p = th * kInv2PiF;
+        const float pe = fmaf(th, kInv2PiF, -p);
+        const float s = h - p;
+        const float bb = s - h;
+        const float e = (h - (s - bb)) + (-p - bb);
+        const float lo = (e - pe) - th * kInv2PiLoF;
+        om = f32_to_f64_exact(s) + f32_to_f64_exact(lo);
+    }
+    return om32 >= 0.5f ? 1 : 0;
+}
+
 // ------------------------------------------------------------------ sweep
 struct SweepArgs {
     const DomDev *doms;
@@ -136,6 +179,7 @@ struct SweepArgs {
     long long cap_near;
     unsigned long long *counters;
     unsigned long long *work;   // WK_* tallies of the counting build, or null
+    int unit_ctr;               // the counter (CNT_*) the kernel's CTAs draw units from
 };
 
 // Exact recomputation of one record's crossings and gap angle in FP64, for a
@@ -386,14 +430,16 @@ __device__ __forceinline__ void sweep_record_cross(const float4 R0, const float4
 }
 
 // Sum of a node's gap angles at each of the QPT queries of a thread from the
-// node's Laurent expansion, Im sum_{k<K} c_k w^k with w = r_c / (z_c - p),
+// node's Laurent expansion, Im sum_{t<Kq} c_t w^t with w = r_c / (z_c - p),
 // by Horner's rule; slot k only when use[k] (uniform across the warp).  One
-// coefficient load per term serves every slot; K is a multiple of 4 and
-// uniform across the warp.
+// coefficient load per term serves every slot: the loop runs the warp's
+// largest K (a multiple of 4, uniform across the warp), and each slot adds
+// only its own terms t < kq[k] (the series length its query's distance
+// needs), so a query's sum does not depend on which queries share its warp.
 template <int QPT>
 __device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, const float *fx, const float *fy,
-                                              const float *fxl, const float *fyl, const bool *use, int K,
-                                              float *out)
+                                              const float *fxl, const float *fyl, const bool *use,
+                                              const int *kq, int K, float *out)
 {
     const float4 z = __ldg(N + 2);
     const float rc = __ldg(&N[3].x);
@@ -407,8 +453,9 @@ __device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, cons
         const float inv = __fdividef(rc, fmaf(dx, dx, dy * dy));
         wr[k] = dx * inv;
         wi[k] = -dy * inv;
-        sr[k] = cl.x;
-        si[k] = cl.y;
+        const bool own = K - 1 < kq[k];
+        sr[k] = own ? cl.x : 0.f;
+        si[k] = own ? cl.y : 0.f;
     }
 #pragma unroll 4
     for (int t = K - 2; t >= 0; t--) {
@@ -416,8 +463,10 @@ __device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, cons
 #pragma unroll
         for (int k = 0; k < QPT; k++) {
             if (!use[k]) continue;
-            const float tr = fmaf(sr[k], wr[k], fmaf(-si[k], wi[k], c.x));
-            const float ti = fmaf(sr[k], wi[k], fmaf(si[k], wr[k], c.y));
+            const bool own = t < kq[k];
+            const float cx = own ? c.x : 0.f, cy = own ? c.y : 0.f;
+            const float tr = fmaf(sr[k], wr[k], fmaf(-si[k], wi[k], cx));
+            const float ti = fmaf(sr[k], wi[k], fmaf(si[k], wr[k], cy));
             sr[k] = tr;
             si[k] = ti;
         }
@@ -438,9 +487,11 @@ __device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, cons
 //
 // The CNT build adds per-lane tallies of the work done (WK_*), summed per
 // warp into A.work when the warp runs out of units; its decisions and
-// arithmetic are those of the plain build.
-template <int QPT, bool CNT>
-__global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs A)
+// arithmetic are those of the plain build.  MINB CTAs per SM set the
+// register budget (64 registers at 4, 80 at 3, 128 at 2): fewer resident
+// warps, fewer spills.
+template <int QPT, bool CNT, int MINB>
+__global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepArgs A)
 {
     constexpr int SB = 2 * QPT;                     // status bits per level
     constexpr uint64_t SMASK = (1ull << SB) - 1ull;
@@ -453,9 +504,9 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint32_t wk[WK_N];
+    uint32_t wk[WK_SWEEP_N];
 #pragma unroll
-    for (int i = 0; i < WK_N; i++) wk[i] = 0u;
+    for (int i = 0; i < WK_SWEEP_N; i++) wk[i] = 0u;
 
     // every warp works on its own units (32*QPT queries): no block barrier.
     // A warp claims `batch` consecutive units per atomic on the shared
@@ -475,7 +526,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
         if (u >= A.n_units) {
             if constexpr (CNT) {
 #pragma unroll
-                for (int i = 0; i < WK_N; i++) {
+                for (int i = 0; i < WK_SWEEP_N; i++) {
                     const unsigned s = __reduce_add_sync(0xffffffffu, wk[i]);
                     if (lane == 0 && s) atomicAdd(&A.work[i], (unsigned long long)s);
                 }
@@ -503,7 +554,9 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
             if (valid[k]) {
                 const uint32_t pos = (uint32_t)(U.y + ql);
                 if (A.perm) {
-                    qid[k] = (uint32_t)__ldg(&A.perm[pos]);
+                    // bucketed: the unit's positions start at U.w in the
+                    // bucketed order (tree domains only)
+                    qid[k] = (uint32_t)__ldg(&A.perm[(uint32_t)(U.w + ql)]);
                 } else if (A.src.tiles_x) {
                     // grid in 8 x 8 tiles, row-major: position -> cell
                     const uint32_t t = pos >> 6, j = pos & 63u;
@@ -521,7 +574,10 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
             s_p[k][tid] = make_double2(x, y);
             // the query's FP64 work, once per query: p - o split into FP32
             // hi/lo pairs (each instance then subtracts its lattice shift in
-            // FP32), and the reduced point in FP32 for the window pre-tests
+            // FP32), and the reduced point in FP32 for the window pre-tests.
+            // (Conversions are cheaper here than the integer-instruction
+            // splits, measured.)  hi is p - o rounded, lo its remainder
+            // rounded: within 2^-48 |p - o|
             const double dx0 = x - ox, dy0 = y - oy;
             const float hx = (float)dx0, hy = (float)dy0;
             s_ph[k][tid] = make_float4(hx, (float)(dx0 - (double)hx), hy, (float)(dy0 - (double)hy));
@@ -649,16 +705,18 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
                         if (cur + 1 >= end) sp--;
                         const uint32_t f = (uint32_t)((lf >> (lvl * SB)) & SMASK);
                         if (!__any_sync(0xffffffffu, f != 0u)) continue;
+                        if constexpr (CNT) wk[WK_WARP_NODE] += lane == 0 ? 1u : 0u;
                         const float4 *__restrict__ N = nodes + (size_t)kCluF4 * cur;
                         const float4 nb = __ldg(N), yx = __ldg(N + 1), meta = __ldg(N + 3), sp6 = __ldg(N + 6);
                         const int nflags = __float_as_int(meta.y);
                         const bool gaps = nflags & 1, leaf = (nflags & 2) != 0;
                         uint32_t cf = 0u, nearb = 0u, mpb = 0u;
-                        int kneed = 0;
+                        int kneed = 0, kqs[QPT];
                         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (gaps) z = __ldg(N + 2);
 #pragma unroll
                         for (int k = 0; k < QPT; k++) {
+                            kqs[k] = 0;
                             const uint32_t sk = (f >> (2 * k)) & 3u;
                             if (!sk) continue;
                             if constexpr (CNT) wk[WK_NODE]++;
@@ -680,6 +738,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
                                         const int kq = d2 >= t0.x ? 4 : d2 >= t0.y ? 8 : d2 >= t0.z ? 12 : d2 >= t0.w ? 16
                                                      : d2 >= t1.x ? 20 : d2 >= t1.y ? 24 : d2 >= t1.z ? 28 : kCluTerms;
                                         kneed = max(kneed, kq);
+                                        kqs[k] = kq;
                                         mpb |= 1u << k;
                                     } else {
                                         full = true;
@@ -714,14 +773,14 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
 #pragma unroll
                                 for (int k = 0; k < QPT; k++) use[k] = __any_sync(0xffffffffu, (mpb >> k) & 1u);
                                 float gs[QPT];
-                                node_gap_sums<QPT>(N, fx, fy, fxl, fyl, use, K, gs);
+                                node_gap_sums<QPT>(N, fx, fy, fxl, fyl, use, kqs, K, gs);
 #pragma unroll
                                 for (int k = 0; k < QPT; k++)
                                     if (mpb >> k & 1u) {
                                         two_sum_add(th[k], thl[k], gs[k]);
                                         if constexpr (CNT) {
                                             wk[WK_EXPANSION]++;
-                                            wk[WK_TERMS] += (uint32_t)K;
+                                            wk[WK_TERMS] += (uint32_t)kqs[k];
                                         }
                                     }
                             }
@@ -756,6 +815,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_sweep_tree(const SweepArgs
 #pragma unroll
                         for (int k = 0; k < QPT; k++) tcl[k] = 0.f;
                         for (int r = r0; r < r1; r++) {
+                            if constexpr (CNT) wk[WK_WARP_REC] += lane == 0 ? 1u : 0u;
                             const float4 R0 = __ldg(rec + 4 * r), R1 = __ldg(rec + 4 * r + 1), R2 = __ldg(rec + 4 * r + 2);
                             if (wn) {
                                 const float4 R3 = __ldg(rec + 4 * r + 3);
@@ -1057,7 +1117,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[CNT_UNIT], 1ULL);
+        if (tid == 0) s_unit = (int)atomicAdd(&A.counters[A.unit_ctr], 1ULL);
         __syncthreads();
         const int u = s_unit;
         if (u >= A.n_units) return;
@@ -1116,6 +1176,13 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
                 any |= inc[k];
             }
             if (!__syncthreads_or(any)) continue;
+            if (A.work) {
+                // counting: every included query meets every record of the instance
+                int n_inc = 0;
+#pragma unroll
+                for (int k = 0; k < QPT; k++) n_inc += __syncthreads_count(inc[k]);
+                if (tid == 0) atomicAdd(&A.work[WK_REC_NEAR], (unsigned long long)n_inc * (unsigned long long)(in.r1 - in.r0));
+            }
             for (int r0 = in.r0; r0 < in.r1; r0 += kChunk) {
                 const int cnt = min(kChunk, in.r1 - r0);
                 for (int i = tid; i < 4 * cnt; i += kSweepThreads) s_rec[i] = __ldg(rec + 4 * r0 + i);
@@ -1281,8 +1348,13 @@ __device__ __noinline__ float2 near_eval_rat(float4 x0, float4 x1, float4 y0, fl
 // Set up the walk of one near pair.  Returns false when the item needs no
 // walk (already decided: *result 0 done, 1 boundary).  The query-relative
 // control points come from FP32 hi/lo pairs (control point and query, both
-// relative to the domain origin), within 2^-24 |q| + 2^-46 (|P - o| + |p - o|)
-// of P - p: the second term, below 2^-44 M, joins the evaluation bound E.
+// relative to the domain origin), within 2^-24 |q| + eabs of P - p: the
+// control point's pair is within 2^-48 |P - o| <= 2^-48 M, the query's
+// (p - o split by rounding, within 2^-48 |p - o|, then the lattice shift T
+// subtracted in double-float arithmetic, within 2^-47 (|p - o| + |T|) more)
+// within 2^-46 (|p' - o| + 2 |T|) <= 2^-46 (Mq + 2 Tm), with Mq = 2 M (a
+// query beyond Mq goes to FP64); eabs = 2^-44 (6 M + 2 Tm) covers both and
+// joins the evaluation bound E.
 template <bool RAT>
 __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S,
                                            int &result)
@@ -1304,7 +1376,7 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
             W.qy[k] = 0.f;
         }
     }
-    const float eabs = kTwoM44 * 4.f * Dp->M;
+    const float eabs = kTwoM44 * (6.f * Dp->M + 2.f * Dp->Tm);
     // the endpoint signs must be those of the exact differences (the sweep
     // decides the same vertices exactly): inside the representation error,
     // the pair goes to FP64, which takes them from the FP64 control points
@@ -1595,15 +1667,6 @@ __device__ void plain_query(const DomDev *Dp, double x0, double y0, double &om, 
     }
 }
 
-__device__ __forceinline__ void write_out(const OutDst &o, uint32_t q, double om, int st, bool atomic_bits)
-{
-    if (o.w) o.w[q] = om;
-    if (o.st) o.st[q] = (uint8_t)st;
-    if (o.bits && atomic_bits) {
-        if (st != 0) atomicOr(&o.bits[q >> 5], 1u << (q & 31));
-        if (st == 2 && o.nbound) atomicAdd(o.nbound, 1ull);
-    }
-}
 
 __global__ void __launch_bounds__(128) k_plain(const DomDev *Dp, long long q0, long long n,
                                                PointSrc src, OutDst out, unsigned long long *counters)
@@ -1656,35 +1719,8 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs A)
         double om = 0.0;
         bool esc = false;
         if (in_range) {
-            const uint32_t f = A.flags[q];
-            if (f & QF_ESCALATE) {
-                esc = true;
-            } else if (f & QF_BOUNDARY) {
-                st = 2;
-                om = __longlong_as_double(0x7ff8000000000000ULL);
-            } else {
-                // classify in FP32 (its error, ~1e-7 of the terms, is far
-                // inside the band); omega itself in FP64 only when asked for
-                const int a2 = A.acc2[q];
-                const float th = A.theta[q];
-                const float om32 = fmaf(-th, kInv2PiF, 0.5f * (float)a2);
-                const float band = kOmegaBandF + 1e-6f * (fabsf(0.5f * (float)a2) + fabsf(th) * kInv2PiF);
-                if (fabsf(om32 - 0.5f) < band) esc = true;
-                st = om32 >= 0.5f ? 1 : 0;
-                // omega = a2/2 - theta/(2 pi) as an FP32 pair hi + lo (exact
-                // product residual, TwoSum, 1/(2 pi) split in two floats), so
-                // its FP64 value costs one FP64 addition
-                if (A.out.w) {
-                    const float h = 0.5f * (float)a2;
-                    const float p = th * kInv2PiF;
-                    const float pe = fmaf(th, kInv2PiF, -p);
-                    const float s = h - p;
-                    const float bb = s - h;
-                    const float e = (h - (s - bb)) + (-p - bb);
-                    const float lo = (e - pe) - th * kInv2PiLoF;
-                    om = f32_to_f64_exact(s) + f32_to_f64_exact(lo);
-                }
-            }
+            st = settle(A.acc2[q], A.theta[q], A.flags[q], A.out.w != nullptr, om);
+            esc = st < 0;
             if (esc) {
                 const unsigned long long idx = atomicAdd(&A.counters[CNT_ESC], 1ULL);
                 A.esc[idx] = make_uint2(q, find_dom(A.offsets, A.n_doms, (long long)q));
@@ -1911,7 +1947,7 @@ bool mixed_buckets(const Work &W, const LaunchCfg &cfg)
 
 int mixed_kernel_count(const Work &W, const LaunchCfg &cfg)
 {
-    return 5 + (mixed_buckets(W, cfg) ? 5 : 0);
+    return 5 + (mixed_buckets(W, cfg) ? 5 : 0) + (cfg.tun.tree && cfg.n_flat > 0 ? 1 : 0);
 }
 
 cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const int4 *d_units,
@@ -1971,16 +2007,33 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     sa.cap_near = W.cap_near;
     sa.counters = W.counters;
     sa.work = cfg.work;
+    sa.unit_ctr = CNT_UNIT;
     const int sweep_grid = max(1, min(n_units, cfg.n_sm * cfg.tun.sweep_ctas_per_sm));
     mark(1);
+    if (cfg.tun.tree && cfg.n_flat > 0) {
+        // the small planar domains: the flat sweep over their own units
+        SweepArgs fa_ = sa;
+        fa_.units = d_units + n_units;
+        fa_.n_units = cfg.n_flat;
+        fa_.perm = nullptr;
+        fa_.unit_ctr = CNT_FLAT_UNIT;
+        k_sweep<kFlatQpt><<<max(1, min(cfg.n_flat, cfg.n_sm * 3)), kSweepThreads, 0, s>>>(fa_);
+    }
     if (cfg.tun.tree) {
-        // the level flags fit 2 slots
+        // the level flags fit 2 slots; the register budget follows the CTAs
+        // per SM (2: 128 registers, 3: 80, more: 64)
+        const int cps = cfg.tun.sweep_ctas_per_sm;
         if (cfg.work) {
-            if (cfg.tun.qpt == 1) k_sweep_tree<1, true><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
-            else k_sweep_tree<2, true><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            if (cfg.tun.qpt == 1) k_sweep_tree<1, true, 4><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            else k_sweep_tree<2, true, 4><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+        } else if (cfg.tun.qpt == 1) {
+            if (cps <= 2) k_sweep_tree<1, false, 2><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            else if (cps == 3) k_sweep_tree<1, false, 3><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            else k_sweep_tree<1, false, 4><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
         } else {
-            if (cfg.tun.qpt == 1) k_sweep_tree<1, false><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
-            else k_sweep_tree<2, false><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            if (cps <= 2) k_sweep_tree<2, false, 2><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            else if (cps == 3) k_sweep_tree<2, false, 3><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
+            else k_sweep_tree<2, false, 4><<<sweep_grid, kSweepThreads, 0, s>>>(sa);
         }
     } else {
         switch (cfg.tun.qpt) {

@@ -64,11 +64,12 @@ def test_validation_codes_without_gpu(wnlib):
     assert L.wn_set_near_tuning(5, 0, 0) == 1 and L.wn_set_near_tuning(31, 0, 0) == 1
     assert L.wn_set_near_tuning(0, 33, 0) == 1 and L.wn_set_near_tuning(0, 0, 40) == 1
     assert L.wn_set_queue_limits(-1, 0) == 1
+    assert L.wn_set_flat_records(-1) == 1 and L.wn_set_flat_records(5000) == 1
     assert L.wn_get_tuning(None, 3) == 1
     assert L.wn_last_escalated(None, 0, None) == 1
     assert L.wn_eval_gap_angle(None, None, None, -1, None) == 1
     assert L.wn_near_work(None) == 1
-    assert L.wn_sweep_work(None) == 1
+    assert L.wn_sweep_work(None, 12) == 1
     assert L.wn_grid_triangles(None, 4, 4, 0, 0, None, 0, None, None) == 1
     assert L.wn_query_midpoints(None, None, 3, None, 1, None) == 1
     assert L.wn_query_surfaces(None, None, 1, None, None, None, 1, None) == 1

@@ -68,6 +68,9 @@ def test_noalloc_matches_wn_query_twice(wn):
         ok = s_ref != wn.BOUNDARY
         assert np.max(np.abs(w[ok] - w_ref[ok])) <= TOL_MIXED
         assert np.all(np.isnan(w[~ok]))
+        # each query's arithmetic is its own, whatever queries share a warp:
+        # the windings are in fact identical
+        assert np.array_equal(w, w_ref, equal_nan=True)
         h.close()
 
 
