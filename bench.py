@@ -361,6 +361,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--qpt", type=int, default=0, help="queries per sweep thread (profiling cases; 0: tuned)")
+    ap.add_argument("--ctas", type=int, default=0, help="sweep CTAs per SM (profiling cases; 0: tuned)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -404,6 +406,8 @@ def main():
     torch.cuda.set_stream(stream)
     if not grid and not args.no_autotune:
         wn.autotune(handles, pts, off, iterations=2, stream=stream)
+    if args.qpt or args.ctas:
+        wn.set_tuning(qpt=args.qpt, sweep_ctas_per_sm=args.ctas)
 
     def step(prec=wn.MIXED):
         if grid:

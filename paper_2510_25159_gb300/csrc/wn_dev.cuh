@@ -102,7 +102,8 @@ struct DomDev {
     float M;                    // max |P - o|_inf over lifted control points
     float Tm;                   // max |lattice shift|_inf over the instances (0 planar)
     float Mq;                   // queries with |p' - o|_inf > Mq go to FP64
-    float pad1;
+    float Om;                   // max(|ox|, |oy|)
+    float oxh, oxl, oyh, oyl;   // the origin as FP32 pairs (to ~2^-48)
     const int *seg_deg;         // [n_segs]
     const int *seg_cp;          // [n_segs] first control point (in points)
     const double *cp;           // [2 * total_cp] lifted control points

@@ -638,6 +638,11 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     dv.nx = nx; dv.ny = ny; dv.PP = PP;
     dv.M = (float)M;
     dv.Mq = (float)Mq;
+    dv.Om = (float)std::fmax(std::fabs(ox), std::fabs(oy));
+    dv.oxh = (float)ox;
+    dv.oxl = (float)(ox - (double)dv.oxh);
+    dv.oyh = (float)oy;
+    dv.oyl = (float)(oy - (double)dv.oyh);
     dv.seg_deg = up.up(seg_deg);
     dv.seg_cp = up.up(seg_cp);
     dv.cp = up.up(P);

@@ -96,6 +96,20 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x)
     return __uint_as_float(sign | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
+// The remainder x - f64_to_f32_trunc(x) (the low 29 bits of x's fraction)
+// as an FP32 value, with integer instructions and one conversion: within
+// 2^-24 of itself, so the pair (trunc, remainder) is x within 2^-47 |x|.
+// For |x| < 2^-74 the remainder (below 2^-97) is dropped; for |x| >= 2^180
+// it is not formed (such a query is escalated).
+__device__ __forceinline__ float f64_rem_f32(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    if (e < 949 || e > 1202) return 0.f;
+    const float r = __uint2float_rn((uint32_t)b & 0x1fffffffu) * __int_as_float((e - 948) << 23);   // * 2^(e-1075)
+    return (b >> 63) ? -r : r;
+}
+
 // An interval of FP32 values around a truncated coordinate r (within 2^-23
 // of the double it came from, or below 2^-126) that holds that double.
 __device__ __forceinline__ float pt_lo(float r) { return r - fabsf(r) * 2.384185791015625e-7f - 1e-30f; }
@@ -535,7 +549,7 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
         }
         const int4 U = __ldg(&A.units[u]);
         const DomDev *__restrict__ Dp = A.doms + U.x;
-        const double Pu = Dp->Pu, Pv = Dp->Pv, ox = Dp->ox, oy = Dp->oy;
+        const double Pu = Dp->Pu, Pv = Dp->Pv;
         const float M = Dp->M, Mq = Dp->Mq;
         const int n_inst = Dp->n_inst;
         const float4 *__restrict__ rec = Dp->rec;
@@ -545,6 +559,20 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
         int acc[QPT];
         uint32_t fl[QPT], qid[QPT];
         bool valid[QPT], inc[QPT];
+        // the next unit of the warp's claimed run: its queries' permutation
+        // entries are read now, and their points prefetched into L2 once this
+        // unit's own points have arrived, so that the next unit does not
+        // start with a DRAM round trip (the points of a bucketed batch are
+        // read in a scattered order)
+        int nq_next[QPT];
+#pragma unroll
+        for (int k = 0; k < QPT; k++) nq_next[k] = -1;
+        if (A.perm && u_next < u_end && u_next < A.n_units) {
+            const int4 Un = __ldg(&A.units[u_next]);
+#pragma unroll
+            for (int k = 0; k < QPT; k++)
+                if (lane * QPT + k < Un.z) nq_next[k] = __ldg(&A.perm[(uint32_t)(Un.w + lane * QPT + k)]);
+        }
 #pragma unroll
         for (int k = 0; k < QPT; k++) {
             const int ql = lane * QPT + k;          // the warp owns the unit's 32*QPT positions
@@ -572,21 +600,27 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
             x = reduce_period(x, Pu);
             y = reduce_period(y, Pv);
             s_p[k][tid] = make_double2(x, y);
-            // the query's FP64 work, once per query: p - o split into FP32
-            // hi/lo pairs (each instance then subtracts its lattice shift in
-            // FP32), and the reduced point in FP32 for the window pre-tests.
-            // (Conversions are cheaper here than the integer-instruction
-            // splits, measured.)  hi is p - o rounded, lo its remainder
-            // rounded: within 2^-48 |p - o|
-            const double dx0 = x - ox, dy0 = y - oy;
-            const float hx = (float)dx0, hy = (float)dy0;
-            s_ph[k][tid] = make_float4(hx, (float)(dx0 - (double)hx), hy, (float)(dy0 - (double)hy));
-            s_pr[k][tid] = make_float2(f64_to_f32_trunc(x), f64_to_f32_trunc(y));
+            // the query in FP32 without FP64 instructions (GB300's FP64
+            // unit is narrow and every query passes here): p as a truncated
+            // FP32 value (the window pre-tests' point) plus its remainder,
+            // then p - o as an FP32 pair by TwoSum against the origin's pair;
+            // each instance then subtracts its lattice shift the same way.
+            // Within 2^-46 (|p - o| + |o|) of p - o.
+            const float xt = f64_to_f32_trunc(x), yt = f64_to_f32_trunc(y);
+            float hx, lx, hy, ly;
+            df_sub(xt, f64_rem_f32(x), Dp->oxh, Dp->oxl, hx, lx);
+            df_sub(yt, f64_rem_f32(y), Dp->oyh, Dp->oyl, hy, ly);
+            s_ph[k][tid] = make_float4(hx, lx, hy, ly);
+            s_pr[k][tid] = make_float2(xt, yt);
             acc[k] = 0;
             th[k] = 0.f;
             thl[k] = 0.f;
             fl[k] = 0u;
         }
+#pragma unroll
+        for (int k = 0; k < QPT; k++)
+            if (nq_next[k] >= 0)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.src.pts + 2 * (size_t)nq_next[k]));
         // warp box of the reduced queries (FP32, rounded outward): instances
         // whose window misses it are skipped by the whole warp, 32 tested
         // per round (a domain with one instance needs no test).  The box
@@ -787,10 +821,16 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
                         }
                         if (!leaf) {
                             if (__any_sync(0xffffffffu, cf != 0u)) {
+                                // the children are visited next: one lane per
+                                // child starts its first 128 bytes (the tests'
+                                // data) towards L1, all in flight at once
+                                const int c0 = __float_as_int(meta.z), c1 = __float_as_int(meta.w);
+                                if (lane < c1 - c0)
+                                    asm volatile("prefetch.global.L1 [%0];" ::"l"(nodes + (size_t)kCluF4 * (c0 + lane)));
                                 sp++;
                                 if (lane == sp) {
-                                    st_cur = __float_as_int(meta.z);
-                                    st_end = __float_as_int(meta.w);
+                                    st_cur = c0;
+                                    st_end = c1;
                                     st_lvl = lvl + 1;
                                 }
                                 const int sh = (lvl + 1) * SB;
@@ -811,14 +851,22 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
                         const bool wc = __any_sync(0xffffffffu, need_cross);
                         if (!we && !wc) continue;
                         const int r0 = __float_as_int(meta.z), r1 = __float_as_int(meta.w);
+                        // the leaf's records (64 bytes each), one 128-byte
+                        // line per lane, all in flight before the record loop
+                        if (lane < (r1 - r0 + 1) / 2)
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + 4 * (size_t)(r0 + 2 * lane)));
                         float tcl[QPT];
 #pragma unroll
                         for (int k = 0; k < QPT; k++) tcl[k] = 0.f;
                         for (int r = r0; r < r1; r++) {
                             if constexpr (CNT) wk[WK_WARP_REC] += lane == 0 ? 1u : 0u;
-                            const float4 R0 = __ldg(rec + 4 * r), R1 = __ldg(rec + 4 * r + 1), R2 = __ldg(rec + 4 * r + 2);
+                            // the gap data (R2, R3) only where the leaf has gaps
+                            // (closed C0 loops have none)
+                            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                            const float4 R0 = __ldg(rec + 4 * r), R1 = __ldg(rec + 4 * r + 1),
+                                         R2 = gaps ? __ldg(rec + 4 * r + 2) : z4;
                             if (wn) {
-                                const float4 R3 = __ldg(rec + 4 * r + 3);
+                                const float4 R3 = gaps ? __ldg(rec + 4 * r + 3) : z4;
                                 bool nr[QPT];
                                 bool any_near = false;
 #pragma unroll
@@ -877,7 +925,7 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
                                     }
                                 }
                             } else if (we) {
-                                const float4 R3 = __ldg(rec + 4 * r + 3);
+                                const float4 R3 = gaps ? __ldg(rec + 4 * r + 3) : z4;
 #pragma unroll
                                 for (int k = 0; k < QPT; k++) {
                                     const uint32_t ck = (cf >> (2 * k)) & 3u;
@@ -1350,11 +1398,12 @@ __device__ __noinline__ float2 near_eval_rat(float4 x0, float4 x1, float4 y0, fl
 // control points come from FP32 hi/lo pairs (control point and query, both
 // relative to the domain origin), within 2^-24 |q| + eabs of P - p: the
 // control point's pair is within 2^-48 |P - o| <= 2^-48 M, the query's
-// (p - o split by rounding, within 2^-48 |p - o|, then the lattice shift T
-// subtracted in double-float arithmetic, within 2^-47 (|p - o| + |T|) more)
-// within 2^-46 (|p' - o| + 2 |T|) <= 2^-46 (Mq + 2 Tm), with Mq = 2 M (a
-// query beyond Mq goes to FP64); eabs = 2^-44 (6 M + 2 Tm) covers both and
-// joins the evaluation bound E.
+// (p - o from p's truncation and remainder and the origin's pair, within
+// 2^-46 (|p - o| + |o|), then the lattice shift T subtracted in
+// double-float arithmetic, within 2^-47 (|p - o| + |T|) more) within
+// 2^-45 (|p' - o| + 2 |T| + |o|) <= 2^-45 (Mq + 2 Tm + Om), with Mq = 2 M (a
+// query beyond Mq goes to FP64) and Om = |o|; eabs = 2^-44 (6 M + 2 Tm +
+// Om) covers both and joins the evaluation bound E.
 template <bool RAT>
 __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, NearWalk &W, NearStack &S,
                                            int &result)
@@ -1376,7 +1425,7 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
             W.qy[k] = 0.f;
         }
     }
-    const float eabs = kTwoM44 * (6.f * Dp->M + 2.f * Dp->Tm);
+    const float eabs = kTwoM44 * (6.f * Dp->M + 2.f * Dp->Tm + Dp->Om);
     // the endpoint signs must be those of the exact differences (the sweep
     // decides the same vertices exactly): inside the representation error,
     // the pair goes to FP64, which takes them from the FP64 control points
