@@ -1007,6 +1007,20 @@ struct BinArgs {
 constexpr int kBinChunk = 4096;     // cells per block of the chunked scan
 constexpr int kBinThreads = 512;
 
+// v rounded to the nearest integer by FP32 addition (ties to even), for
+// -2^22 <= v < 2^22 (other values, NaN included, are clamped into that
+// range first; the callers clamp the result again): as a float and an int.
+__device__ __forceinline__ float round_near(float v)
+{
+    const float m = 12582912.0f;    // 1.5 * 2^23
+    return fminf(fmaxf(v, -4194304.f), 4194303.f) + m - m;
+}
+__device__ __forceinline__ int round_near_int(float v)
+{
+    const float t = fminf(fmaxf(v, -4194304.f), 4194303.f) + 12582912.0f;
+    return (__float_as_int(t) & 0x7fffff) - 0x400000;
+}
+
 // Cell of every query, counted per cell.  One CTA per run of one domain's
 // queries: the run is counted into the domain's cells in shared memory, then
 // one global atomic per non-empty cell adds the run's counts.
@@ -1036,9 +1050,13 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const BinArgs A)
             double x, y;
             get_point(A.src, q, x, y);
             float xf = f64_to_f32_trunc(x), yf = f64_to_f32_trunc(y);
-            if (pu) xf -= floorf(xf * ipu) * wx;
-            if (pv) yf -= floorf(yf * ipv) * wy;
-            int cx = (int)floorf((xf - x0) * sx), cy = (int)floorf((yf - y0) * sy);
+            // integer parts by FP32 rounding (no conversion instructions,
+            // which share GB300's narrow FP64 unit): round_near(v) is the
+            // low bits of v + 1.5 * 2^23 for |v| < 2^22; a cell choice needs
+            // neither floor nor exactness, only the clamp below
+            if (pu) xf -= round_near(xf * ipu - 0.5f) * wx;
+            if (pv) yf -= round_near(yf * ipv - 0.5f) * wy;
+            int cx = round_near_int((xf - x0) * sx - 0.5f), cy = round_near_int((yf - y0) * sy - 0.5f);
             cx = min(max(cx, 0), G - 1);
             cy = min(max(cy, 0), G - 1);
             const int lc = cy * G + ((cy & 1) ? G - 1 - cx : cx);      // serpentine order

@@ -548,6 +548,42 @@ def pin_cylinder_unfold(L, seed=28):
         assert np.max(np.abs(w2[ok] - w[ok])) < 1e-9, axis
 
 
+def pin_sphere_cone_puncture(L, seed=29):
+    """Sec. 4.3: a sphere or cone whose singular points (poles, apex) are
+    removed from the parameter domain is a cylinder.  One non-contractible
+    loop bounds the region holding a removed point, and the removed point
+    itself is the region's second boundary: its line in the parameter domain
+    (pole latitude, apex distance 0) is passed as a loop, as B-Rep models
+    store a degenerate edge there.  The cap north of a wavy latitude curve
+    (less a hole across the seam) and, on a cone, the apex region plus an
+    outer band: omega is the indicator of the face (the line terms of the
+    two separation loops, +-1/2 each, Eq. 9), read from the geometry of
+    points sampled on the surface."""
+    rng = np.random.default_rng(seed)
+    loops, hc, hr = ws.sphere_cap_face(rng)
+    dom = ws.make_domain(loops, TWO_PI, 0.0, eps=1e-9)
+    p = ws.sphere_points(rng, 4000)
+    curve = 0.35 + 0.15 * np.sin(3 * p[:, 0])
+    du = np.mod(p[:, 0] - hc[0] + np.pi, TWO_PI) - np.pi
+    dh = np.hypot(du, p[:, 1] - hc[1])
+    keep = (np.abs(p[:, 1] - curve) > 2e-3) & (np.abs(dh - hr) > 2e-3) & (p[:, 1] < 0.5 * np.pi - 2e-3)
+    w, st = oracle.query(dom, p[keep], threads=1, L=L)
+    exp = ((p[keep, 1] > curve[keep]) & (dh[keep] > hr)).astype(float)
+    assert np.all(st != 2)
+    assert np.array_equal(st, (exp > 0).astype(st.dtype))
+    assert np.max(np.abs(w - exp)) < 1e-9, np.max(np.abs(w - exp))
+    cone = ws.make_domain(ws.cone_face(), TWO_PI, 0.0, eps=1e-9)
+    q = np.stack([rng.uniform(0, TWO_PI, 4000), np.sqrt(rng.uniform(1e-6, 1, 4000))], axis=1)   # area-uniform on the cone
+    t0 = 0.3 + 0.05 * np.sin(2 * q[:, 0])
+    keep = (np.abs(q[:, 1] - t0) > 2e-3) & (np.abs(q[:, 1] - 0.8) > 2e-3) & (np.abs(q[:, 1] - 1.0) > 2e-3) & \
+        (q[:, 1] > 2e-3)
+    w, st = oracle.query(cone, q[keep], threads=1, L=L)
+    exp = ((q[keep, 1] < t0[keep]) | ((q[keep, 1] > 0.8) & (q[keep, 1] < 1.0))).astype(float)
+    assert np.all(st != 2)
+    assert np.array_equal(st, (exp > 0).astype(st.dtype))
+    assert np.max(np.abs(w - exp)) < 1e-9, np.max(np.abs(w - exp))
+
+
 def pin_lift_homology(L, seed=26):
     """Lifting reconnects per-segment wrapped loops: each lifted segment
     starts where the previous ended and the homology is the generated
@@ -820,5 +856,6 @@ PLANAR_PINS = [pin_polygon_exact, pin_single_chord, pin_circles, pin_hull_oracle
 RATIONAL_PINS = [pin_rational_circle_arcs, pin_rational_bound, pin_rational_dense_polyline,
                  pin_rational_invariants, pin_control_box_far]
 PERIODIC_PINS = [pin_cylinder_closed_form, pin_torus_bands, pin_lattice_translate,
-                 pin_window_enlargement, pin_unfold_3x3, pin_cylinder_unfold, pin_lift_homology, pin_errors]
+                 pin_window_enlargement, pin_unfold_3x3, pin_cylinder_unfold, pin_sphere_cone_puncture, pin_lift_homology,
+                 pin_errors]
 ALL_PINS = PLANAR_PINS + RATIONAL_PINS + PERIODIC_PINS

@@ -160,28 +160,41 @@ def test_grid_bitmask(wn, nu, nv):
 
 
 def test_workload5_full_face_sampled(wn):
-    """One face of the tessellation workload at full size (~100k cubics,
-    4096 x 4096 cells): the bitmask on sampled cells, on cells next to the
-    curves, and the boundary count's consistency."""
+    """Faces of the tessellation workload at full size (~100k cubics,
+    4096 x 4096 cells): the bitmask against the oracle on stratified cells,
+    on every cell the GPU recomputed in FP64, on cells next to a change of
+    state (the cells nearest the curves) and on cells around control
+    points; the boundary count is consistent."""
     import torch
-    dom = ws.config5_face(3)
-    h = wn.Domain.from_dict(dom)
-    bits, nb = wn.query_grid_bitmask(h, 4096, 4096, precision=1)
-    torch.cuda.synchronize()
-    b = bits.cpu().numpy().view(np.uint32)
-    h.close()
-    rng = np.random.default_rng(11)
-    cells = rng.choice(4096 * 4096, 600, replace=False)
-    # cells whose centre is within two cells of a control point (near the curves)
-    cp = dom["cps"][rng.choice(len(dom["cps"]), 200, replace=False)]
-    ij = np.clip(np.floor(cp * 4096).astype(np.int64) + rng.integers(-2, 3, cp.shape), 0, 4095)
-    cells = np.unique(np.concatenate([cells, ij[:, 1] * 4096 + ij[:, 0]]))
-    pts = np.stack([((cells % 4096) + 0.5) / 4096, ((cells // 4096) + 0.5) / 4096], axis=1)
     from oracle import query
-    ow, osd = query(dom, pts)
-    got = (b[cells >> 5] >> (cells & 31).astype(np.uint32)) & 1
-    assert np.array_equal(got, (osd != 0).astype(np.uint32))
-    assert 0 <= int(nb.item()) < 4096 * 4096
+    G = 4096
+    rng = np.random.default_rng(11)
+    for face in (3, 17):
+        dom = ws.config5_face(face)
+        h = wn.Domain.from_dict(dom)
+        bits, nb = wn.query_grid_bitmask(h, G, G, precision=1)
+        torch.cuda.synchronize()
+        esc = wn.last_escalated()
+        b = bits.cpu().numpy().view(np.uint32)
+        h.close()
+        k = np.arange(G * G, dtype=np.int64)
+        v = ((b[k >> 5] >> (k & 31).astype(np.uint32)) & 1).reshape(G, G)
+        edge = np.zeros_like(v, dtype=bool)
+        edge[:, :-1] |= v[:, 1:] != v[:, :-1]
+        edge[:-1, :] |= v[1:, :] != v[:-1, :]
+        cand = np.flatnonzero(edge)
+        rows = (np.arange(512) * G) // 512 + rng.integers(0, G // 512, 512)
+        strat = rows * G + rng.integers(0, G, 512)
+        cp = dom["cps"][rng.choice(len(dom["cps"]), 200, replace=False)]
+        ij = np.clip(np.floor(cp * G).astype(np.int64) + rng.integers(-2, 3, cp.shape), 0, G - 1)
+        cells = np.unique(np.concatenate([strat, ij[:, 1] * G + ij[:, 0], esc[:2000],
+                                          rng.choice(cand, min(len(cand), 600), replace=False)]))
+        pts = np.stack([((cells % G) + 0.5) / G, ((cells // G) + 0.5) / G], axis=1)
+        ow, osd, om = query(dom, pts, margins=True)
+        got = (b[cells >> 5] >> (cells & 31).astype(np.uint32)) & 1
+        bad = (got != (osd != 0).astype(np.uint32)) & (om >= 1e-12)
+        assert not bad.any(), (face, int(bad.sum()))
+        assert 0 <= int(nb.item()) < G * G
 
 
 def test_edge_cases(wn):
@@ -385,3 +398,31 @@ def test_flat_sweep_for_small_planar_faces(wn, flat):
         wn.set_flat_records(saved)
     for d, q, (w, s) in zip(doms, qs, res):
         compare(d, q, w, s, TOL_MIXED, closed=True)
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_sphere_cone_punctured(wn, name, prec, tol):
+    """Sphere and cone faces with their singular points punctured (Sec. 4.3):
+    cylinders in the parameter domain, each removed point passed as the
+    degenerate boundary loop B-Rep models store; queries sampled on the
+    surfaces, against the oracle and the faces' closed forms."""
+    rng = np.random.default_rng(30)
+    loops, hc, hr = ws.sphere_cap_face(rng)
+    sphere = ws.make_domain(loops, ws.TWO_PI, 0.0, eps=1e-9)
+    cone = ws.make_domain(ws.cone_face(), ws.TWO_PI, 0.0, eps=1e-9)
+    ps = ws.sphere_points(rng, 20011)
+    pc = np.stack([rng.uniform(0, ws.TWO_PI, 15013), np.sqrt(rng.uniform(1e-6, 1, 15013))], axis=1)
+    res = run(wn, [sphere, cone], [ps, pc], prec)
+    for d, q, (w, s) in zip([sphere, cone], [ps, pc], res):
+        compare(d, q, w, s, tol, closed=True)
+    (ws_, ss), (wc, sc) = res
+    curve = 0.35 + 0.15 * np.sin(3 * ps[:, 0])
+    du = np.mod(ps[:, 0] - hc[0] + np.pi, ws.TWO_PI) - np.pi
+    dh = np.hypot(du, ps[:, 1] - hc[1])
+    far = (np.abs(ps[:, 1] - curve) > 1e-3) & (np.abs(dh - hr) > 1e-3) & (ps[:, 1] < 0.5 * np.pi - 1e-3)
+    assert np.array_equal(ss[far], ((ps[far, 1] > curve[far]) & (dh[far] > hr)).astype(np.uint8))
+    t0 = 0.3 + 0.05 * np.sin(2 * pc[:, 0])
+    far = (np.abs(pc[:, 1] - t0) > 1e-3) & (np.abs(pc[:, 1] - 0.8) > 1e-3) & (np.abs(pc[:, 1] - 1.0) > 1e-3) & \
+        (pc[:, 1] > 1e-3)
+    exp = (pc[far, 1] < t0[far]) | ((pc[far, 1] > 0.8) & (pc[far, 1] < 1.0))
+    assert np.array_equal(sc[far], exp.astype(np.uint8))

@@ -414,6 +414,45 @@ def reverse_loop(segs):
     return [s[::-1].copy() for s in segs[::-1]]
 
 
+def sphere_cap_face(rng, v0=0.35, amp=0.15, k=3, m=24, hole=True):
+    """A trimmed sphere, parameterized by longitude u in [0, 2 pi) (periodic)
+    and latitude v in [-pi/2, pi/2], with the two poles (singular points of
+    the parameterization) removed, so that the domain is a cylinder (Sec. 4.3):
+    the face is the cap north of the wavy latitude curve
+    v = v0 + amp sin(k u) (one loop with homology (1, 0), traversed in +u so
+    the cap lies on its left) up to the punctured north pole, whose line
+    v = pi/2 is the cap's second boundary loop (traversed in -u; B-Rep models
+    store a degenerate edge there), less an optional small hole crossing the
+    seam.  Returns (loops wrapped per segment, hole centre, hole radius)."""
+    segs = wavy_line((0.0, v0), (TWO_PI, 0.0), (0.0, 1.0), amp, k, m)
+    pole = reverse_loop(wavy_line((0.0, 0.5 * math.pi), (TWO_PI, 0.0), (0.0, 1.0), 0.0, 1, 4))
+    loops = [segs, pole]
+    hc, hr = (0.05, v0 + 0.6), 0.12
+    if hole:
+        loops.append(circle_loop(hc, hr, 16, ccw=False))
+    return [_wrap_segments(lp, TWO_PI, 0.0) for lp in loops], hc, hr
+
+
+def sphere_points(rng, n):
+    """Points uniform on the unit sphere as (longitude in [0, 2 pi), latitude)."""
+    z = rng.uniform(-1.0, 1.0, n)
+    lon = rng.uniform(0.0, TWO_PI, n)
+    return np.stack([lon, np.arcsin(z)], axis=1)
+
+
+def cone_face(t0=0.3, t1=0.8, amp=0.05, k=2, m=16):
+    """A trimmed cone, parameterized by the angle u in [0, 2 pi) (periodic) and
+    the distance t from the apex, the apex (t = 0, a singular point) removed:
+    the face is the apex region 0 < t < t0 + amp sin(k u) (a loop traversed
+    in -u, the apex side on its left, and the punctured apex's line t = 0 in
+    +u) and the band t1 < t < 1 (a loop in +u at t1 and one in -u at 1)."""
+    apex = wavy_line((0.0, 0.0), (TWO_PI, 0.0), (0.0, 1.0), 0.0, 1, 4)
+    a = reverse_loop(wavy_line((0.0, t0), (TWO_PI, 0.0), (0.0, 1.0), amp, k, m))
+    b = wavy_line((0.0, t1), (TWO_PI, 0.0), (0.0, 1.0), 0.0, 1, 8)
+    c = reverse_loop(wavy_line((0.0, 1.0), (TWO_PI, 0.0), (0.0, 1.0), 0.0, 1, 8))
+    return [_wrap_segments(lp, TWO_PI, 0.0) for lp in (apex, a, b, c)]
+
+
 def swap_axes_loops(loops):
     """The same loops with u and v exchanged and each loop reversed: a face
     periodic in u becomes a face periodic in v with the same inside (the
