@@ -285,11 +285,11 @@ wn_status wn_autotune(const wn_domain *const *domains, int32_t n_domains,
                       const int64_t *point_offsets, const double *points, int32_t iterations,
                       double *best_ms, wn_stream stream);
 
-/* Current tuning: the first min(n_out, 11) of (queries per sweep thread,
+/* Current tuning: the first min(n_out, 12) of (queries per sweep thread,
  * sweep CTAs per SM, near-pair CTAs per SM, graph replay, tree sweep, bucket
  * cell size in queries, spatial bucketing on/off, FP32 near-walk depth cap,
- * near-pair draw, refill threshold, flat-sweep record limit) into out (host
- * int32[n_out]). */
+ * near-pair draw, refill threshold, flat-sweep record limit, grid tile
+ * width) into out (host int32[n_out]). */
 wn_status wn_get_tuning(int32_t *out, int32_t n_out);
 
 /*
@@ -319,6 +319,15 @@ wn_status wn_set_near_tuning(int32_t depth_cap, int32_t chunk, int32_t refill);
  * fast or faster for every limit tried.  Errors: WN_ERR_ARG outside 0..4096.
  */
 wn_status wn_set_flat_records(int32_t max_records);
+
+/*
+ * Tile shape of the grid queries (wn_query_grid_bitmask) in the tree sweep:
+ * a warp sweeps 64 cells, `width` wide (8, 16, 32 or 64) and 64 / width
+ * high.  Wide tiles keep a warp's queries on few rows, so their +x rays
+ * cross the same segments; square tiles keep them close to one another.
+ * Results do not depend on it.  Default 8.  Errors: WN_ERR_ARG.
+ */
+wn_status wn_set_grid_tile(int32_t width);
 
 /*
  * Test hook: caps on the near-pair and FP64-pair queues of the mixed path

@@ -78,6 +78,7 @@ def lib():
         L.wn_set_near_tuning.argtypes = [I32, I32, I32]
         L.wn_set_queue_limits.argtypes = [I64, I64]
         L.wn_set_flat_records.argtypes = [I32]
+        L.wn_set_grid_tile.argtypes = [I32]
         L.wn_near_work.argtypes = [P]
         L.wn_last_escalated.argtypes = [P, I64, P]
         L.wn_eval_gap_angle.argtypes = [P, P, P, I64, P]
@@ -89,7 +90,7 @@ def lib():
                   "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times", "wn_autotune",
                   "wn_get_tuning", "wn_set_work_counting", "wn_sweep_work", "wn_set_near_tuning",
                   "wn_set_queue_limits", "wn_near_work", "wn_last_escalated",
-                  "wn_eval_gap_angle", "wn_set_flat_records"):
+                  "wn_eval_gap_angle", "wn_set_flat_records", "wn_set_grid_tile"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -275,7 +276,7 @@ def autotune(domains, points, offsets, iterations=3, stream=None):
 
 
 TUNING = ("qpt", "sweep_ctas_per_sm", "near_ctas_per_sm", "use_graph", "tree", "cell_q", "bucket",
-          "near_depth", "near_chunk", "near_refill", "flat_max")
+          "near_depth", "near_chunk", "near_refill", "flat_max", "grid_tile_w")
 
 
 def get_tuning():
@@ -294,6 +295,11 @@ def set_flat_records(max_records):
     """Planar domains with at most max_records records take the flat sweep
     (0: none)."""
     _check(lib().wn_set_flat_records(int(max_records)))
+
+
+def set_grid_tile(width):
+    """Grid queries: tiles of 64 cells, `width` (8, 16, 32, 64) wide."""
+    _check(lib().wn_set_grid_tile(int(width)))
 
 
 def set_queue_limits(near_pairs=0, fp64_pairs=0):

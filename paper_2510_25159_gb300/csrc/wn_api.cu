@@ -302,6 +302,15 @@ wn_status wn_set_flat_records(int32_t max_records)
     return WN_OK;
 }
 
+wn_status wn_set_grid_tile(int32_t width)
+{
+    if (width != 8 && width != 16 && width != 32 && width != 64) return fail(WN_ERR_ARG, "width must be 8, 16, 32 or 64");
+    std::lock_guard<std::mutex> lk(g_mu);
+    drop_graphs();
+    g_tun.grid_tile_w = width;
+    return WN_OK;
+}
+
 wn_status wn_set_queue_limits(int64_t near_pairs, int64_t fp64_pairs)
 {
     if (near_pairs < 0 || fp64_pairs < 0) return fail(WN_ERR_ARG, "limits must be >= 0");
@@ -354,7 +363,8 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
         h_doms[d] = domains[d]->dev;
         flat[d] = flat_domain(domains[d], grid_tiled);
         // positions to sweep: the queries, or the cells of every tile of the grid
-        const int64_t cnt = grid_tiled ? (int64_t)src.tiles_x * ((grid_nv + 7) / 8) * 64 : offsets[d + 1] - offsets[d];
+        const int th = 64 >> src.tile_lw;
+        const int64_t cnt = grid_tiled ? (int64_t)src.tiles_x * ((grid_nv + th - 1) / th) * 64 : offsets[d + 1] - offsets[d];
         // sweep cost of one query of this domain: records of every instance
         const double work = (double)std::max<int64_t>(domains[d]->sweep_records, 1);
         const int64_t t = flat[d] ? (int64_t)kSweepThreads * kFlatQpt : tile;
@@ -516,11 +526,14 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
     out.nbound = reinterpret_cast<unsigned long long *>(nbound);
     PointSrc src = grid;
     src.pts = grid.nu ? nullptr : d_pts;
-    // a grid swept by the tree kernel walks 8 x 8 tiles of cells (spatially
-    // coherent warps without the bucketing kernels)
+    // a grid swept by the tree kernel walks tiles of 64 cells, w wide and
+    // 64 / w high (spatially coherent warps without the bucketing kernels;
+    // wide tiles share the rows, and so the +x rays' crossings)
+    const int tw = g_tun.grid_tile_w, th = 64 / tw;
     const bool grid_tiled = grid.nu > 0 && precision != WN_PREC_PLAIN_FP64 && g_tun.tree &&
-                            (int64_t)((grid.nu + 7) / 8) * ((grid.nv + 7) / 8) * 64 <= (int64_t)INT32_MAX;
-    src.tiles_x = grid_tiled ? (grid.nu + 7) / 8 : 0;
+                            (int64_t)((grid.nu + tw - 1) / tw) * ((grid.nv + th - 1) / th) * 64 <= (int64_t)INT32_MAX;
+    src.tiles_x = grid_tiled ? (grid.nu + tw - 1) / tw : 0;
+    src.tile_lw = tw == 64 ? 6 : tw == 32 ? 5 : tw == 16 ? 4 : 3;
 
     if (precision == WN_PREC_PLAIN_FP64) {
         if (bits && (e = cudaMemsetAsync(bits, 0, (size_t)((n + 31) / 32) * 4, stream)) != cudaSuccess)
@@ -541,8 +554,8 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
         const int qpt = g_tun.tree ? std::min(g_tun.qpt, 2) : g_tun.qpt;
         // the tree sweep gives each warp its own unit, the flat sweep each CTA
         const int64_t tile = (g_tun.tree ? 32LL : 256LL) * qpt;
-        const int key = (((qpt * 2 + (g_tun.tree ? 1 : 0)) * 4096 + g_tun.cell_q) * 2 + (grid_tiled ? 1 : 0)) * 8192 +
-                        std::min(g_tun.flat_max, 8191);
+        const int key = (((qpt * 2 + (g_tun.tree ? 1 : 0)) * 4096 + g_tun.cell_q) * 5 +
+                         (grid_tiled ? src.tile_lw - 2 : 0)) * 4096 + std::min(g_tun.flat_max, 4095);
         if (grouped) {
             // groups of consecutive domains with about n / G queries each
             const int G = n_groups;
@@ -842,10 +855,10 @@ wn_status wn_get_tuning(int32_t *out, int32_t n_out)
 {
     if (!out || n_out < 0) return fail(WN_ERR_ARG, "out is NULL or n_out < 0");
     std::lock_guard<std::mutex> lk(g_mu);
-    const int32_t v[11] = {g_tun.qpt, g_tun.sweep_ctas_per_sm, g_tun.near_ctas_per_sm, g_tun.use_graph,
+    const int32_t v[12] = {g_tun.qpt, g_tun.sweep_ctas_per_sm, g_tun.near_ctas_per_sm, g_tun.use_graph,
                            g_tun.tree, g_tun.cell_q, g_tun.bucket, g_tun.near_depth, g_tun.near_chunk,
-                           g_tun.near_refill, g_tun.flat_max};
-    for (int i = 0; i < n_out && i < 11; i++) out[i] = v[i];
+                           g_tun.near_refill, g_tun.flat_max, g_tun.grid_tile_w};
+    for (int i = 0; i < n_out && i < 12; i++) out[i] = v[i];
     return WN_OK;
 }
 

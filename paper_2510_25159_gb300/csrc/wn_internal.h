@@ -27,7 +27,8 @@ struct PointSrc {
     const double *pts;         // x,y interleaved, indexed by global query index
     int32_t nu, nv;            // grid mode when pts == nullptr
     double su, sv;             // grid scale (period or 1)
-    int32_t tiles_x;           // grid mode, tree sweep: positions walk 8 x 8 tiles, this many per row
+    int32_t tiles_x;           // grid mode, tree sweep: positions walk tiles of 64 cells, this many per row
+    int32_t tile_lw;           // log2 of the tile width in cells (the height is 64 / width)
 };
 
 // Output of a query call.
@@ -110,6 +111,7 @@ struct Tuning {
     int near_chunk = 128;      // near pairs a warp draws per atomic (32..1024, multiple of 32)
     int near_refill = 16;      // idle lanes that trigger a refill (1..32)
     int flat_max = 0;          // planar domains with at most this many records take the flat sweep (0: none)
+    int grid_tile_w = 8;       // grid queries: tile width in cells (8, 16, 32 or 64; 64 cells per tile)
 };
 
 constexpr int kSweepThreads = 256;   // threads of a sweep CTA

@@ -586,10 +586,11 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
                     // bucketed order (tree domains only)
                     qid[k] = (uint32_t)__ldg(&A.perm[(uint32_t)(U.w + ql)]);
                 } else if (A.src.tiles_x) {
-                    // grid in 8 x 8 tiles, row-major: position -> cell
-                    const uint32_t t = pos >> 6, j = pos & 63u;
-                    const uint32_t ci = (t % (uint32_t)A.src.tiles_x) * 8u + (j & 7u);
-                    const uint32_t cj = (t / (uint32_t)A.src.tiles_x) * 8u + (j >> 3);
+                    // grid in tiles of 64 cells (w x 64/w), row-major:
+                    // position -> cell
+                    const uint32_t t = pos >> 6, j = pos & 63u, lw = (uint32_t)A.src.tile_lw;
+                    const uint32_t ci = (t % (uint32_t)A.src.tiles_x << lw) + (j & ((1u << lw) - 1u));
+                    const uint32_t cj = (t / (uint32_t)A.src.tiles_x << (6u - lw)) + (j >> lw);
                     valid[k] = ci < (uint32_t)A.src.nu && cj < (uint32_t)A.src.nv;
                     qid[k] = valid[k] ? cj * (uint32_t)A.src.nu + ci : 0u;
                 } else {

@@ -65,6 +65,7 @@ def test_validation_codes_without_gpu(wnlib):
     assert L.wn_set_near_tuning(0, 33, 0) == 1 and L.wn_set_near_tuning(0, 0, 40) == 1
     assert L.wn_set_queue_limits(-1, 0) == 1
     assert L.wn_set_flat_records(-1) == 1 and L.wn_set_flat_records(5000) == 1
+    assert L.wn_set_grid_tile(12) == 1
     assert L.wn_get_tuning(None, 3) == 1
     assert L.wn_last_escalated(None, 0, None) == 1
     assert L.wn_eval_gap_angle(None, None, None, -1, None) == 1

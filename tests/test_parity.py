@@ -138,15 +138,18 @@ def test_workload4_batched_mixed_kinds(wn, name, prec, tol):
         compare(d, q, w, s, tol)
 
 
-@pytest.mark.parametrize("nu,nv", [(200, 137), (203, 61), (1, 9), (8, 8)])
-def test_grid_bitmask(wn, nu, nv):
-    """Cell-centre grids (ragged against the 8 x 8 tiles of the tree sweep),
-    mixed and plain, bit for bit against the oracle."""
+@pytest.mark.parametrize("nu,nv,tile", [(200, 137, 8), (203, 61, 8), (1, 9, 8), (8, 8, 8), (203, 61, 64),
+                                         (131, 70, 16), (65, 3, 32)])
+def test_grid_bitmask(wn, nu, nv, tile):
+    """Cell-centre grids (ragged against the tiles of the tree sweep, of
+    every width), mixed and plain, bit for bit against the oracle."""
     import torch
     dom = ws.config5_face(0, levels=8, n_holes=25, hole_segs=24)
     pts = ws.grid_points(nu, nv)
     from oracle import query
     ow, osd = query(dom, pts)
+    saved = wn.get_tuning()["grid_tile_w"]
+    wn.set_grid_tile(tile)
     for prec in (1, 0):
         h = wn.Domain.from_dict(dom)
         bits, nb = wn.query_grid_bitmask(h, nu, nv, precision=prec)
@@ -157,6 +160,7 @@ def test_grid_bitmask(wn, nu, nv):
         assert np.array_equal(got, (osd != 0).astype(np.uint32))
         assert int(nb.item()) == int((osd == 2).sum())
         h.close()
+    wn.set_grid_tile(saved)
 
 
 def test_workload5_full_face_sampled(wn):
