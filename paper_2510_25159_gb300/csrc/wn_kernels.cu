@@ -444,12 +444,14 @@ __device__ __forceinline__ void sweep_record_cross(const float4 R0, const float4
 }
 
 // Sum of a node's gap angles at each of the QPT queries of a thread from the
-// node's Laurent expansion, Im sum_{t<Kq} c_t w^t with w = r_c / (z_c - p),
+// node's Laurent expansion, Im sum_{t<Kq} c_t w^(t+1) with w = r_c / (z_c - p),
 // by Horner's rule; slot k only when use[k] (uniform across the warp).  One
 // coefficient load per term serves every slot: the loop runs the warp's
-// largest K (a multiple of 4, uniform across the warp), and each slot adds
-// only its own terms t < kq[k] (the series length its query's distance
-// needs), so a query's sum does not depend on which queries share its warp.
+// largest K in blocks of 4 terms (every K is a multiple of 4), and a slot
+// takes a block only when it lies below its own length kq[k] (the series
+// length its query's distance needs; starting from 0, its sum is the
+// Horner sum of its own terms), so a query's sum does not depend on which
+// queries share its warp.
 template <int QPT>
 __device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, const float *fx, const float *fy,
                                               const float *fxl, const float *fyl, const bool *use,
@@ -458,8 +460,7 @@ __device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, cons
     const float4 z = __ldg(N + 2);
     const float rc = __ldg(&N[3].x);
     float wr[QPT], wi[QPT], sr[QPT], si[QPT];
-    const float2 *cf = reinterpret_cast<const float2 *>(N + kCluCoef);
-    const float2 cl = __ldg(cf + (K - 1));
+    const float4 *cf = N + kCluCoef;              // two complex coefficients per float4
 #pragma unroll
     for (int k = 0; k < QPT; k++) {
         const float dx = (z.x - fx[k]) + (z.z - fxl[k]);
@@ -467,22 +468,22 @@ __device__ __forceinline__ void node_gap_sums(const float4 *__restrict__ N, cons
         const float inv = __fdividef(rc, fmaf(dx, dx, dy * dy));
         wr[k] = dx * inv;
         wi[k] = -dy * inv;
-        const bool own = K - 1 < kq[k];
-        sr[k] = own ? cl.x : 0.f;
-        si[k] = own ? cl.y : 0.f;
+        sr[k] = 0.f;
+        si[k] = 0.f;
     }
-#pragma unroll 4
-    for (int t = K - 2; t >= 0; t--) {
-        const float2 c = __ldg(cf + t);
+    for (int b = K / 4 - 1; b >= 0; b--) {
+        const float4 c01 = __ldg(cf + 2 * b), c23 = __ldg(cf + 2 * b + 1);
+        const float cr[4] = {c23.z, c23.x, c01.z, c01.x}, ci[4] = {c23.w, c23.y, c01.w, c01.y};
 #pragma unroll
         for (int k = 0; k < QPT; k++) {
-            if (!use[k]) continue;
-            const bool own = t < kq[k];
-            const float cx = own ? c.x : 0.f, cy = own ? c.y : 0.f;
-            const float tr = fmaf(sr[k], wr[k], fmaf(-si[k], wi[k], cx));
-            const float ti = fmaf(sr[k], wi[k], fmaf(si[k], wr[k], cy));
-            sr[k] = tr;
-            si[k] = ti;
+            if (!use[k] || 4 * b >= kq[k]) continue;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float tr = fmaf(sr[k], wr[k], fmaf(-si[k], wi[k], cr[j]));
+                const float ti = fmaf(sr[k], wi[k], fmaf(si[k], wr[k], ci[j]));
+                sr[k] = tr;
+                si[k] = ti;
+            }
         }
     }
 #pragma unroll
@@ -559,20 +560,6 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
         int acc[QPT];
         uint32_t fl[QPT], qid[QPT];
         bool valid[QPT], inc[QPT];
-        // the next unit of the warp's claimed run: its queries' permutation
-        // entries are read now, and their points prefetched into L2 once this
-        // unit's own points have arrived, so that the next unit does not
-        // start with a DRAM round trip (the points of a bucketed batch are
-        // read in a scattered order)
-        int nq_next[QPT];
-#pragma unroll
-        for (int k = 0; k < QPT; k++) nq_next[k] = -1;
-        if (A.perm && u_next < u_end && u_next < A.n_units) {
-            const int4 Un = __ldg(&A.units[u_next]);
-#pragma unroll
-            for (int k = 0; k < QPT; k++)
-                if (lane * QPT + k < Un.z) nq_next[k] = __ldg(&A.perm[(uint32_t)(Un.w + lane * QPT + k)]);
-        }
 #pragma unroll
         for (int k = 0; k < QPT; k++) {
             const int ql = lane * QPT + k;          // the warp owns the unit's 32*QPT positions
@@ -618,10 +605,7 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
             thl[k] = 0.f;
             fl[k] = 0u;
         }
-#pragma unroll
-        for (int k = 0; k < QPT; k++)
-            if (nq_next[k] >= 0)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.src.pts + 2 * (size_t)nq_next[k]));
+
         // warp box of the reduced queries (FP32, rounded outward): instances
         // whose window misses it are skipped by the whole warp, 32 tested
         // per round (a domain with one instance needs no test).  The box
@@ -822,16 +806,10 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
                         }
                         if (!leaf) {
                             if (__any_sync(0xffffffffu, cf != 0u)) {
-                                // the children are visited next: one lane per
-                                // child starts its first 128 bytes (the tests'
-                                // data) towards L1, all in flight at once
-                                const int c0 = __float_as_int(meta.z), c1 = __float_as_int(meta.w);
-                                if (lane < c1 - c0)
-                                    asm volatile("prefetch.global.L1 [%0];" ::"l"(nodes + (size_t)kCluF4 * (c0 + lane)));
                                 sp++;
                                 if (lane == sp) {
-                                    st_cur = c0;
-                                    st_end = c1;
+                                    st_cur = __float_as_int(meta.z);
+                                    st_end = __float_as_int(meta.w);
                                     st_lvl = lvl + 1;
                                 }
                                 const int sh = (lvl + 1) * SB;
@@ -852,10 +830,6 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
                         const bool wc = __any_sync(0xffffffffu, need_cross);
                         if (!we && !wc) continue;
                         const int r0 = __float_as_int(meta.z), r1 = __float_as_int(meta.w);
-                        // the leaf's records (64 bytes each), one 128-byte
-                        // line per lane, all in flight before the record loop
-                        if (lane < (r1 - r0 + 1) / 2)
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + 4 * (size_t)(r0 + 2 * lane)));
                         float tcl[QPT];
 #pragma unroll
                         for (int k = 0; k < QPT; k++) tcl[k] = 0.f;
