@@ -433,7 +433,7 @@ wn_status wn_near_work(int64_t *out4);
  * fixed device-memory budget.  This entry point keeps all of its scratch
  * (per-query accumulators, the near-pair and FP64 queues, the work list)
  * in one fixed-size device array that is part of the library image (about
- * 12.3 MiB per device).  The library is built without relocatable device
+ * 12.0 MiB per device).  The library is built without relocatable device
  * code and CUDA loads modules lazily by default, so the array and the
  * kernels' code are placed on a device when the FIRST call on that device
  * loads them; that call also launches every kernel a call can use once on

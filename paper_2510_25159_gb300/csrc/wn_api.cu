@@ -171,10 +171,9 @@ cudaError_t ensure_work(Work &W, int64_t n, int64_t near_expected)
     cudaError_t e = cudaSuccess;
     int64_t nq = std::max<int64_t>(n, 1024);
     if (nq > W.cap_q) {
-        int64_t c0 = W.cap_q, c1 = W.cap_q, c2 = W.cap_q, c3 = W.cap_q;
+        int64_t c0 = W.cap_q, c1 = W.cap_q, c3 = W.cap_q;
         if ((e = grow(W.acc2, c0, nq)) != cudaSuccess) return e;
         if ((e = grow(W.theta, c1, nq)) != cudaSuccess) return e;
-        if ((e = grow(W.flags, c2, nq)) != cudaSuccess) return e;
         if ((e = grow(W.esc_q, c3, nq)) != cudaSuccess) return e;
         W.cap_q = nq;
     }
@@ -397,8 +396,8 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
     // spatial buckets: about cell_q queries per cell; G x G cells per
     // domain (the bucketing kernel lays them over the domain's box),
     // G <= kBinMaxG so that one CTA holds a domain's cell counters;
-    // the bucketing kernels take each domain's queries in chunks of
-    // about twice its cell count
+    // the bucketing kernels take each domain's queries in runs of about
+    // twice its cell count
     std::vector<int4> dcell(n_domains);
     std::vector<int4> bch;
     int64_t ncell = 0;
@@ -407,6 +406,8 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
         const int G = cnt == 0 ? 0 : (int)std::min<double>((double)kBinMaxG, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
         dcell[d] = make_int4((int)ncell, G, 0, 0);
         ncell += (int64_t)G * G;
+        // runs of about twice the cell count, 4k-32k queries (longer runs
+        // measured slower: fewer of them balance worse over the CTAs)
         const int64_t csz = std::min<int64_t>(32768, std::max<int64_t>(4096, 2LL * G * G));
         for (int64_t q0 = 0; q0 < cnt; q0 += csz)
             bch.push_back(make_int4(d, (int)(offsets[d] + q0), (int)std::min(csz, cnt - q0), 0));

@@ -43,9 +43,8 @@ struct OutDst {
 // place (the tables themselves are owned and sized elsewhere: the API keeps
 // one set per list of domains, the allocation-free query a fixed one).
 struct Work {
-    int32_t *acc2 = nullptr;   // 2 * crossings + line halves, per query
+    int32_t *acc2 = nullptr;   // per query: (2 * crossings + line halves) * 4 | QF_* flags
     float *theta = nullptr;    // sum of gap angles, per query
-    uint32_t *flags = nullptr; // QF_*, per query
     Item *near_items = nullptr;
     SubItem *f64_items = nullptr;
     uint2 *esc_q = nullptr;    // (query, batch entry) recomputed in FP64

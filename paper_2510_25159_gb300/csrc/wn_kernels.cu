@@ -179,6 +179,25 @@ __device__ __forceinline__ int settle(int32_t a2, float th, uint32_t f, bool wan
     return om32 >= 0.5f ? 1 : 0;
 }
 
+// Asynchronous global -> shared copies (cp.async): 16 bytes, both addresses
+// 16-byte aligned; commit closes a group, wait_all waits for the thread's
+// copies.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The per-query accumulator of the mixed path: the doubled crossings and
+// line halves times 4 with the QF_* flags in the two low bits, so that one
+// word is written per query and the near walks' atomic adds (multiples of
+// 4) and ORs (the low bits) never disturb each other.
+static_assert((QF_BOUNDARY | QF_ESCALATE) == 3u, "the flags fill the two low bits");
+__device__ __forceinline__ int32_t pack_acc(int acc2, uint32_t flags) { return acc2 * 4 + (int32_t)flags; }
+__device__ __forceinline__ int unpack_acc(int32_t v) { return (v - (v & 3)) / 4; }
+
 // ------------------------------------------------------------------ sweep
 struct SweepArgs {
     const DomDev *doms;
@@ -186,9 +205,8 @@ struct SweepArgs {
     int n_units;
     const int *perm;            // position -> query index (spatially bucketed), or null
     PointSrc src;
-    int32_t *acc2;
+    int32_t *acc2;              // packed per query: (2 crossings + line halves) * 4 | QF_* flags
     float *theta;
-    uint32_t *flags;
     Item *near_items;
     long long cap_near;
     unsigned long long *counters;
@@ -515,6 +533,11 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
     __shared__ float4 s_ph[QPT][kSweepThreads];       // p - o as FP32 hi/lo pairs (x hi, x lo, y hi, y lo)
     __shared__ float2 s_pr[QPT][kSweepThreads];       // reduced query in FP32 (within 2^-23)
     __shared__ float s_wb[kSweepThreads / 32][8];     // per warp: query box, |max|, family normal
+    // the next unit of a warp's claimed run, staged while the current one
+    // runs: its unit record, its queries' indices and (by cp.async) points
+    __shared__ double2 s_nq[QPT][kSweepThreads];
+    __shared__ int s_nid[QPT][kSweepThreads];
+    __shared__ int4 s_nu[kSweepThreads / 32];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -530,12 +553,14 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
     const int n_warps = (int)(gridDim.x * (kSweepThreads / 32));
     const int batch = max(1, min(8, A.n_units / (64 * n_warps)));
     int u_next = 0, u_end = 0;          // the warp's claimed units (warp-uniform)
+    bool staged = false;                // the unit about to start is staged in shared memory (warp-uniform)
     for (;;) {
         if (u_next >= u_end) {
             unsigned long long uu = 0;
             if (lane == 0) uu = atomicAdd(&A.counters[CNT_UNIT], (unsigned long long)batch);
             u_next = (int)__shfl_sync(0xffffffffu, uu, 0);
             u_end = u_next + batch;
+            staged = false;
         }
         const int u = u_next++;
         if (u >= A.n_units) {
@@ -548,13 +573,31 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
             }
             return;
         }
-        const int4 U = __ldg(&A.units[u]);
+        if (staged) {
+            cp_async_wait_all();
+            __syncwarp();
+        }
+        const int4 U = staged ? s_nu[warp] : __ldg(&A.units[u]);
         const DomDev *__restrict__ Dp = A.doms + U.x;
         const double Pu = Dp->Pu, Pv = Dp->Pv;
         const float M = Dp->M, Mq = Dp->Mq;
         const int n_inst = Dp->n_inst;
         const float4 *__restrict__ rec = Dp->rec;
         const float4 *__restrict__ nodes = Dp->nodes;
+        // the next unit of the run (bucketed queries): its record and query
+        // indices are loaded now, their latency hidden by this unit's start,
+        // and staged below once this unit's own staged data has been read
+        const bool stage_next = A.perm && u_next < u_end && u_next < A.n_units;
+        int4 Un = make_int4(0, 0, 0, 0);
+        int qn[QPT];
+#pragma unroll
+        for (int k = 0; k < QPT; k++) qn[k] = -1;
+        if (stage_next) {
+            Un = __ldg(&A.units[u_next]);
+#pragma unroll
+            for (int k = 0; k < QPT; k++)
+                if (lane * QPT + k < Un.z) qn[k] = __ldg(&A.perm[(uint32_t)(Un.w + lane * QPT + k)]);
+        }
 
         float fx[QPT], fy[QPT], fxl[QPT], fyl[QPT], T[QPT], th[QPT], thl[QPT];
         int acc[QPT];
@@ -571,7 +614,7 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
                 if (A.perm) {
                     // bucketed: the unit's positions start at U.w in the
                     // bucketed order (tree domains only)
-                    qid[k] = (uint32_t)__ldg(&A.perm[(uint32_t)(U.w + ql)]);
+                    qid[k] = staged ? (uint32_t)s_nid[k][tid] : (uint32_t)__ldg(&A.perm[(uint32_t)(U.w + ql)]);
                 } else if (A.src.tiles_x) {
                     // grid in tiles of 64 cells (w x 64/w), row-major:
                     // position -> cell
@@ -583,7 +626,15 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
                 } else {
                     qid[k] = pos;
                 }
-                if (valid[k]) get_point(A.src, qid[k], x, y);
+                if (valid[k]) {
+                    if (staged) {
+                        const double2 v = s_nq[k][tid];
+                        x = v.x;
+                        y = v.y;
+                    } else {
+                        get_point(A.src, qid[k], x, y);
+                    }
+                }
             }
             x = reduce_period(x, Pu);
             y = reduce_period(y, Pv);
@@ -605,6 +656,19 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
             thl[k] = 0.f;
             fl[k] = 0u;
         }
+        // stage the next unit: each lane writes its own slots (it has just
+        // read this unit's from them), lane 0 the unit record
+        if (stage_next) {
+            if (lane == 0) s_nu[warp] = Un;
+#pragma unroll
+            for (int k = 0; k < QPT; k++)
+                if (qn[k] >= 0) {
+                    s_nid[k][tid] = qn[k];
+                    cp_async16(&s_nq[k][tid], A.src.pts + 2 * (size_t)qn[k]);
+                }
+            cp_async_commit();
+        }
+        staged = stage_next;
 
         // warp box of the reduced queries (FP32, rounded outward): instances
         // whose window misses it are skipped by the whole warp, 32 tested
@@ -953,9 +1017,8 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
 #pragma unroll
         for (int k = 0; k < QPT; k++) {
             if (!valid[k]) continue;
-            A.acc2[qid[k]] = acc[k];
+            A.acc2[qid[k]] = pack_acc(acc[k], fl[k]);
             A.theta[qid[k]] = th[k] + thl[k];
-            A.flags[qid[k]] = fl[k];
         }
     }
 }
@@ -1226,7 +1289,12 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
             }
             for (int r0 = in.r0; r0 < in.r1; r0 += kChunk) {
                 const int cnt = min(kChunk, in.r1 - r0);
-                for (int i = tid; i < 4 * cnt; i += kSweepThreads) s_rec[i] = __ldg(rec + 4 * r0 + i);
+                // the records of the chunk into shared memory by cp.async
+                // (float4 records, 16-byte aligned), shared by every query
+                // of the tile
+                for (int i = tid; i < 4 * cnt; i += kSweepThreads) cp_async16(&s_rec[i], rec + 4 * r0 + i);
+                cp_async_commit();
+                cp_async_wait_all();
                 __syncthreads();
                 float tc[QPT];
 #pragma unroll
@@ -1293,9 +1361,8 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
         for (int k = 0; k < QPT; k++) {
             if (!valid[k]) continue;
             const uint32_t q = (uint32_t)(U.y + tid + k * kSweepThreads);
-            A.acc2[q] = acc[k];
+            A.acc2[q] = pack_acc(acc[k], fl[k]);
             A.theta[q] = th[k] + thl[k];
-            A.flags[q] = fl[k];
         }
     }
 }
@@ -1324,8 +1391,7 @@ struct NearArgs {
     PointSrc src;
     const Item *items;
     long long cap_near;
-    int32_t *acc2;
-    uint32_t *flags;
+    int32_t *acc2;              // packed, see SweepArgs
     SubItem *f64_items;
     long long cap_f64;
     unsigned long long *counters;
@@ -1359,7 +1425,7 @@ __device__ __forceinline__ void emit_f64(const NearArgs &A, const Item &it, floa
         si.pad = 0;
         A.f64_items[idx] = si;
     } else {
-        atomicOr(&A.flags[it.q], QF_ESCALATE);
+        atomicOr(&A.acc2[it.q], (int)QF_ESCALATE);
     }
 }
 
@@ -1606,7 +1672,7 @@ __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
                         it = A.items[i];
                         int res = 0;
                         busy = near_start<RAT>(A, it, W, S, res);
-                        if (!busy && res == 1) atomicOr(&A.flags[it.q], QF_BOUNDARY);
+                        if (!busy && res == 1) atomicOr(&A.acc2[it.q], (int)QF_BOUNDARY);
                     }
                 }
                 pool = min(pool + (unsigned long long)__popc(idle), pool_end);
@@ -1619,8 +1685,8 @@ __global__ void __launch_bounds__(256, 4) k_near(const NearArgs A)
         if (busy) {
             const int r = near_step<RAT, CNT>(A, it, W, S, wk);
             if (r != 0) {
-                if (r == 2) atomicOr(&A.flags[it.q], QF_BOUNDARY);
-                else if (W.cnt) atomicAdd(&A.acc2[it.q], 2 * W.cnt);
+                if (r == 2) atomicOr(&A.acc2[it.q], (int)QF_BOUNDARY);
+                else if (W.cnt) atomicAdd(&A.acc2[it.q], 8 * W.cnt);        // 2 crossings each, packed
                 busy = false;
             }
         }
@@ -1657,10 +1723,10 @@ __global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
         const int res = alg1_fp64_sub(P, seg_weights(*Dp, s), deg, Dp->max_deg, Dp->seg_B[s], pxp, pyp, Dp->eps,
                                       (double)si.a, (double)si.b, sa, sb, cnt);
         if (res != WALK_DONE) {
-            atomicOr(&A.flags[it.q], QF_BOUNDARY);
+            atomicOr(&A.acc2[it.q], (int)QF_BOUNDARY);
             if (res == WALK_DEPTH) atomicAdd(&A.counters[CNT_DEPTH], 1ULL);
         } else if (cnt) {
-            atomicAdd(&A.acc2[it.q], 2 * cnt);
+            atomicAdd(&A.acc2[it.q], 8 * cnt);
         }
     }
 }
@@ -1731,9 +1797,8 @@ struct FinArgs {
     long long n;
     const int64_t *offsets;
     int n_doms;
-    const int32_t *acc2;
+    const int32_t *acc2;        // packed, see SweepArgs
     const float *theta;
-    const uint32_t *flags;
     uint2 *esc;
     unsigned long long *counters;
     OutDst out;
@@ -1761,7 +1826,8 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs A)
         double om = 0.0;
         bool esc = false;
         if (in_range) {
-            st = settle(A.acc2[q], A.theta[q], A.flags[q], A.out.w != nullptr, om);
+            const int32_t v = A.acc2[q];
+            st = settle(unpack_acc(v), A.theta[q], (uint32_t)v & 3u, A.out.w != nullptr, om);
             esc = st < 0;
             if (esc) {
                 const unsigned long long idx = atomicAdd(&A.counters[CNT_ESC], 1ULL);
@@ -2044,7 +2110,6 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     sa.src = src;
     sa.acc2 = W.acc2;
     sa.theta = W.theta;
-    sa.flags = W.flags;
     sa.near_items = W.near_items;
     sa.cap_near = W.cap_near;
     sa.counters = W.counters;
@@ -2090,7 +2155,6 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     na.items = W.near_items;
     na.cap_near = W.cap_near;
     na.acc2 = W.acc2;
-    na.flags = W.flags;
     na.f64_items = W.f64_items;
     na.cap_f64 = W.cap_f64;
     na.counters = W.counters;
@@ -2118,7 +2182,6 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     fa.n_doms = n_doms;
     fa.acc2 = W.acc2;
     fa.theta = W.theta;
-    fa.flags = W.flags;
     fa.esc = W.esc_q;
     fa.counters = W.counters;
     fa.out = out;

@@ -39,8 +39,7 @@ constexpr size_t kOffUnits = align256(kOffCounters + CNT_N * sizeof(unsigned lon
 constexpr size_t kOffOffsets = align256(kOffUnits + kMaxUnits * sizeof(int4));
 constexpr size_t kOffAcc2 = align256(kOffOffsets + 2 * sizeof(int64_t));
 constexpr size_t kOffTheta = align256(kOffAcc2 + kMaxQ * sizeof(int32_t));
-constexpr size_t kOffFlags = align256(kOffTheta + kMaxQ * sizeof(float));
-constexpr size_t kOffEsc = align256(kOffFlags + kMaxQ * sizeof(uint32_t));
+constexpr size_t kOffEsc = align256(kOffTheta + kMaxQ * sizeof(float));
 constexpr size_t kOffNear = align256(kOffEsc + kMaxQ * sizeof(uint2));
 constexpr size_t kOffF64 = align256(kOffNear + kNearCap * sizeof(Item));
 constexpr size_t kScratchBytes = align256(kOffF64 + kF64Cap * sizeof(SubItem));
@@ -64,7 +63,6 @@ Work scratch_work(unsigned char *base)
     W.offsets = reinterpret_cast<int64_t *>(base + kOffOffsets);
     W.acc2 = reinterpret_cast<int32_t *>(base + kOffAcc2);
     W.theta = reinterpret_cast<float *>(base + kOffTheta);
-    W.flags = reinterpret_cast<uint32_t *>(base + kOffFlags);
     W.esc_q = reinterpret_cast<uint2 *>(base + kOffEsc);
     W.near_items = reinterpret_cast<Item *>(base + kOffNear);
     W.f64_items = reinterpret_cast<SubItem *>(base + kOffF64);
