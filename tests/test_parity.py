@@ -430,3 +430,30 @@ def test_sphere_cone_punctured(wn, name, prec, tol):
         (pc[:, 1] > 1e-3)
     exp = (pc[far, 1] < t0[far]) | ((pc[far, 1] > 0.8) & (pc[far, 1] < 1.0))
     assert np.array_equal(sc[far], exp.astype(np.uint8))
+
+
+def _sampled_full_size(wn, doms, qs, per_dom, big_extra, seed):
+    """One mixed batched call over a whole workload; the oracle checks
+    per_dom stratified queries of every domain and big_extra more of every
+    large domain (1000+ segments or 2^18+ queries)."""
+    res = run(wn, doms, qs, 1)
+    rng = np.random.default_rng(seed)
+    for d, q, (w, s) in zip(doms, qs, res):
+        big = ws.n_segments(d) >= 1000 or len(q) >= (1 << 18)
+        m = min(len(q), per_dom + (big_extra if big else 0))
+        idx = np.sort(rng.choice(len(q), m, replace=False))
+        compare(d, q[idx], w[idx], s[idx], TOL_MIXED, threads=1)
+
+
+def test_workload3_full_size_sampled(wn):
+    """All 256 tori with their 20M queries in one call; every face checked."""
+    doms, qs = ws.config3()
+    _sampled_full_size(wn, doms, qs, 40, 200, 31)
+
+
+def test_workload4_full_size_sampled(wn):
+    """The batched B-Rep workload at full size (10k faces, 2e8 queries) in
+    one call; every face checked, the large ones (up to 4000 segments or 1M
+    queries) more."""
+    doms, qs = ws.config4()
+    _sampled_full_size(wn, doms, qs, 6, 150, 32)
