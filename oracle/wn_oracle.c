@@ -63,6 +63,10 @@
  *       spacing of alpha's), take the copies left of alpha (ToLeft, Alg. 8,
  *       on the loop's parameter midpoint) and keep the one that lies left of
  *       the current best in the beta orientation (the nearest one).
+ *   R11 a sphere's or cone's singular point, punctured (Sec. 4.3), enters as
+ *       a boundary loop along its line in the parameter domain, as B-Rep
+ *       models store a degenerate edge there (an input convention: this
+ *       file treats it as any other loop).
  *
  * Pins (tests/pins.py, tests/test_oracle.py): exact integer winding of
  * degree-1 polygons, atan2 for a single chord, +-1/0 for circles, the hull

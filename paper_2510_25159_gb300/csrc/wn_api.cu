@@ -177,11 +177,12 @@ cudaError_t ensure_work(Work &W, int64_t n, int64_t near_expected)
         if ((e = grow(W.esc_q, c3, nq)) != cudaSuccess) return e;
         W.cap_q = nq;
     }
-    // near pairs: 3 per query or twice the expected count, whichever is more
-    // (an overflowing pair sends its query to the FP64 recomputation), but
-    // at most a quarter of the free device memory: a smaller queue only
-    // moves the pairs that do not fit to that recomputation
-    int64_t need_near = std::max<int64_t>(std::max<int64_t>(1 << 22, 3 * nq), 2 * near_expected);
+    // near pairs: twice the expected count (from the records' circle areas),
+    // at least one per four queries and 4M (an overflowing pair sends its
+    // query to the FP64 recomputation), but at most a quarter of the free
+    // device memory: a smaller queue only moves the pairs that do not fit
+    // to that recomputation
+    int64_t need_near = std::max<int64_t>(std::max<int64_t>(1 << 22, nq / 4), 2 * near_expected);
     if (need_near > W.cap_near) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
