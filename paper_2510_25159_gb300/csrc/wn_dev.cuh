@@ -127,6 +127,9 @@ struct DomDev {
                                 //   ratio W/w as FP32 bits for a rational segment, else 0)
     const double *w;            // [total_cp] weights, or null when no segment is rational
     const float *w32;           // [total_cp] the weights rounded to FP32, or null
+    const double *seg_bsub;     // [8 n_segs] bound of |gamma'| on each eighth [j/8, (j+1)/8]
+                                //   of a segment (rational domains only, else null)
+    const float *seg_bsub32;    // [8 n_segs] the same rounded up to FP32, or null
     float eps32;                // eps rounded to FP32
     int pad4;
 };
@@ -466,6 +469,12 @@ __device__ __forceinline__ const double *seg_weights(const DomDev &D, int s)
     return si.w ? D.w + si.x : nullptr;
 }
 
+// Bounds of |gamma'| on the eighths of a rational segment, or null
+__device__ __forceinline__ const double *seg_bsub(const DomDev &D, int s)
+{
+    return D.seg_bsub ? D.seg_bsub + 8 * (size_t)s : nullptr;
+}
+
 // ---------------------------------------------------------------- Alg. 1, FP64
 // Far actions of Algorithm 1: the chord of an excluded sub-segment either adds
 // its signed angle (Eq. 3, the plain method) or its signed crossing of the
@@ -535,6 +544,43 @@ __device__ int alg1_fp64(const double *P, const double *Wt, int n, int nmax, dou
         sp++;
     }
     return WALK_DONE;
+}
+
+// The eighth [j/8, (j+1)/8] of the parameter interval that holds a node:
+// j = floor(8 a) for its start a in [0, 1) and ceil(8 b) - 1 for its end b
+// in (0, 1]; the node lies in one eighth iff the two agree.  From the bits
+// (a, b >= 0 are dyadic node ends), so no conversion instructions.
+__device__ __forceinline__ int eighth_lo(float a)
+{
+    const uint32_t u = __float_as_uint(a);
+    const int e = (int)(u >> 23) - 127;                 // a = 1.m 2^e
+    if (e < -3) return 0;
+    return (int)(((u & 0x7fffffu) | 0x800000u) >> (20 - e));
+}
+__device__ __forceinline__ int eighth_hi(float b)
+{
+    const uint32_t u = __float_as_uint(b);
+    const int e = (int)(u >> 23) - 127;
+    if (e < -3) return 0;
+    const uint32_t m = (u & 0x7fffffu) | 0x800000u;
+    const int sh = 20 - e;
+    return (int)(m >> sh) - ((m & ((1u << sh) - 1u)) == 0u ? 1 : 0);
+}
+__device__ __forceinline__ int eighth_lo(double a)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(a);
+    const int e = (int)(hi >> 20) - 1023;
+    if (e < -3) return 0;
+    return (int)(((hi & 0xfffffu) | 0x100000u) >> (17 - e));
+}
+__device__ __forceinline__ int eighth_hi(double b)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(b), lo = (uint32_t)__double2loint(b);
+    const int e = (int)(hi >> 20) - 1023;
+    if (e < -3) return 0;
+    const uint32_t m = (hi & 0xfffffu) | 0x100000u;
+    const int sh = 17 - e;
+    return (int)(m >> sh) - (((m & ((1u << sh) - 1u)) | lo) == 0u ? 1 : 0);
 }
 
 // Algorithm 1 in FP64 on the sub-interval [a0, b0] of a polynomial segment
@@ -642,10 +688,20 @@ __device__ __noinline__ int alg1_fp64_sub_pow(const double *P, int n, double B, 
 // power basis.  Since W > 0, signs and cross products take Q alone, and the
 // eps and far tests are those of the polynomial walk multiplied through by
 // the squared weights (|Q|^2 = |gamma - p|^2 W^2), so no node divides.
+//
+// A rational segment's bound B (App. A.1) grows with its weight ratio
+// (about 2 / w for a circular arc of weights (1, w, 1)), and the walk's
+// node count with it.  With bsub (the segment's bounds on its eighths, or
+// null), a node inside one eighth is also far when ra + rb > Bj (b - a) + 2 eps
+// holds for that eighth's bound Bj: the sub-curve then lies in the smaller
+// ellipse, so the chord's crossings are the curve's, and every one of its
+// points is more than eps from the query (|q - c| >= (ra + rb - Bj (b - a)) / 2
+// for c in that ellipse), so the eps test of the walk with B alone would not
+// have fired inside the node either.
 template <int NM>
 __device__ __noinline__ int alg1_fp64_sub_rpow(const double *P, const double *Wt, int n, double B, double px,
                                                 double py, double eps, double a0, double b0, bool sa0, bool sb0,
-                                                int &cnt)
+                                                const double *bsub, int &cnt)
 {
     double cx[NM + 1], cy[NM + 1], cw[NM + 1];
 #pragma unroll
@@ -712,7 +768,11 @@ __device__ __noinline__ int alg1_fp64_sub_rpow(const double *P, const double *Wt
         const double nb = bx * bx + by * by, wb2 = bw * bw;
         if (na < eps2 * wa2 || nb < eps2 * wb2) return WALK_BOUNDARY;
         const bool sb = (b == b0) ? sb0 : (by > 0.0);
-        const double L = B * (b - a);
+        double L = B * (b - a);
+        if (bsub) {
+            const int j = eighth_lo(a);
+            if (j == eighth_hi(b)) L = fmin(L, fma(__ldg(bsub + j), b - a, 2.0 * eps));
+        }
         const double S = L * L * wa2 * wb2 - (na * wb2 + nb * wa2);
         if (S < 0.0 || 4.0 * na * nb * wa2 * wb2 > S * S) {
             if (sa != sb) {
@@ -737,11 +797,13 @@ __device__ __noinline__ int alg1_fp64_sub_rpow(const double *P, const double *Wt
 
 // Algorithm 1 in FP64 on the sub-interval [a0, b0] of one segment, adding
 // the signed crossings of the +x ray from (px, py) by its chords; the end
-// points take the given signs (those of the FP32 chain around it).
+// points take the given signs (those of the FP32 chain around it).  bsub:
+// the segment's bounds on its eighths (rational segments), or null.
 // Returns WALK_DONE, or WALK_BOUNDARY / WALK_DEPTH when the query is on the
 // boundary.
 __device__ inline int alg1_fp64_sub(const double *P, const double *Wt, int n, int nmax, double B, double px,
-                                     double py, double eps, double a0, double b0, bool sa0, bool sb0, int &cnt)
+                                     double py, double eps, double a0, double b0, bool sa0, bool sb0,
+                                     const double *bsub, int &cnt)
 {
     if (!Wt) {
         switch (nmax) {
@@ -755,13 +817,13 @@ __device__ inline int alg1_fp64_sub(const double *P, const double *Wt, int n, in
         }
     }
     switch (nmax) {
-    case 1: return alg1_fp64_sub_rpow<1>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
-    case 2: return alg1_fp64_sub_rpow<2>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
-    case 3: return alg1_fp64_sub_rpow<3>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
-    case 4: return alg1_fp64_sub_rpow<4>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
-    case 5: return alg1_fp64_sub_rpow<5>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
-    case 6: return alg1_fp64_sub_rpow<6>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
-    default: return alg1_fp64_sub_rpow<kMaxDeg>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, cnt);
+    case 1: return alg1_fp64_sub_rpow<1>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, bsub, cnt);
+    case 2: return alg1_fp64_sub_rpow<2>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, bsub, cnt);
+    case 3: return alg1_fp64_sub_rpow<3>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, bsub, cnt);
+    case 4: return alg1_fp64_sub_rpow<4>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, bsub, cnt);
+    case 5: return alg1_fp64_sub_rpow<5>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, bsub, cnt);
+    case 6: return alg1_fp64_sub_rpow<6>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, bsub, cnt);
+    default: return alg1_fp64_sub_rpow<kMaxDeg>(P, Wt, n, B, px, py, eps, a0, b0, sa0, sb0, bsub, cnt);
     }
 }
 

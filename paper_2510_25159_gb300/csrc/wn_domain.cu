@@ -68,6 +68,81 @@ struct DevBuf {
 
 long long lround_ll(double x) { return (long long)std::llround(x); }
 
+// App. A.1's bounds of |gamma'| on each eighth [j/8, (j+1)/8] of a rational
+// segment of degree n (control points P, weights w > 0, segment bound B).
+// An eighth is itself a rational Bezier curve of degree n, its homogeneous
+// control points (w P, w) those of the segment's de Casteljau subdivision;
+// App. A.1 bounds its speed in its own parameter, and 8 times that bounds
+// |gamma'| there in the segment's parameter.  Near an arc's middle the
+// eighths' weights vary far less than the segment's (an arc of weights
+// (1, w, 1) has ratio 1 / w, its eighths ratios near 1), so their bounds are
+// much smaller than B.  The subdivision's rounding is covered: the
+// sub-curve's control points are convex combinations of the segment's, so
+// each differs from the computed one by at most
+// Delta = 32 n u R max|P| (R the segment's weight ratio, u = 2^-53), its
+// weights by a relative 32 n u R; each distance is widened by 2 Delta and
+// the ratio by that relative amount.  No result exceeds B.
+void rational_eighth_bounds(const double *P, const double *w, int n, double B, double out[8])
+{
+    constexpr double u = 1.1102230246251565e-16;
+    double wmax = w[0], wmin = w[0], Pm = 0.0;
+    for (int i = 0; i <= n; i++) {
+        wmax = std::fmax(wmax, w[i]);
+        wmin = std::fmin(wmin, w[i]);
+        Pm = std::fmax(Pm, std::fmax(std::fabs(P[2 * i]), std::fabs(P[2 * i + 1])));
+    }
+    const double rel = 32.0 * n * u * (wmax / wmin);
+    const double Delta = rel * Pm;
+    // de Casteljau at t: the left (keep_left) or right part of h
+    auto split = [n](double (*h)[3], double t, bool keep_left) {
+        double tmp[kMaxDeg + 1][3], part[kMaxDeg + 1][3];
+        for (int i = 0; i <= n; i++)
+            for (int c = 0; c < 3; c++) tmp[i][c] = h[i][c];
+        for (int c = 0; c < 3; c++) {
+            part[0][c] = tmp[0][c];
+            part[n][c] = tmp[n][c];
+        }
+        for (int k = 1; k <= n; k++) {
+            for (int i = 0; i <= n - k; i++)
+                for (int c = 0; c < 3; c++) tmp[i][c] = (1.0 - t) * tmp[i][c] + t * tmp[i + 1][c];
+            for (int c = 0; c < 3; c++) {
+                if (keep_left) part[k][c] = tmp[0][c];
+                else part[n - k][c] = tmp[n - k][c];
+            }
+        }
+        for (int i = 0; i <= n; i++)
+            for (int c = 0; c < 3; c++) h[i][c] = part[i][c];
+    };
+    for (int j = 0; j < 8; j++) {
+        double h[kMaxDeg + 1][3];
+        for (int i = 0; i <= n; i++) {
+            h[i][0] = w[i] * P[2 * i];
+            h[i][1] = w[i] * P[2 * i + 1];
+            h[i][2] = w[i];
+        }
+        split(h, (j + 1) / 8.0, true);                       // [0, (j+1)/8]
+        if (j > 0) split(h, (double)j / (double)(j + 1), false);     // then its part from j/8
+        double smax = h[0][2], smin = h[0][2];
+        double q[kMaxDeg + 1][2];
+        for (int i = 0; i <= n; i++) {
+            smax = std::fmax(smax, h[i][2]);
+            smin = std::fmin(smin, h[i][2]);
+            q[i][0] = h[i][0] / h[i][2];
+            q[i][1] = h[i][1] / h[i][2];
+        }
+        const double r = (smax / smin) * (1.0 + rel) / (1.0 - rel);
+        double dall = 0.0, dnext = 0.0;
+        for (int i = 0; i <= n; i++)
+            for (int k = i + 1; k <= n; k++) {
+                const double d = std::hypot(q[k][0] - q[i][0], q[k][1] - q[i][1]);
+                dall = std::fmax(dall, d);
+                if (k == i + 1) dnext = std::fmax(dnext, d);
+            }
+        const double bj = std::fmin((double)n * r * (dall + 2.0 * Delta), (double)n * r * r * (dnext + 2.0 * Delta));
+        out[j] = std::fmin(B, 8.0 * bj * (1.0 + 1e-12));
+    }
+}
+
 }  // namespace
 
 int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
@@ -693,6 +768,23 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             for (long long i = 0; i < ncp; i++) w32[i] = (float)Wt[i];
             dv.w = up.up(Wt);
             dv.w32 = up.up(w32);
+            // bounds on the eighths of the rational segments (the polynomial
+            // ones repeat B; only rational walks read these)
+            std::vector<double> bs(8 * (size_t)ns);
+            std::vector<float> bs32(8 * (size_t)ns);
+            for (int i = 0; i < ns; i++) {
+                double e8[8];
+                if (seg_rat[i]) rational_eighth_bounds(&P[2 * seg_cp[i]], &Wt[seg_cp[i]], seg_deg[i], segB[i], e8);
+                else std::fill(e8, e8 + 8, segB[i]);
+                for (int j = 0; j < 8; j++) {
+                    float f = (float)e8[j];
+                    if ((double)f < e8[j]) f = std::nextafter(f, INFINITY);
+                    bs[8 * (size_t)i + j] = e8[j];
+                    bs32[8 * (size_t)i + j] = f;
+                }
+            }
+            dv.seg_bsub = up.up(bs);
+            dv.seg_bsub32 = up.up(bs32);
         }
         dv.eps32 = (float)eps;
     }

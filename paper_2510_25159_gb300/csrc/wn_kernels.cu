@@ -1066,24 +1066,35 @@ __device__ __forceinline__ int round_near_int(float v)
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(const BinArgs A)
 {
     __shared__ int s_cnt[kBinSmemCells];
+    __shared__ float s_box[8];          // the run's cell frame, from the domain's FP64 fields once per run
     for (int c = blockIdx.x; c < A.n_bchunks; c += gridDim.x) {
         const int4 R = __ldg(&A.bchunks[c]);
-        const DomDev *Dp = A.doms + R.x;
         const int4 dc = __ldg(&A.dcell[R.x]);
         const int G = dc.y, G2 = G * G;
-        // G x G cells over the domain's box (the base tile on periodic axes);
-        // FP32 is enough to choose a cell
-        const float x0 = Dp->Pu > 0 ? 0.f : (float)Dp->ox - Dp->M;
-        const float y0 = Dp->Pv > 0 ? 0.f : (float)Dp->oy - Dp->M;
-        const float wx = Dp->Pu > 0 ? (float)Dp->Pu : 2.f * Dp->M;
-        const float wy = Dp->Pv > 0 ? (float)Dp->Pv : 2.f * Dp->M;
-        const float sx = __fdividef((float)G, wx), sy = __fdividef((float)G, wy);
-        // periodic axes: the coordinate's tile offset removed in FP32 (a cell
-        // choice needs no exactness)
-        const bool pu = Dp->Pu > 0, pv = Dp->Pv > 0;
-        const float ipu = pu ? __fdividef(1.f, wx) : 0.f, ipv = pv ? __fdividef(1.f, wy) : 0.f;
+        if (threadIdx.x == 0) {
+            // G x G cells over the domain's box (the base tile on periodic
+            // axes); FP32 is enough to choose a cell.  One thread converts
+            // the FP64 fields (the FP64 unit is narrow on GB300)
+            const DomDev *Dp = A.doms + R.x;
+            const bool pu = Dp->Pu > 0, pv = Dp->Pv > 0;
+            const float wx = pu ? (float)Dp->Pu : 2.f * Dp->M;
+            const float wy = pv ? (float)Dp->Pv : 2.f * Dp->M;
+            s_box[0] = pu ? 0.f : (float)Dp->ox - Dp->M;
+            s_box[1] = pv ? 0.f : (float)Dp->oy - Dp->M;
+            s_box[2] = wx;
+            s_box[3] = wy;
+            // periodic axes: the coordinate's tile offset removed in FP32 (a
+            // cell choice needs no exactness)
+            s_box[4] = pu ? __fdividef(1.f, wx) : 0.f;
+            s_box[5] = pv ? __fdividef(1.f, wy) : 0.f;
+            s_box[6] = pu ? 1.f : 0.f;
+            s_box[7] = pv ? 1.f : 0.f;
+        }
         for (int i = threadIdx.x; i < G2; i += blockDim.x) s_cnt[i] = 0;
         __syncthreads();
+        const float x0 = s_box[0], y0 = s_box[1], wx = s_box[2], wy = s_box[3], ipu = s_box[4], ipv = s_box[5];
+        const bool pu = s_box[6] != 0.f, pv = s_box[7] != 0.f;
+        const float sx = __fdividef((float)G, wx), sy = __fdividef((float)G, wy);
         for (int i = threadIdx.x; i < R.z; i += blockDim.x) {
             const uint32_t q = (uint32_t)(R.y + i);
             double x, y;
@@ -1377,6 +1388,7 @@ __global__ void __launch_bounds__(kSweepThreads, (QPT <= 2 ? 3 : 2)) k_sweep(con
 struct NearWalk {                      // scalars and control points (registers)
     float qx[kNcp], qy[kNcp];           // q_k = P_k - p; times w_k for a rational segment
     const float *qw;                    // rational segment: its FP32 weights (global, read per evaluation)
+    const float *bsub;                  // rational segment: bounds on its eighths (global), see below
     float a, ax, ay, ra, B, E, eps;
     int n, nmax, sp, cnt;
     bool sa, b_tested, rat;
@@ -1526,6 +1538,7 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
     S.d[0] = 0;
     if (W.rat) {
         W.qw = Dp->w32 + si.x;
+        W.bsub = Dp->seg_bsub32 + 8 * (size_t)it.seg;
 #pragma unroll
         for (int k = 0; k < kNcp; k++) {
             const float w = k <= deg ? __ldg(W.qw + k) : 1.f;
@@ -1558,7 +1571,13 @@ __device__ __forceinline__ int near_step(const NearArgs &A, const Item &it, Near
         undecided = rb - er < W.eps;
         W.b_tested = true;
     }
-    const float lim = W.B * (b - W.a);
+    float lim = W.B * (b - W.a);
+    if (RAT && W.rat && d >= 3) {
+        // a node of the walk from [0, 1] lies in the eighth of its start from
+        // depth 3 on: the eighth's bound with a margin of 2 eps (the FP64
+        // walk's tighter test; es covers the roundings)
+        lim = fminf(lim, fmaf(__ldg(W.bsub + eighth_lo(W.a)), b - W.a, 2.f * W.eps));
+    }
     const float s = (W.ra + rb) - lim;
     const float es = 2.f * W.E + (W.ra + rb + lim) * (2.f * kTwoM22);
     bool far = false;
@@ -1722,7 +1741,7 @@ __global__ void __launch_bounds__(128) k_f64items(const NearArgs A)
         const bool sb = si.b == 1.f ? P[2 * deg + 1] > pyp : (si.signs & 2u) != 0;
         int cnt = 0;
         const int res = alg1_fp64_sub(P, seg_weights(*Dp, s), deg, Dp->max_deg, Dp->seg_B[s], pxp, pyp, Dp->eps,
-                                      (double)si.a, (double)si.b, sa, sb, cnt);
+                                      (double)si.a, (double)si.b, sa, sb, seg_bsub(*Dp, s), cnt);
         if (res != WALK_DONE) {
             atomicOr(&A.acc2[it.q], (int)QF_BOUNDARY);
             if (res == WALK_DEPTH) atomicAdd(&A.counters[CNT_DEPTH], 1ULL);
@@ -1896,7 +1915,7 @@ __device__ __noinline__ int record_f64(const DomDev *__restrict__ Dp, int r, dou
             // inside the root ellipse: the FP64 walk
             int cnt = 0;
             const int res = alg1_fp64_sub(Dp->cp + 2 * (size_t)Dp->seg_cp[s], seg_weights(*Dp, s), Dp->seg_deg[s],
-                                          Dp->max_deg, L, pxp, pyp, eps, 0.0, 1.0, sa, sb, cnt);
+                                          Dp->max_deg, L, pxp, pyp, eps, 0.0, 1.0, sa, sb, seg_bsub(*Dp, s), cnt);
             if (res != WALK_DONE) return res;
             c = cnt;
             chord = false;
