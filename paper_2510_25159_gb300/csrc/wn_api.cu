@@ -28,6 +28,7 @@ struct Tables {
     std::vector<int64_t> key_offsets;
     int key = 0;
     int n_units = 0, n_flat = 0, n_cells = 0, n_bchunks = 0;
+    int64_t n_runoff = 0;               // run_off entries: the cells of each run's domain, summed over runs
     bool flat0 = false;                 // a one-domain list: its domain takes the flat sweep
     int4 *units = nullptr;
     DomDev *doms = nullptr;
@@ -159,6 +160,8 @@ DevState *dev_state(wn_status &st)
             return nullptr;
         }
         cudaMemset(S.W.counters, 0, CNT_N * sizeof(unsigned long long));
+        bin_blocks_per_sm(0);      // the bucketing grids' occupancy, cached before any capture
+        bin_blocks_per_sm(1);
         S.init = true;
     }
     st = WN_OK;
@@ -348,7 +351,8 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
     if (same) {
         // the shared cell scratch may have been sized for a smaller list since
         if ((e = grow(S->W.cell_cnt, S->W.cap_cells, (int64_t)T.n_cells)) != cudaSuccess ||
-            (e = grow(S->W.bin_chunk, S->W.cap_chunk, ((int64_t)T.n_cells + 4095) / 4096)) != cudaSuccess)
+            (e = grow(S->W.bin_chunk, S->W.cap_chunk, ((int64_t)T.n_cells + 4095) / 4096)) != cudaSuccess ||
+            (e = grow(S->W.run_off, S->W.cap_runoff, std::max<int64_t>(1, T.n_runoff))) != cudaSuccess)
             return cuda_fail(e, "cells");
         return WN_OK;
     }
@@ -397,23 +401,27 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
     // spatial buckets: about cell_q queries per cell; G x G cells per
     // domain (the bucketing kernel lays them over the domain's box),
     // G <= kBinMaxG so that one CTA holds a domain's cell counters;
-    // the bucketing kernels take each domain's queries in runs of about
-    // twice its cell count
+    // the bucketing kernels take each domain's queries in runs of a few
+    // queries per cell
     std::vector<int4> dcell(n_domains);
     std::vector<int4> bch;
-    int64_t ncell = 0;
+    int64_t ncell = 0, nro = 0;
     for (int d = 0; d < n_domains; d++) {
         const int64_t cnt = flat[d] ? 0 : offsets[d + 1] - offsets[d];    // the flat sweep needs no bucketing
         const int G = cnt == 0 ? 0 : (int)std::min<double>((double)kBinMaxG, std::max<double>(1.0, std::floor(std::sqrt((double)cnt / (double)g_tun.cell_q))));
         dcell[d] = make_int4((int)ncell, G, 0, 0);
         ncell += (int64_t)G * G;
-        // runs of about twice the cell count, 4k-32k queries (longer runs
-        // measured slower: fewer of them balance worse over the CTAs)
-        const int64_t csz = std::min<int64_t>(32768, std::max<int64_t>(4096, 2LL * G * G));
-        for (int64_t q0 = 0; q0 < cnt; q0 += csz)
-            bch.push_back(make_int4(d, (int)(offsets[d] + q0), (int)std::min(csz, cnt - q0), 0));
+        // runs of about kBinRunPerCell queries per cell, 4096 to kBinRunMax
+        // queries (the kernels draw them largest first from a counter)
+        const int64_t csz = std::min<int64_t>(kBinRunMax, std::max<int64_t>(4096, (int64_t)kBinRunPerCell * G * G));
+        for (int64_t q0 = 0; q0 < cnt; q0 += csz) {
+            bch.push_back(make_int4(d, (int)(offsets[d] + q0), (int)std::min(csz, cnt - q0), (int)std::min<int64_t>(nro, INT32_MAX)));
+            nro += (int64_t)G * G;
+        }
     }
-    if (ncell > INT32_MAX) return fail(WN_ERR_LIMIT, "too many query cells");
+    // largest runs first: the kernels take them in this order from a counter
+    std::stable_sort(bch.begin(), bch.end(), [](const int4 &a, const int4 &b) { return a.z > b.z; });
+    if (ncell > INT32_MAX || nro > INT32_MAX) return fail(WN_ERR_LIMIT, "too many query cells");
     if ((e = grow(T.bchunks, T.cap_bchunks, (int64_t)bch.size())) != cudaSuccess) return cuda_fail(e, "cells");
     T.n_bchunks = (int)bch.size();
     if (!bch.empty() &&
@@ -423,7 +431,10 @@ static wn_status build_tables(DevState *S, Tables &T, const wn_domain *const *do
     if ((e = grow(S->W.cell_cnt, S->W.cap_cells, ncell)) != cudaSuccess) return cuda_fail(e, "cells");
     if ((e = grow(S->W.bin_chunk, S->W.cap_chunk, (ncell + 4095) / 4096)) != cudaSuccess)
         return cuda_fail(e, "cells");
+    if ((e = grow(S->W.run_off, S->W.cap_runoff, std::max<int64_t>(1, nro))) != cudaSuccess)
+        return cuda_fail(e, "cells");
     T.n_cells = (int)ncell;
+    T.n_runoff = nro;
     if ((e = cudaMemcpy(T.dcell, dcell.data(), n_domains * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "upload cells");
     T.key_doms.assign(domains, domains + n_domains);
@@ -667,7 +678,7 @@ static wn_status query_impl(const wn_domain *const *domains, int32_t n_domains,
                                          (uintptr_t)T.key, (uintptr_t)g_tun.sweep_ctas_per_sm,
                                          (uintptr_t)g_tun.near_ctas_per_sm, (uintptr_t)g_tun.bucket,
                                          (uintptr_t)S->W.acc2, (uintptr_t)S->W.near_items, (uintptr_t)S->W.perm,
-                                         (uintptr_t)T.units, (uintptr_t)S->W.cell_cnt, (uintptr_t)T.bchunks,
+                                         (uintptr_t)T.units, (uintptr_t)S->W.cell_cnt, (uintptr_t)T.bchunks, (uintptr_t)S->W.run_off,
                                          (uintptr_t)g_tun.near_depth, (uintptr_t)g_tun.near_chunk,
                                          (uintptr_t)g_tun.near_refill, (uintptr_t)Wl.cap_near,
                                          (uintptr_t)Wl.cap_f64};

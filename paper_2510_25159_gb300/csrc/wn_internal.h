@@ -56,12 +56,13 @@ struct Work {
     int *cell_of = nullptr;    // per query
     int *perm = nullptr;       // per query
     int *cell_cnt = nullptr;   // per cell
+    int *run_off = nullptr;    // per run and cell of the run's domain: the run's offset in the cell
     int4 *dcell = nullptr;     // per domain: first cell, G
     int *bin_chunk = nullptr;  // per 4096 cells: chunk sum, then its first position
-    int4 *bchunks = nullptr;   // (domain, first query, count, 0): runs of one domain's queries
+    int4 *bchunks = nullptr;   // (domain, first query, count, first run_off entry): runs of one domain's queries
     int n_cells = 0;
     int n_bchunks = 0;
-    int64_t cap_bin_q = 0, cap_cells = 0, cap_chunk = 0;
+    int64_t cap_bin_q = 0, cap_cells = 0, cap_chunk = 0, cap_runoff = 0;
     int64_t cap_q = 0, cap_near = 0, cap_f64 = 0;
 };
 
@@ -69,13 +70,20 @@ struct Work {
 // CTA can count one domain's cells in shared memory.
 constexpr int kBinMaxG = 110;
 constexpr int kBinSmemCells = 12288;
+// A query's cell (< 2^14) and its rank among its run's queries of that cell
+// share one 32-bit word: runs hold at most 2^kBinRankBits queries.
+constexpr int kBinRankBits = 17;
+constexpr int kBinRunMax = 1 << kBinRankBits;
+constexpr int kBinRunPerCell = 2;       // a run: about this many queries per cell of its domain
+                                        //   (measured on the B-Rep batch: 2 < 4 < 8 < 16 in time)
 static_assert(kBinMaxG * kBinMaxG <= kBinSmemCells, "cell counters must fit shared memory");
+static_assert(kBinSmemCells <= (1 << (31 - kBinRankBits)), "a cell and a rank must fit one int");
 
 // Device counters of one mixed call.  CNT_DEPTH counts FP64 walks that
 // reached the depth cap (reported BOUNDARY: the oracle's reading of a walk
 // that cannot end, unreachable for d > eps by Lemma 2).
 enum { CNT_NEAR = 0, CNT_F64 = 1, CNT_ESC = 2, CNT_UNIT = 3, CNT_DEPTH = 4, CNT_OVF = 5,
-       CNT_FLAT_UNIT = 6, CNT_NEAR_CURSOR = 7, CNT_N = 8 };
+       CNT_FLAT_UNIT = 6, CNT_NEAR_CURSOR = 7, CNT_BIN_RUN = 8, CNT_SCAT_RUN = 9, CNT_N = 10 };
 
 // Work tallies of the counting build of the tree sweep (per query slot):
 // node tests, nodes whose crossings telescoped, expansion evaluations and
@@ -132,6 +140,10 @@ struct LaunchCfg {
 
 // Kernels (wn_kernels.cu)
 bool mixed_buckets(const Work &W, const LaunchCfg &cfg);        // bucketing kernels run
+// CTAs of k_bin_count (0) or k_bin_scatter (1) that fit on one SM; queried
+// once and cached (first called when a device's state is set up, outside
+// stream capture)
+int bin_blocks_per_sm(int scatter);
 int mixed_kernel_count(const Work &W, const LaunchCfg &cfg);    // kernels one launch_mixed issues
 cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const int4 *d_units,
                          int n_units, const int64_t *d_offsets, int64_t n_queries, PointSrc src,

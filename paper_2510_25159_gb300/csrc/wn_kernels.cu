@@ -1033,13 +1033,15 @@ struct BinArgs {
     const DomDev *doms;
     long long n;
     PointSrc src;
+    unsigned long long *counters;   // CNT_BIN_RUN, CNT_SCAT_RUN: the next run of each kernel
     const int4 *dcell;          // per domain: first cell, G
-    int *cell_of;               // per query
-    int *cnt;                   // per cell: count, then cursor
+    int *cell_of;               // per query: its cell in the run's domain << kBinRankBits | its rank there in the run
+    int *cnt;                   // per cell: count, then first position
+    int *run_off;               // per run and cell of its domain (from the run's .w): the run's offset in the cell
     int *chunk;                 // per chunk of kBinChunk cells: its sum, then its first position
     int *perm;
     int n_cells;
-    const int4 *bchunks;        // (domain, first query, count): runs of one domain's queries
+    const int4 *bchunks;        // (domain, first query, count, first run_off entry): runs of one domain's queries
     int n_bchunks;
 };
 
@@ -1061,64 +1063,93 @@ __device__ __forceinline__ int round_near_int(float v)
 }
 
 // Cell of every query, counted per cell.  One CTA per run of one domain's
-// queries: the run is counted into the domain's cells in shared memory, then
-// one global atomic per non-empty cell adds the run's counts.
-__global__ void __launch_bounds__(kBinThreads) k_bin_count(const BinArgs A)
+// queries: the run is counted into the domain's cells in shared memory (the
+// shared atomic's old value is the query's rank among the run's queries of
+// its cell), then one global atomic per non-empty cell adds the run's count
+// and returns the run's offset within the cell.  Each query keeps its cell
+// and rank in one word (cell < 2^14, rank < 2^kBinRankBits).
+// (3 CTAs of 512 threads per SM: measured faster than 2 with more registers or 4 with spills)
+__global__ void __launch_bounds__(kBinThreads, 3) k_bin_count(const BinArgs A)
 {
-    __shared__ int s_cnt[kBinSmemCells];
+    __shared__ int s_cnt[kBinSmemCells];   // zero at the start of every run (each run clears what it used)
     __shared__ float s_box[8];          // the run's cell frame, from the domain's FP64 fields once per run
-    for (int c = blockIdx.x; c < A.n_bchunks; c += gridDim.x) {
-        const int4 R = __ldg(&A.bchunks[c]);
-        const int4 dc = __ldg(&A.dcell[R.x]);
-        const int G = dc.y, G2 = G * G;
+    __shared__ int4 s_R, s_dc;
+    __shared__ int s_run;
+    for (int i = threadIdx.x; i < kBinSmemCells; i += blockDim.x) s_cnt[i] = 0;
+    for (;;) {
+        // the next run from the shared counter (runs come largest first):
+        // CTAs finish together whatever the mix of run sizes
         if (threadIdx.x == 0) {
-            // G x G cells over the domain's box (the base tile on periodic
-            // axes); FP32 is enough to choose a cell.  One thread converts
-            // the FP64 fields (the FP64 unit is narrow on GB300)
-            const DomDev *Dp = A.doms + R.x;
-            const bool pu = Dp->Pu > 0, pv = Dp->Pv > 0;
-            const float wx = pu ? (float)Dp->Pu : 2.f * Dp->M;
-            const float wy = pv ? (float)Dp->Pv : 2.f * Dp->M;
-            s_box[0] = pu ? 0.f : (float)Dp->ox - Dp->M;
-            s_box[1] = pv ? 0.f : (float)Dp->oy - Dp->M;
-            s_box[2] = wx;
-            s_box[3] = wy;
-            // periodic axes: the coordinate's tile offset removed in FP32 (a
-            // cell choice needs no exactness)
-            s_box[4] = pu ? __fdividef(1.f, wx) : 0.f;
-            s_box[5] = pv ? __fdividef(1.f, wy) : 0.f;
-            s_box[6] = pu ? 1.f : 0.f;
-            s_box[7] = pv ? 1.f : 0.f;
+            const int c = (int)atomicAdd(&A.counters[CNT_BIN_RUN], 1ULL);
+            s_run = c;
+            if (c < A.n_bchunks) {
+                const int4 R = __ldg(&A.bchunks[c]);
+                const int4 dc = __ldg(&A.dcell[R.x]);
+                s_R = R;
+                s_dc = dc;
+                // G x G cells over the domain's box (the base tile on periodic
+                // axes); FP32 is enough to choose a cell.  One thread converts
+                // the FP64 fields (the FP64 unit is narrow on GB300)
+                const DomDev *Dp = A.doms + R.x;
+                const bool pu = Dp->Pu > 0, pv = Dp->Pv > 0;
+                const float wx = pu ? (float)Dp->Pu : 2.f * Dp->M;
+                const float wy = pv ? (float)Dp->Pv : 2.f * Dp->M;
+                s_box[0] = pu ? 0.f : (float)Dp->ox - Dp->M;
+                s_box[1] = pv ? 0.f : (float)Dp->oy - Dp->M;
+                s_box[2] = wx;
+                s_box[3] = wy;
+                // periodic axes: the coordinate's tile offset removed in FP32 (a
+                // cell choice needs no exactness)
+                s_box[4] = pu ? __fdividef(1.f, wx) : 0.f;
+                s_box[5] = pv ? __fdividef(1.f, wy) : 0.f;
+                s_box[6] = pu ? 1.f : 0.f;
+                s_box[7] = pv ? 1.f : 0.f;
+            }
         }
-        for (int i = threadIdx.x; i < G2; i += blockDim.x) s_cnt[i] = 0;
+        // (the previous run's flush is also ordered before this run's counts here)
         __syncthreads();
+        if (s_run >= A.n_bchunks) return;
+        const int4 R = s_R, dc = s_dc;
+        const int G = dc.y, G2 = G * G;
         const float x0 = s_box[0], y0 = s_box[1], wx = s_box[2], wy = s_box[3], ipu = s_box[4], ipv = s_box[5];
         const bool pu = s_box[6] != 0.f, pv = s_box[7] != 0.f;
         const float sx = __fdividef((float)G, wx), sy = __fdividef((float)G, wy);
-        for (int i = threadIdx.x; i < R.z; i += blockDim.x) {
-            const uint32_t q = (uint32_t)(R.y + i);
-            double x, y;
-            get_point(A.src, q, x, y);
-            float xf = f64_to_f32_trunc(x), yf = f64_to_f32_trunc(y);
-            // integer parts by FP32 rounding (no conversion instructions,
-            // which share GB300's narrow FP64 unit): round_near(v) is the
-            // low bits of v + 1.5 * 2^23 for |v| < 2^22; a cell choice needs
-            // neither floor nor exactness, only the clamp below
-            if (pu) xf -= round_near(xf * ipu - 0.5f) * wx;
-            if (pv) yf -= round_near(yf * ipv - 0.5f) * wy;
-            int cx = round_near_int((xf - x0) * sx - 0.5f), cy = round_near_int((yf - y0) * sy - 0.5f);
-            cx = min(max(cx, 0), G - 1);
-            cy = min(max(cy, 0), G - 1);
-            const int lc = cy * G + ((cy & 1) ? G - 1 - cx : cx);      // serpentine order
-            A.cell_of[q] = dc.x + lc;
-            atomicAdd(&s_cnt[lc], 1);
+        // four queries per thread at a time: their point loads issue together
+        for (int i0 = threadIdx.x; i0 < R.z; i0 += 4 * blockDim.x) {
+            double px[4], py[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                px[k] = py[k] = 0.0;
+                if (i0 + k * (int)blockDim.x < R.z) get_point(A.src, (uint32_t)(R.y + i0 + k * blockDim.x), px[k], py[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (i0 + k * (int)blockDim.x >= R.z) continue;
+                const uint32_t q = (uint32_t)(R.y + i0 + k * blockDim.x);
+                float xf = f64_to_f32_trunc(px[k]), yf = f64_to_f32_trunc(py[k]);
+                // integer parts by FP32 rounding (no conversion instructions,
+                // which share GB300's narrow FP64 unit): round_near(v) is the
+                // low bits of v + 1.5 * 2^23 for |v| < 2^22; a cell choice needs
+                // neither floor nor exactness, only the clamp below
+                if (pu) xf -= round_near(xf * ipu - 0.5f) * wx;
+                if (pv) yf -= round_near(yf * ipv - 0.5f) * wy;
+                int cx = round_near_int((xf - x0) * sx - 0.5f), cy = round_near_int((yf - y0) * sy - 0.5f);
+                cx = min(max(cx, 0), G - 1);
+                cy = min(max(cy, 0), G - 1);
+                const int lc = cy * G + ((cy & 1) ? G - 1 - cx : cx);      // serpentine order
+                A.cell_of[q] = lc << kBinRankBits | atomicAdd(&s_cnt[lc], 1);
+            }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < G2; i += blockDim.x) {
             const int v = s_cnt[i];
-            if (v) atomicAdd(&A.cnt[dc.x + i], v);
+            if (v) {
+                A.run_off[R.w + i] = atomicAdd(&A.cnt[dc.x + i], v);
+                s_cnt[i] = 0;
+            }
         }
-        __syncthreads();
+        // no barrier: thread 0 rewrites s_run, s_R, s_dc and s_box only after
+        // every thread has passed the barrier above, past its last read of them
     }
 }
 
@@ -1194,28 +1225,47 @@ __global__ void __launch_bounds__(1024) k_bin_chunk_apply(const BinArgs A)
     }
 }
 
-// Every query to its slot: per run of one domain's queries, the run's count
-// per cell in shared memory, one global atomic per non-empty cell reserves
-// the run's slots of that cell, and the queries take them in turn.
+// Every query to its slot, with no atomics: per run of one domain's
+// queries, the run's first slot in each cell (the cell's first position plus
+// the run's offset in it) in shared memory, and each query at that slot plus
+// its rank.  (Entries of cells the run does not reach were never written and
+// are never used.)
 __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const BinArgs A)
 {
-    __shared__ int s_cnt[kBinSmemCells];
-    for (int c = blockIdx.x; c < A.n_bchunks; c += gridDim.x) {
-        const int4 R = __ldg(&A.bchunks[c]);
-        const int4 dc = __ldg(&A.dcell[R.x]);
-        const int G2 = dc.y * dc.y;
-        for (int i = threadIdx.x; i < G2; i += blockDim.x) s_cnt[i] = 0;
-        __syncthreads();
-        for (int i = threadIdx.x; i < R.z; i += blockDim.x) atomicAdd(&s_cnt[A.cell_of[R.y + i] - dc.x], 1);
-        __syncthreads();
-        for (int i = threadIdx.x; i < G2; i += blockDim.x) {
-            const int v = s_cnt[i];
-            if (v) s_cnt[i] = atomicAdd(&A.cnt[dc.x + i], v);      // the run's first slot in the cell
+    __shared__ uint32_t s_slot[kBinSmemCells];
+    __shared__ int4 s_R, s_dc;
+    __shared__ int s_run;
+    for (;;) {
+        // runs from a shared counter, as in k_bin_count
+        if (threadIdx.x == 0) {
+            const int c = (int)atomicAdd(&A.counters[CNT_SCAT_RUN], 1ULL);
+            s_run = c;
+            if (c < A.n_bchunks) {
+                const int4 R = __ldg(&A.bchunks[c]);
+                s_R = R;
+                s_dc = __ldg(&A.dcell[R.x]);
+            }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < R.z; i += blockDim.x) {
-            const int q = R.y + i;
-            A.perm[atomicAdd(&s_cnt[A.cell_of[q] - dc.x], 1)] = q;
+        if (s_run >= A.n_bchunks) return;
+        const int4 R = s_R, dc = s_dc;
+        const int G2 = dc.y * dc.y;
+        for (int i = threadIdx.x; i < G2; i += blockDim.x)
+            s_slot[i] = (uint32_t)A.cnt[dc.x + i] + (uint32_t)A.run_off[R.w + i];
+        __syncthreads();
+        // four queries per thread at a time: their loads issue together
+        for (int i0 = threadIdx.x; i0 < R.z; i0 += 4 * blockDim.x) {
+            uint32_t v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int i = i0 + k * blockDim.x;
+                v[k] = i < R.z ? (uint32_t)__ldg(&A.cell_of[R.y + i]) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int i = i0 + k * blockDim.x;
+                if (i < R.z) A.perm[s_slot[v[k] >> kBinRankBits] + (v[k] & (kBinRunMax - 1u))] = R.y + i;
+            }
         }
         __syncthreads();
     }
@@ -2067,10 +2117,22 @@ __global__ void k_pe_eval(const DomDev *Dp, const PeReq *req, int n, double *out
 }
 
 // ------------------------------------------------------------------ launchers
+int bin_blocks_per_sm(int scatter)
+{
+    static int per_sm[2] = {0, 0};
+    if (!per_sm[scatter]) {
+        int n = 0;
+        const cudaError_t e = scatter ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bin_scatter, kBinThreads, 0)
+                                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bin_count, kBinThreads, 0);
+        per_sm[scatter] = (e == cudaSuccess && n > 0) ? n : 1;
+    }
+    return per_sm[scatter];
+}
+
 bool mixed_buckets(const Work &W, const LaunchCfg &cfg)
 {
     return cfg.tun.tree && cfg.tun.bucket && !cfg.grid_tiled && W.perm && W.cell_of && W.cell_cnt && W.dcell &&
-           W.bin_chunk && W.bchunks && W.n_cells > 0 && W.n_bchunks > 0;
+           W.bin_chunk && W.bchunks && W.run_off && W.n_cells > 0 && W.n_bchunks > 0;
 }
 
 int mixed_kernel_count(const Work &W, const LaunchCfg &cfg)
@@ -2109,18 +2171,23 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
         ba.dcell = W.dcell;
         ba.cell_of = W.cell_of;
         ba.cnt = W.cell_cnt;
+        ba.run_off = W.run_off;
+        ba.counters = W.counters;
         ba.perm = W.perm;
         ba.n_cells = W.n_cells;
         if ((e = cudaMemsetAsync(W.cell_cnt, 0, (size_t)W.n_cells * sizeof(int), s)) != cudaSuccess) return e;
         ba.bchunks = W.bchunks;
         ba.n_bchunks = W.n_bchunks;
-        const int bin_blocks = std::max(1, std::min(W.n_bchunks, cfg.n_sm * 4));
+        // one wave: as many CTAs as fit on the SMs at once (they draw runs
+        // from a counter, so no CTA waits for a slot while others idle)
+        const int count_blocks = std::max(1, std::min(W.n_bchunks, cfg.n_sm * bin_blocks_per_sm(0)));
+        const int scatter_blocks = std::max(1, std::min(W.n_bchunks, cfg.n_sm * bin_blocks_per_sm(1)));
         const int n_chunks = (W.n_cells + kBinChunk - 1) / kBinChunk;
-        k_bin_count<<<bin_blocks, kBinThreads, 0, s>>>(ba);
+        k_bin_count<<<count_blocks, kBinThreads, 0, s>>>(ba);
         k_bin_chunk_sum<<<n_chunks, 1024, 0, s>>>(ba);
         k_bin_chunk_scan<<<1, 1024, 0, s>>>(ba, n_chunks);
         k_bin_chunk_apply<<<n_chunks, 1024, 0, s>>>(ba);
-        k_bin_scatter<<<bin_blocks, kBinThreads, 0, s>>>(ba);
+        k_bin_scatter<<<scatter_blocks, kBinThreads, 0, s>>>(ba);
     }
     SweepArgs sa;
     sa.doms = d_doms;

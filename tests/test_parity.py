@@ -95,6 +95,29 @@ def test_rational_exact_circles_closed(wn, name, prec, tol):
 
 
 @pytest.mark.parametrize("name,prec,tol", PRECS)
+def test_rational_wide_arcs_near(wn, name, prec, tol):
+    """Circles of wide rational arcs (up to 3 radians: middle weight down to
+    cos(1.5) = 0.07, where App. A.1's segment bound is loosest and the walks
+    also use the bounds of the segments' eighths): points 3e-9..1e-3 from
+    the arcs (states and rounded omega exact) and points on them (boundary)."""
+    rng = np.random.default_rng(11)
+    centres = np.array([[0.5, 0.5], [0.45, 0.55]])
+    radii = np.array([0.4, 0.15])
+    outer = ws.rational_circle_loop(tuple(centres[0]), radii[0], [3.0, 3.0, 2 * np.pi - 6.0])
+    hole = ws.rational_circle_loop(tuple(centres[1]), radii[1], [2.9, 2.2, 2 * np.pi - 5.1], ccw=False)
+    dom = ws.make_domain([outer, hole], eps=1e-9)
+    n, n_on = 4001, 300
+    which = rng.integers(0, 2, n + n_on)
+    off = rng.choice([-1, 1], n) * np.exp(rng.uniform(np.log(3e-9), np.log(1e-3), n))
+    r = radii[which] + np.concatenate([off, np.zeros(n_on)])
+    ph = rng.uniform(0, 2 * np.pi, n + n_on)
+    q = centres[which] + r[:, None] * np.stack([np.cos(ph), np.sin(ph)], axis=1)
+    (w, s), = run(wn, [dom], [q], prec)
+    compare(dom, q, w, s, tol, closed=True)
+    assert np.all(s[n:] == 2)
+
+
+@pytest.mark.parametrize("name,prec,tol", PRECS)
 def test_uniperiodic_cylinders(wn, name, prec, tol):
     rng = ws.rng_for(40)
     doms, qs = [], []
