@@ -103,6 +103,7 @@ struct DomDev {
     float Tm;                   // max |lattice shift|_inf over the instances (0 planar)
     float Mq;                   // queries with |p' - o|_inf > Mq go to FP64
     float Om;                   // max(|ox|, |oy|)
+    float nxf, nyf;             // nx, ny rounded to FP32
     float oxh, oxl, oyh, oyl;   // the origin as FP32 pairs (to ~2^-48)
     const int *seg_deg;         // [n_segs]
     const int *seg_cp;          // [n_segs] first control point (in points)

@@ -714,6 +714,8 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
     dv.M = (float)M;
     dv.Mq = (float)Mq;
     dv.Om = (float)std::fmax(std::fabs(ox), std::fabs(oy));
+    dv.nxf = (float)nx;
+    dv.nyf = (float)ny;
     dv.oxh = (float)ox;
     dv.oxl = (float)(ox - (double)dv.oxh);
     dv.oyh = (float)oy;

@@ -155,6 +155,11 @@ __device__ __forceinline__ void write_out(const OutDst &o, uint32_t q, double om
 // ~1e-7 of the terms, is far inside the band); omega is formed as an exact
 // FP32 pair (product residual, TwoSum, 1/(2 pi) split in two floats) so
 // that its FP64 value costs one FP64 addition.
+// (float)n for |n| < 2^22 without a conversion instruction (conversions
+// share GB300's narrow FP64 unit): 1.5 * 2^23 + n is exact in FP32 with n in
+// the low bits of its fraction.
+__device__ __forceinline__ float small_i2f(int n) { return __int_as_float(0x4B400000 + n) - 12582912.0f; }
+
 __device__ __forceinline__ int settle(int32_t a2, float th, uint32_t f, bool want_w, double &om)
 {
     om = 0.0;
@@ -163,11 +168,12 @@ __device__ __forceinline__ int settle(int32_t a2, float th, uint32_t f, bool wan
         om = __longlong_as_double(0x7ff8000000000000ULL);
         return 2;
     }
-    const float om32 = fmaf(-th, kInv2PiF, 0.5f * (float)a2);
-    const float band = kOmegaBandF + 1e-6f * (fabsf(0.5f * (float)a2) + fabsf(th) * kInv2PiF);
+    const float fa2 = (a2 > -4194304 && a2 < 4194304) ? small_i2f(a2) : (float)a2;
+    const float om32 = fmaf(-th, kInv2PiF, 0.5f * fa2);
+    const float band = kOmegaBandF + 1e-6f * (fabsf(0.5f * fa2) + fabsf(th) * kInv2PiF);
     if (fabsf(om32 - 0.5f) < band) return -1;
     if (want_w) {
-        const float h = 0.5f * (float)a2;
+        const float h = 0.5f * fa2;
         const float p = th * kInv2PiF;
         const float pe = fmaf(th, kInv2PiF, -p);
         const float s = h - p;
@@ -702,8 +708,8 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_tree(const SweepA
             }
         }
         if (lane == 0) {
-            s_wb[warp][5] = (float)Dp->nx;
-            s_wb[warp][6] = (float)Dp->ny;
+            s_wb[warp][5] = Dp->nxf;
+            s_wb[warp][6] = Dp->nyf;
         }
         __syncwarp();
         for (int jb = 0; jb < n_inst; jb += 32) {
@@ -1563,8 +1569,8 @@ __device__ __forceinline__ bool near_start(const NearArgs &A, const Item &it, Ne
     // evaluation error bound: de Casteljau on q (2n + 4 ulps of mq); for a
     // rational segment the homogeneous sums and the division scale it by
     // the weight ratio W/w (with a factor 2 to spare)
-    W.E = W.rat ? kTwoM24 * mq * ((float)(8 * deg + 8) * __int_as_float(si.w) + 8.f) + eabs
-                : (float)(2 * deg + 4) * kTwoM24 * mq + eabs;
+    W.E = W.rat ? kTwoM24 * mq * (small_i2f(8 * deg + 8) * __int_as_float(si.w) + 8.f) + eabs
+                : small_i2f(2 * deg + 4) * kTwoM24 * mq + eabs;
     W.eps = Dp->eps32;
     W.cnt = 0;
     W.a = 0.f;
@@ -1913,6 +1919,56 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs A)
                 A.out.bits[i >> 5] = m;
                 if (mb && A.out.nbound) atomicAdd(A.out.nbound, (unsigned long long)__popc(mb));
             }
+        }
+    }
+}
+
+// The same for outputs in windings and states (no bitmask), four queries
+// per thread and iteration with 16-byte loads and stores (two double2 for
+// omega, one word for the states); the outputs must be 16- and 4-byte
+// aligned.  The last n mod 4 queries take one thread each.
+__global__ void __launch_bounds__(256) k_finalize4(const FinArgs A)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n4 = A.n >> 2;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long j = t0; j < n4; j += stride) {
+        const int4 v = __ldg(reinterpret_cast<const int4 *>(A.acc2) + j);
+        const float4 th = __ldg(reinterpret_cast<const float4 *>(A.theta) + j);
+        const int32_t vv[4] = {v.x, v.y, v.z, v.w};
+        const float tt[4] = {th.x, th.y, th.z, th.w};
+        double om[4];
+        uint32_t stw = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t q = (uint32_t)(4 * j + k);
+            const int st = settle(unpack_acc(vv[k]), tt[k], (uint32_t)vv[k] & 3u, A.out.w != nullptr, om[k]);
+            if (st < 0) {
+                const unsigned long long idx = atomicAdd(&A.counters[CNT_ESC], 1ULL);
+                A.esc[idx] = make_uint2(q, find_dom(A.offsets, A.n_doms, (long long)q));
+                om[k] = 0.0;            // rewritten by the FP64 recomputation
+            } else {
+                stw |= (uint32_t)st << (8 * k);
+            }
+        }
+        if (A.out.w) {
+            double2 *w2 = reinterpret_cast<double2 *>(A.out.w) + 2 * j;
+            w2[0] = make_double2(om[0], om[1]);
+            w2[1] = make_double2(om[2], om[3]);
+        }
+        if (A.out.st) reinterpret_cast<uint32_t *>(A.out.st)[j] = stw;
+    }
+    const long long i = 4 * n4 + t0;
+    if (i < A.n) {
+        const uint32_t q = (uint32_t)i;
+        const int32_t v = A.acc2[q];
+        double om = 0.0;
+        const int st = settle(unpack_acc(v), A.theta[q], (uint32_t)v & 3u, A.out.w != nullptr, om);
+        if (st < 0) {
+            const unsigned long long idx = atomicAdd(&A.counters[CNT_ESC], 1ULL);
+            A.esc[idx] = make_uint2(q, find_dom(A.offsets, A.n_doms, (long long)q));
+        } else {
+            write_out(A.out, q, om, st, false);
         }
     }
 }
@@ -2273,7 +2329,11 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     fa.counters = W.counters;
     fa.out = out;
     const long long fin_blocks = std::max(1LL, std::min((long long)(n_queries + 255) / 256, (long long)cfg.n_sm * 16));
-    k_finalize<<<(int)fin_blocks, 256, 0, s>>>(fa);
+    if (!out.bits && ((uintptr_t)out.w & 15u) == 0 && ((uintptr_t)out.st & 3u) == 0)
+        k_finalize4<<<(int)std::max(1LL, std::min((long long)(n_queries / 4 + 255) / 256, (long long)cfg.n_sm * 16)),
+                      256, 0, s>>>(fa);
+    else
+        k_finalize<<<(int)fin_blocks, 256, 0, s>>>(fa);
     mark(5);
     EscArgs ea;
     ea.doms = d_doms;
