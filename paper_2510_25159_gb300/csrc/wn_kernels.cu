@@ -1068,6 +1068,16 @@ __device__ __forceinline__ int round_near_int(float v)
     return (__float_as_int(t) & 0x7fffff) - 0x400000;
 }
 
+// An FP32 value near the double x from its high word alone (its top 20
+// fraction bits): within 2^-20 relative for |x| in FP32's normal range, a
+// signed zero below it, some other value above it; for cell choices only,
+// which clamp whatever they get.
+__device__ __forceinline__ float f64_hi_to_f32(double x)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), sign = hi & 0x80000000u;
+    return __uint_as_float((hi & 0x7ff00000u) < 0x38100000u ? sign : sign | ((hi - 0x38000000u) << 3));
+}
+
 // Cell of every query, counted per cell.  One CTA per run of one domain's
 // queries: the run is counted into the domain's cells in shared memory (the
 // shared atomic's old value is the query's rank among the run's queries of
@@ -1132,7 +1142,7 @@ __global__ void __launch_bounds__(kBinThreads, 3) k_bin_count(const BinArgs A)
             for (int k = 0; k < 4; k++) {
                 if (i0 + k * (int)blockDim.x >= R.z) continue;
                 const uint32_t q = (uint32_t)(R.y + i0 + k * blockDim.x);
-                float xf = f64_to_f32_trunc(px[k]), yf = f64_to_f32_trunc(py[k]);
+                float xf = f64_hi_to_f32(px[k]), yf = f64_hi_to_f32(py[k]);
                 // integer parts by FP32 rounding (no conversion instructions,
                 // which share GB300's narrow FP64 unit): round_near(v) is the
                 // low bits of v + 1.5 * 2^23 for |v| < 2^22; a cell choice needs
@@ -1147,12 +1157,24 @@ __global__ void __launch_bounds__(kBinThreads, 3) k_bin_count(const BinArgs A)
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < G2; i += blockDim.x) {
-            const int v = s_cnt[i];
-            if (v) {
-                A.run_off[R.w + i] = atomicAdd(&A.cnt[dc.x + i], v);
-                s_cnt[i] = 0;
+        // four cells per thread at a time, so that four returning atomics
+        // are in flight together
+        for (int i0 = threadIdx.x; i0 < G2; i0 += 4 * blockDim.x) {
+            int v[4], old[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int i = i0 + k * blockDim.x;
+                v[k] = i < G2 ? s_cnt[i] : 0;
             }
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (v[k]) old[k] = atomicAdd(&A.cnt[dc.x + i0 + k * blockDim.x], v[k]);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (v[k]) {
+                    A.run_off[R.w + i0 + k * blockDim.x] = old[k];
+                    s_cnt[i0 + k * blockDim.x] = 0;
+                }
         }
         // no barrier: thread 0 rewrites s_run, s_R, s_dc and s_box only after
         // every thread has passed the barrier above, past its last read of them
@@ -1256,8 +1278,18 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const BinArgs A)
         if (s_run >= A.n_bchunks) return;
         const int4 R = s_R, dc = s_dc;
         const int G2 = dc.y * dc.y;
-        for (int i = threadIdx.x; i < G2; i += blockDim.x)
-            s_slot[i] = (uint32_t)A.cnt[dc.x + i] + (uint32_t)A.run_off[R.w + i];
+        for (int i0 = threadIdx.x; i0 < G2; i0 += 4 * blockDim.x) {
+            uint32_t a[4], b[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int i = i0 + k * blockDim.x;
+                a[k] = i < G2 ? (uint32_t)__ldg(&A.cnt[dc.x + i]) : 0u;
+                b[k] = i < G2 ? (uint32_t)__ldg(&A.run_off[R.w + i]) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (i0 + k * (int)blockDim.x < G2) s_slot[i0 + k * blockDim.x] = a[k] + b[k];
+        }
         __syncthreads();
         // four queries per thread at a time: their loads issue together
         for (int i0 = threadIdx.x; i0 < R.z; i0 += 4 * blockDim.x) {
