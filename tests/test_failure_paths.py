@@ -1,7 +1,8 @@
 """Failure and tuning paths of the mixed query, on the GPU, made on the host
 side: queues capped from the host (a pair that does not fit sends its query
 to the FP64 recomputation), the FP32 near walk at its extreme depth caps and
-draw sizes, the escalated-query readback, and the gap angle of the sweep
+draw sizes, the escalated-query readback, output buffers of any alignment
+(the vectorised and the scalar finalize), and the gap angle of the sweep
 against the library's atan2 (the chord angle of Eq. 3 in the crossing form)."""
 import numpy as np
 import pytest
@@ -83,6 +84,43 @@ def test_last_escalated_lists_fp64_queries(wn):
     assert len(esc) == wn.stats()["fp64_queries"]
     assert set(range(300)) <= set(esc.tolist())
     assert np.all(esc < len(q))
+
+
+def test_unaligned_outputs_same_results(wn):
+    """Outputs 16-byte aligned take the four-query finalize, outputs one
+    element off take the scalar one: the same windings (bit for bit) and
+    states, escalated queries (next to a circle's centre) included, on a
+    ragged batch."""
+    import torch
+    doms, qs = _batch()
+    arcs = ws.circle_loop((0.5, 0.5), 0.3, n_arcs=16)[:8]
+    doms = doms + [ws.make_domain([arcs], eps=1e-9)]
+    rng = np.random.default_rng(5)
+    qs = qs + [np.concatenate([0.5 + rng.uniform(-1e-6, 1e-6, (301, 2)), rng.uniform(0.0, 1.0, (2000, 2))])]
+    handles = [wn.Domain.from_dict(d) for d in doms]
+    pts = torch.from_numpy(np.ascontiguousarray(np.concatenate(qs))).cuda()
+    off = np.concatenate([[0], np.cumsum([len(x) for x in qs])]).astype(np.int64)
+    n = int(off[-1])
+    assert n % 4 != 0
+    w_a = torch.empty(n, dtype=torch.float64, device="cuda")
+    s_a = torch.empty(n, dtype=torch.uint8, device="cuda")
+    wn.query_batched(handles, pts, off, out_winding=w_a, out_inside=s_a)
+    torch.cuda.synchronize()
+    assert wn.stats()["fp64_queries"] >= 301
+    W = torch.full((n + 1,), 7.0, dtype=torch.float64, device="cuda")
+    S = torch.full((n + 1,), 9, dtype=torch.uint8, device="cuda")
+    w_u, s_u = W[1:], S[1:]
+    assert w_u.data_ptr() % 16 == 8 and s_u.data_ptr() % 4 == 1
+    wn.query_batched(handles, pts, off, out_winding=w_u, out_inside=s_u)
+    torch.cuda.synchronize()
+    for h in handles:
+        h.close()
+    assert torch.equal(w_a.view(torch.int64), w_u.view(torch.int64))
+    assert torch.equal(s_a, s_u)
+    assert W[0].item() == 7.0 and S[0].item() == 9
+    wa, sa = w_a.cpu().numpy(), s_a.cpu().numpy()
+    for d, q, a, b in zip(doms, qs, off[:-1], off[1:]):
+        compare(d, q, wa[a:b], sa[a:b], TOL_MIXED)
 
 
 def test_gap_angle_against_atan2(wn):
