@@ -367,6 +367,21 @@ wn_status wn_get_stats(wn_stats *out);
 wn_status wn_last_escalated(int64_t *out_idx, int64_t capacity, int64_t *n_out);
 
 /*
+ * Verification hook: the bounds of |gamma'(t)| that the walks of Algorithm 1
+ * use for one rational Bezier segment (App. A.1): out9[0] = B, the smaller
+ * of App. A.1's two bounds on the whole segment; out9[1 + j] = the bound on
+ * the eighth [j/8, (j+1)/8] of its parameter interval (each at most B): 8
+ * times App. A.1's bound of that eighth as a rational Bezier curve of its
+ * own (homogeneous de Casteljau subdivision), with allowances for the
+ * subdivision's rounding.  A node of a walk inside one eighth is far when
+ * ra + rb > B_j (b - a) + 2 eps as well as under Eq. 5 with B.
+ * control_points: 2 (degree + 1) doubles (x0, y0, x1, y1, ...); weights:
+ * degree + 1 doubles > 0; degree 1..7.  Host computation only (no device
+ * call).  Errors: WN_ERR_ARG.
+ */
+wn_status wn_rational_bounds(const double *control_points, const double *weights, int32_t degree, double *out9);
+
+/*
  * Verification hook: the FP32 angle the mixed path assigns to a gap between
  * consecutive segments seen from a query (its share of Eq. 3's chord angles
  * in the crossing form), out[i] = angle of the vector (x[i], y[i]) in

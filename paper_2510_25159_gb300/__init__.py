@@ -82,6 +82,7 @@ def lib():
         L.wn_near_work.argtypes = [P]
         L.wn_last_escalated.argtypes = [P, I64, P]
         L.wn_eval_gap_angle.argtypes = [P, P, P, I64, P]
+        L.wn_rational_bounds.argtypes = [P, P, I32, P]
         L.wn_set_profiling.argtypes = [I32]
         L.wn_kernel_times.argtypes = [P, P]
         L.wn_set_work_counting.argtypes = [I32]
@@ -90,7 +91,7 @@ def lib():
                   "wn_set_tuning", "wn_get_stats", "wn_set_profiling", "wn_kernel_times", "wn_autotune",
                   "wn_get_tuning", "wn_set_work_counting", "wn_sweep_work", "wn_set_near_tuning",
                   "wn_set_queue_limits", "wn_near_work", "wn_last_escalated",
-                  "wn_eval_gap_angle", "wn_set_flat_records", "wn_set_grid_tile"):
+                  "wn_eval_gap_angle", "wn_set_flat_records", "wn_set_grid_tile", "wn_rational_bounds"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -317,6 +318,19 @@ def eval_gap_angle(y, x, stream=None):
     import torch
     out = torch.empty_like(x)
     _check(lib().wn_eval_gap_angle(_ptr(y), _ptr(x), _ptr(out), int(x.numel()), _stream(stream)))
+    return out
+
+
+def rational_bounds(control_points, weights):
+    """App. A.1's bounds of |gamma'| the walks use for one rational segment
+    (host only): numpy [B, B_0, ..., B_7], B over the whole segment and B_j
+    over its eighth [j/8, (j+1)/8]."""
+    cp = np.ascontiguousarray(control_points, dtype=np.float64).reshape(-1, 2)
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+    if len(w) != len(cp):
+        raise ValueError("one weight per control point")
+    out = np.zeros(9)
+    _check(lib().wn_rational_bounds(_ptr(cp), _ptr(w), len(cp) - 1, _ptr(out)))
     return out
 
 

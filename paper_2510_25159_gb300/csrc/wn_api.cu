@@ -232,6 +232,21 @@ wn_status wn_create_domain_rational(const int32_t *loop_offsets, int32_t n_loops
     return WN_OK;
 }
 
+wn_status wn_rational_bounds(const double *control_points, const double *weights, int32_t degree, double *out9)
+{
+    if (!control_points || !weights || !out9) return fail(WN_ERR_ARG, "NULL pointer");
+    if (degree < 1 || degree > kMaxDeg) return fail(WN_ERR_ARG, "degree must be 1..7");
+    for (int i = 0; i <= degree; i++) {
+        if (!(weights[i] > 0.0) || !std::isfinite(weights[i])) return fail(WN_ERR_ARG, "weights must be finite and > 0");
+        if (!std::isfinite(control_points[2 * i]) || !std::isfinite(control_points[2 * i + 1]))
+            return fail(WN_ERR_ARG, "control points must be finite");
+    }
+    out9[0] = rational_segment_bound(control_points, weights, degree);
+    rational_eighth_bounds(control_points, weights, degree, out9[0], out9 + 1);
+    g_err.clear();
+    return WN_OK;
+}
+
 wn_status wn_create_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
                            const double *control_points, double period_u, double period_v,
                            double epsilon, wn_domain **out)

@@ -68,6 +68,30 @@ struct DevBuf {
 
 long long lround_ll(double x) { return (long long)std::llround(x); }
 
+}  // namespace
+
+// App. A.1's two bounds of |gamma'| for a rational segment of degree n
+// (control points P, weights w > 0), the smaller of n (W/w) max |P_i - P_j|
+// and n (W/w)^2 max |P_i - P_{i-1}|.
+double rational_segment_bound(const double *P, const double *w, int n)
+{
+    double wmax = w[0], wmin = w[0];
+    for (int i = 1; i <= n; i++) {
+        wmax = std::fmax(wmax, w[i]);
+        wmin = std::fmin(wmin, w[i]);
+    }
+    const double r = wmax / wmin;
+    double dall = 0.0, dnext = 0.0;
+    for (int i = 0; i <= n; i++)
+        for (int j = i + 1; j <= n; j++) {
+            const double dx = P[2 * j] - P[2 * i], dy = P[2 * j + 1] - P[2 * i + 1];
+            const double d = std::sqrt(dx * dx + dy * dy);
+            dall = std::fmax(dall, d);
+            if (j == i + 1) dnext = std::fmax(dnext, d);
+        }
+    return std::fmin((double)n * r * dall, (double)n * r * r * dnext);
+}
+
 // App. A.1's bounds of |gamma'| on each eighth [j/8, (j+1)/8] of a rational
 // segment of degree n (control points P, weights w > 0, segment bound B).
 // An eighth is itself a rational Bezier curve of degree n, its homogeneous
@@ -143,7 +167,6 @@ void rational_eighth_bounds(const double *P, const double *w, int n, double B, d
     }
 }
 
-}  // namespace
 
 int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *degrees,
                  const double *cps, const double *weights, double Pu, double Pv, double eps,
@@ -257,22 +280,7 @@ int build_domain(const int32_t *loop_offsets, int32_t n_loops, const int32_t *de
             } else {
                 // App. A.1 (rational): n (W/w) max |P_i - P_j| and
                 // n (W/w)^2 max |P_i - P_{i-1}| both bound |gamma'|; the smaller
-                const double *w = &Wt[seg_cp[s]];
-                double wmax = w[0], wmin = w[0];
-                for (int i = 1; i <= n; i++) {
-                    wmax = std::fmax(wmax, w[i]);
-                    wmin = std::fmin(wmin, w[i]);
-                }
-                const double r = wmax / wmin;
-                double dall = 0.0, dnext = 0.0;
-                for (int i = 0; i <= n; i++)
-                    for (int j = i + 1; j <= n; j++) {
-                        const double dx = q[2 * j] - q[2 * i], dy = q[2 * j + 1] - q[2 * i + 1];
-                        const double d = std::sqrt(dx * dx + dy * dy);
-                        dall = std::fmax(dall, d);
-                        if (j == i + 1) dnext = std::fmax(dnext, d);
-                    }
-                B = std::fmin((double)n * r * dall, (double)n * r * r * dnext);
+                B = rational_segment_bound(q, &Wt[seg_cp[s]], n);
             }
             segB[s] = B;
             for (int i = 0; i <= n; i++) {

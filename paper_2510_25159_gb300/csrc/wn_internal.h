@@ -139,6 +139,10 @@ struct LaunchCfg {
 };
 
 // Kernels (wn_kernels.cu)
+// App. A.1's bound of |gamma'| for a rational segment of degree n, and the
+// bounds on its eighths [j/8, (j+1)/8] (each at most B) (wn_domain.cu)
+double rational_segment_bound(const double *P, const double *w, int n);
+void rational_eighth_bounds(const double *P, const double *w, int n, double B, double out[8]);
 bool mixed_buckets(const Work &W, const LaunchCfg &cfg);        // bucketing kernels run
 // CTAs of k_bin_count (0) or k_bin_scatter (1) that fit on one SM; queried
 // once and cached (first called when a device's state is set up, outside
