@@ -337,10 +337,17 @@ def run_reference(args, rank, world):
 
 
 def _kernel_sha():
+    """Hash of the kernels' code (wn_kernels.cu, wn_dev.cuh) with comments
+    and whitespace removed: a capture of the kernels' counters stays valid
+    until their code changes."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for f in ("wn_kernels.cu", "wn_dev.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2510_25159_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2510_25159_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:12]
 
 

@@ -21,10 +21,13 @@
 //   k_near        FP32 Algorithm 1 on each queued pair in query-relative
 //                 coordinates; every test carries an error band, and a pair
 //                 whose band cannot settle a decision hands its tail to FP64.
-//   k_f64items    Algorithm 1 in FP64 on those tails.
+//   k_f64items    Algorithm 1 in FP64 on those tails.  (Both walks also test
+//                 a rational segment's nodes against the derivative bound of
+//                 the eighth of [0, 1] they lie in.)
 //   k_finalize    omega = crossings + line terms / 2 - sum(gap angles) / 2 pi;
 //                 a query whose omega lies within 1e-4 of 1/2, or that any
-//                 kernel flagged, is recomputed in FP64.
+//                 kernel flagged, is recomputed in FP64 (k_finalize4: the same,
+//                 four queries per thread, for aligned outputs).
 //   k_f64query    the FP64 recomputation of those queries (crossing form).
 // Plain path (WN_PREC_PLAIN_FP64): k_plain, one thread per query running
 // Algorithm 1 in FP64 on every segment the query sees, chord angles summed
