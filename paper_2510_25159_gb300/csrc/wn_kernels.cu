@@ -26,8 +26,9 @@
 //                 the eighth of [0, 1] they lie in.)
 //   k_finalize    omega = crossings + line terms / 2 - sum(gap angles) / 2 pi;
 //                 a query whose omega lies within 1e-4 of 1/2, or that any
-//                 kernel flagged, is recomputed in FP64 (k_finalize4: the same,
-//                 four queries per thread, for aligned outputs).
+//                 kernel flagged, is recomputed in FP64 (k_finalize4 and
+//                 k_finalize_bits4: the same, four queries per thread, for
+//                 aligned outputs and for bitmasks).
 //   k_f64query    the FP64 recomputation of those queries (crossing form).
 // Plain path (WN_PREC_PLAIN_FP64): k_plain, one thread per query running
 // Algorithm 1 in FP64 on every segment the query sees, chord angles summed
@@ -2008,6 +2009,74 @@ __global__ void __launch_bounds__(256) k_finalize4(const FinArgs A)
     }
 }
 
+// Bit i of a byte to bit 4 i of a word.
+__device__ __forceinline__ uint32_t spread4(uint32_t x)
+{
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    return (x | (x << 3)) & 0x11111111u;
+}
+
+// The bitmask form (a grid's cells, no windings or states out): each warp
+// takes 128 consecutive queries, four per lane by 16-byte loads, and writes
+// their four words (bit 4 j + k of word w is query 4 (8 w + j) + k of the
+// warp's lane 8 w + j, interleaved from four ballots); escalated queries
+// keep 0 here and are ORed in by the FP64 recomputation.
+__global__ void __launch_bounds__(256) k_finalize_bits4(const FinArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const long long n_tasks = (A.n + 127) >> 7;
+    const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < n_tasks; t += n_warps) {
+        const long long q0 = 128 * t + 4 * lane;
+        int32_t v[4] = {0, 0, 0, 0};
+        float th[4] = {0.f, 0.f, 0.f, 0.f};
+        if (q0 + 3 < A.n) {
+            const int4 a = __ldg(reinterpret_cast<const int4 *>(A.acc2) + (q0 >> 2));
+            const float4 b = __ldg(reinterpret_cast<const float4 *>(A.theta) + (q0 >> 2));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            th[0] = b.x; th[1] = b.y; th[2] = b.z; th[3] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (q0 + k < A.n) {
+                    v[k] = A.acc2[q0 + k];
+                    th[k] = A.theta[q0 + k];
+                }
+        }
+        unsigned m[4], mb[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const bool in_range = q0 + k < A.n;
+            bool esc = false;
+            int st = 0;
+            if (in_range) {
+                double om;
+                st = settle(unpack_acc(v[k]), th[k], (uint32_t)v[k] & 3u, false, om);
+                esc = st < 0;
+                if (esc) {
+                    const uint32_t q = (uint32_t)(q0 + k);
+                    const unsigned long long idx = atomicAdd(&A.counters[CNT_ESC], 1ULL);
+                    A.esc[idx] = make_uint2(q, find_dom(A.offsets, A.n_doms, (long long)q));
+                }
+            }
+            m[k] = __ballot_sync(0xffffffffu, in_range && !esc && st != 0);
+            mb[k] = __ballot_sync(0xffffffffu, in_range && !esc && st == 2);
+        }
+        if (lane < 4) {
+            uint32_t word = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; k++) word |= spread4((m[k] >> (8 * lane)) & 0xffu) << k;
+            const long long wi = 4 * t + lane;
+            if (32 * wi < A.n) A.out.bits[wi] = word;
+        }
+        if (lane == 0 && A.out.nbound) {
+            const int nb = __popc(mb[0]) + __popc(mb[1]) + __popc(mb[2]) + __popc(mb[3]);
+            if (nb) atomicAdd(A.out.nbound, (unsigned long long)nb);
+        }
+    }
+}
+
 struct EscArgs {
     const DomDev *doms;
     PointSrc src;
@@ -2367,6 +2436,10 @@ cudaError_t launch_mixed(const Work &W, const DomDev *d_doms, int n_doms, const 
     if (!out.bits && ((uintptr_t)out.w & 15u) == 0 && ((uintptr_t)out.st & 3u) == 0)
         k_finalize4<<<(int)std::max(1LL, std::min((long long)(n_queries / 4 + 255) / 256, (long long)cfg.n_sm * 16)),
                       256, 0, s>>>(fa);
+    else if (out.bits && !out.w && !out.st)
+        k_finalize_bits4<<<(int)std::max(1LL, std::min((long long)(n_queries / 4 + 255) / 256,
+                                                         (long long)cfg.n_sm * 16)),
+                           256, 0, s>>>(fa);
     else
         k_finalize<<<(int)fin_blocks, 256, 0, s>>>(fa);
     mark(5);
